@@ -1,0 +1,66 @@
+"""Pins of the oracle's solvers: dense LU on a 4^3 grid = sparse direct = BiCGStab = GMRES, and
+manufactured solutions b = A e* recovered within kappa * tol (Sec. IV solvers; Eq. e2)."""
+import numpy as np
+import pytest
+
+import fitgen as G
+from oracle import fit as F
+from oracle import krylov as K
+
+
+def _system(case, f):
+    me, mk, mn, mask = F.material_diagonals(case["dx"], case["dy"], case["dz"], case["eps_r"], case["sigma"],
+                                            case["inv_mu_r"], case["pec"])
+    A = F.system_matrix(2 * np.pi * f, F.curl(case["nx"], case["ny"], case["nz"]), me, mk, mn, mask)
+    return A, mask
+
+
+@pytest.mark.parametrize("lossy", [True, False])
+def test_direct_and_krylov_agree_on_4cubed(lossy):
+    c = G.small_random(4, 4, 4, seed=5, lossy=lossy)
+    A, mask = _system(c, 2e9)
+    b = G.random_vector(A.shape[0], seed=6) * (1 - mask)
+    x_dense = K.dense_solve(A, b)
+    x_sparse = K.sparse_solve(A, b)
+    assert np.linalg.norm(x_dense - x_sparse) <= 1e-12 * np.linalg.norm(x_dense)
+    xb, it, rr, st = K.bicgstab(A, b, tol=1e-12, maxiter=5000)
+    assert st == 0 and rr <= 1e-12
+    xg, it, rr, st = K.fgmres(A, b, tol=1e-12, restart=40, maxiter=5000)
+    assert st == 0 and rr <= 1e-12
+    cond = np.linalg.cond(A.toarray())
+    for x in (xb, xg):
+        assert np.linalg.norm(x - x_dense) <= 10 * cond * 1e-12 * np.linalg.norm(x_dense)
+
+
+@pytest.mark.parametrize("kind", ["random", "smooth"])
+def test_manufactured_solution(kind):
+    c = G.small_random(6, 5, 6, seed=12, pec_frac=0.05)
+    A, mask = _system(c, 3e9)
+    n = A.shape[0]
+    if kind == "random":
+        xs = G.random_vector(n, seed=13)
+    else:
+        cell = np.arange(n) // 3
+        i, j, k = cell % 6, (cell // 6) % 5, cell // 30
+        xs = np.sin(np.pi * (i + 0.5) / 6) * np.sin(np.pi * (j + 0.5) / 5) * np.sin(np.pi * (k + 0.5) / 6) + 0j
+    xs = xs * (1 - mask)
+    b = A @ xs
+    x, it, rr, st = K.bicgstab(A, b, tol=1e-12, maxiter=20000)
+    assert st == 0
+    cond = np.linalg.cond(A.toarray())
+    assert np.linalg.norm(x - xs) <= cond * 1e-12 * np.linalg.norm(xs) * 10
+    x2 = K.sparse_solve(A, b)
+    assert np.linalg.norm(x2 - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_cavity16_bicgstab_vs_sparse_direct():
+    """The cavity workload: 16^3 PEC vacuum cube, 5 GHz, unit current on the centre z-edge."""
+    c = G.cavity(16)
+    A, mask = _system(c, c["freqs"][0])
+    b = F.rhs_from_current(2 * np.pi * c["freqs"][0], G.source_vector(c), mask)
+    x_d = K.sparse_solve(A, b)
+    assert K.relres(A, x_d, b) < 1e-12
+    x, it, rr, st = K.bicgstab(A, b, tol=1e-10, maxiter=20000)
+    assert st == 0 and rr <= 1e-10
+    assert np.linalg.norm(x - x_d) <= 1e-6 * np.linalg.norm(x_d)
+    assert np.all(x[mask != 0] == 0)
