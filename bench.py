@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free FIT operator apply (and the Krylov solve built on it).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fit|reference] [--workload NAME]
+
+One step = one fused operator apply y = A(w) x (the kernel every Krylov iteration repeats) over the
+whole synthetic workload, complex64 vectors with FP32 coefficients.  The timed region holds
+exactly K steps; between steps the L2 is flushed (a 512 MiB buffer is written, then a second one
+is read, so no dirty line of the flush is written back inside a timed apply), and each apply is
+timed with CUDA events on the stream it is launched on.  ``value`` = unknowns per second (GDoF/s)
+over all ranks; ``e2e`` is the same metric through the C ABI with pinned host buffers, the
+host->device copy of x and the device->host copy of y inside the timed region.
+
+``--impl reference`` times the CPU oracle (scipy CSR sparse matrix-vector product of the
+explicitly assembled A, single-threaded) on a bounded z-slab sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (frequencies / right-hand sides
+are independent units: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_DOF_C64 = 28.0   # read x 8 + write y 8 + M_nu, M_eps, M_kappa 3 x 4 (compulsory, per unknown)
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def _workload(name):
+    import fitgen as G
+    if name == "layered128":
+        return G.layered_blocks()
+    if name == "stripline96":
+        return G.stripline()
+    if name == "package256":
+        return G.package()
+    if name == "cavity16":
+        return G.cavity()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fit_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [t.strip() for t in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_apply(case, target_s=10.0, nz_sample=16, reps_max=1000):
+    """Time the oracle's CSR SpMV of the assembled A on the first nz_sample z-planes of the case."""
+    from oracle import fit as F
+    nx, ny = case["nx"], case["ny"]
+    nz = min(nz_sample, case["nz"])
+    sl = slice(0, nz)
+    me, mk, mn, mask = F.material_diagonals(case["dx"], case["dy"], case["dz"][:nz], case["eps_r"][sl],
+                                            case["sigma"][sl], case["inv_mu_r"][sl], case["pec"][sl])
+    w = 2 * np.pi * float(case["freqs"][0])
+    A = F.system_matrix(w, F.curl(nx, ny, nz), me, mk, mn, mask)
+    x = np.random.default_rng(0).standard_normal(A.shape[0]) + 0j
+    A @ x
+    times = []
+    t_start = time.perf_counter()
+    while (time.perf_counter() - t_start) < target_s and len(times) < reps_max:
+        t0 = time.perf_counter()
+        A @ x
+        times.append(time.perf_counter() - t0)
+    ne = A.shape[0]
+    return dict(ne=ne, times=times, sample=f"{nx}x{ny}x{nz} z-slab of {case['name']} ({ne} unknowns), "
+                                            f"{len(times)} CSR SpMVs of the assembled A")
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    case = _workload(args.workload)
+    budget_s = min(60.0, max(5.0, 0.5 * (args.steps + args.warmup)))
+    # W warm-up and K timed steps; each step is one SpMV of the bounded sample
+    rr = cpu_oracle_apply(case, target_s=budget_s, reps_max=args.steps + args.warmup)
+    ne = rr["ne"]
+    ts = rr["times"][args.warmup:] or rr["times"]
+    total = sum(ts)
+    val = ne * len(ts) / total / 1e9
+    line = {"impl": "reference", "metric": "GDoF/s operator apply", "value": val, "unit": "GDoF/s",
+            "n_gpus": args.gpus, "steps": len(ts), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": args.workload, "sample": rr["sample"]},
+            "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": rr["sample"]},
+            "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fit", choices=["fit", "reference"])
+    ap.add_argument("--workload", default="layered128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    from paper_1705_08849_gb300 import build, fit
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    fit.lib()
+
+    case = _workload(args.workload)
+    ne = 3 * case["nx"] * case["ny"] * case["nz"]
+    w = 2 * np.pi * float(case["freqs"][0])
+    g = fit.Grid.from_case(case)
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234 + rank)
+    x = torch.randn(ne, dtype=torch.complex64, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    flush_w = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_w.zero_()
+        flush_r.sum()
+
+    for _ in range(args.warmup):
+        g.apply([w], x, y, fit.FIT_C64)
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush()
+            evs[k][0].record(stream)
+            g.apply([w], x, y, fit.FIT_C64)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(times_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * ne * args.steps / (total_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    k_e2e = max(10, min(args.steps, 200))
+    for _ in range(3):
+        xd.copy_(xh, non_blocking=True)
+        g.apply([w], xd, y, fit.FIT_C64)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k_e2e):
+        xd.copy_(xh, non_blocking=True)
+        g.apply([w], xd, y, fit.FIT_C64)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / k_e2e
+    e2e_val = world * ne / (e2e_ms * 1e-3) / 1e9
+
+    peaks, kind = _peaks()
+    achieved = BYTES_PER_DOF_C64 * ne / (ms_step * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind, "traffic": None,
+            "bytes_per_dof": BYTES_PER_DOF_C64, "kernel": "fit apply (c64)"}
+
+    line = {"metric": "GDoF/s operator apply", "value": value, "unit": "GDoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": [case["nx"], case["ny"], case["nz"]], "unknowns": ne,
+                       "omega_hz": float(case["freqs"][0]), "l2": "flushed between timed applies (512 MiB write "
+                       "then 512 MiB read)", "parallelism": f"replicas{world}"},
+            "roofline": roof, "clocks": clk.summary(),
+            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ne, "d2h_bytes_per_step": 8 * ne},
+            "gpu_launches": args.steps}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        r = cpu_oracle_apply(case, target_s=10.0)
+        cv = r["ne"] * len(r["times"]) / sum(r["times"]) / 1e9
+        line["cpu_baseline"] = {"value": cv, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": r["sample"]}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

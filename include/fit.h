@@ -1,0 +1,160 @@
+/*
+ * fit.h -- C ABI of the GB300 (sm_103a) matrix-free FIT operator and its Krylov solvers.
+ *
+ * The library implements the frequency-domain finite integration technique of
+ * A. Geranmayeh, "Parallel Matrix-Free Implementation of Frequency-Domain Finite Difference
+ * Methods for Cluster Computing" (arXiv 1705.08849):
+ *
+ *     A(w) e = (C^T M_nu C - w^2 M_eps + j w M_kappa) e = b                 (Sec. II, Eq. e2)
+ *
+ * on a staggered Cartesian grid of nx * ny * nz cells.  C is the primal curl (Eq. CP), never
+ * stored; M_nu = M_mu^{-1}, M_eps, M_kappa are diagonal material matrices (Eq. Material).
+ *
+ * Conventions shared by every call
+ *  - Unknown layout (Eq. e12Nxyz, cell-by-cell): cell (i, j, k), 0 <= i < nx, ..., has linear
+ *    index c = i + nx*(j + ny*k) and owns the x-, y- and z-edge leaving its low node; the
+ *    unknown index is 3*c + w, w = 0, 1, 2 for x, y, z.  n_e = 3 * nx * ny * nz.  Complex values
+ *    are interleaved (re, im): a FIT_C64 vector is n_e float2, a FIT_C128 vector n_e double2.
+ *    A batch of B vectors is B such vectors back to back (vector b starts at b * n_e).
+ *  - Boundaries: all six walls are PEC.  Edges lying in a low wall plane and all 12 edges of a
+ *    PEC cell are "masked": their rows and columns of A are the identity (E_tan = 0, Sec. II).
+ *    Entities on the high walls are not stored (identically zero).
+ *  - Memory: vectors (x, y, rhs, solutions) are DEVICE pointers owned by the caller, on the
+ *    device that was current at fit_grid_create.  Geometry and material inputs are HOST
+ *    pointers, copied in before the call returns.  The handle owns every derived device array.
+ *  - Errors: every call returns a fit_status and never throws across the ABI.  Negative values
+ *    are errors that leave outputs unspecified; FIT_NOT_CONVERGED / FIT_BREAKDOWN still fill
+ *    the solution and the report.  fit_last_error() gives a message for the calling thread.
+ *  - Threads/streams: a handle is used by one host thread at a time.  Kernels run on the stream
+ *    the caller passes (a cudaStream_t cast to void*, NULL = legacy default stream).
+ */
+#ifndef FIT_GB300_H
+#define FIT_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fit_grid fit_grid; /* opaque, library-owned */
+
+typedef enum {
+  FIT_OK = 0,
+  FIT_NOT_CONVERGED = 1, /* iteration cap reached; x holds the last iterate */
+  FIT_BREAKDOWN = 2,     /* Krylov breakdown (|rho| or |omega| underflow, zero Hessenberg) */
+  FIT_EINVAL = -1,       /* bad argument (null pointer, size, unsupported option) */
+  FIT_ENOMEM = -2,       /* device allocation failed */
+  FIT_ECUDA = -3,        /* a CUDA runtime/driver call failed */
+  FIT_ETIMEOUT = -4,     /* a bounded device-side wait ran out */
+  FIT_EBUDGET = -5,      /* the request exceeds the handle's HBM budget; nothing was allocated */
+  FIT_ENAN = -6          /* a NaN/Inf appeared in the right-hand side or an iterate */
+} fit_status;
+
+typedef enum { FIT_C64 = 0, FIT_C128 = 1 } fit_prec;
+
+#define FIT_BC_PEC_ALL 0x3Fu /* one bit per wall (x-, x+, y-, y+, z-, z+); only PEC is supported */
+
+/* fit_grid_create -- allocate a grid handle on the current CUDA device.
+ * Sec. II (primal/dual grid pair G, G~ with edge lengths L and facet areas A).
+ *   nx, ny, nz   cells per axis, each >= 1
+ *   dx, dy, dz   host arrays of the nx / ny / nz primal cell widths [m], all > 0
+ *   bc_flags     must be FIT_BC_PEC_ALL
+ *   out          receives the handle (NULL on error)
+ * Returns FIT_EINVAL on bad sizes/widths/flags, FIT_ENOMEM / FIT_ECUDA on device failure. */
+fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const double* dy,
+                           const double* dz, unsigned bc_flags, fit_grid** out);
+
+/* fit_set_materials -- build M_eps, M_kappa, M_nu and the edge mask on the device from per-cell
+ * materials (Sec. II, Eq. Material: eps averaged over the dual facet, 1/mu along the dual edge,
+ * times the grid metric; PEC folded in as the edge mask, Sec. II end).
+ *   eps_r, sigma, inv_mu_r   host float arrays of nx*ny*nz cells, index i + nx*(j + ny*k):
+ *                            relative permittivity (> 0), conductivity [S/m] (>= 0), 1/mu_r (> 0)
+ *   pec_cell                 host uint8 array of nx*ny*nz (nonzero = PEC cell) or NULL
+ * Synchronous.  FIT_EINVAL on null pointers. */
+fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma,
+                             const float* inv_mu_r, const unsigned char* pec_cell);
+
+/* fit_set_material_matrices -- load the diagonals directly (Eq. Material, already assembled):
+ *   m_eps, m_kappa   host double arrays of n_e edge values (interleaved ordering)
+ *   m_nu             host double array of n_e facet values (facet w of cell c at 3*c + w)
+ *   edge_mask        host uint8 array of n_e (nonzero = masked edge) or NULL (no mask)
+ * Replaces whatever fit_set_materials built.  Synchronous. */
+fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const double* m_kappa,
+                                     const double* m_nu, const unsigned char* edge_mask);
+
+/* fit_apply -- y_b = A(omega_b) x_b for b = 0 .. nbatch-1 (Eq. e2 operator, matrix-free as in
+ * Sec. III / Eq. e2t, fused into one stencil pass): masked rows return y = x.
+ *   nbatch   >= 1 systems in the batch
+ *   omega    HOST array of nbatch angular frequencies [rad/s]
+ *   x, y     DEVICE arrays of nbatch * n_e complex values of precision prec; must not overlap
+ *   prec     FIT_C64 (float2 vectors, FP32 arithmetic) or FIT_C128 (double2, FP64 arithmetic)
+ *   stream   cudaStream_t (as void*) on which the kernel is enqueued; asynchronous
+ * FIT_EINVAL on bad arguments. */
+fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
+                     fit_prec prec, void* stream);
+
+typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1 } fit_method;
+typedef enum { FIT_SOLVE_C128 = 0, FIT_SOLVE_MIXED = 1 } fit_solve_precision;
+typedef enum { FIT_PC_NONE = 0, FIT_PC_JACOBI = 1, FIT_PC_UNET = 2 } fit_pc_kind;
+
+typedef struct fit_solve_opts {
+  int method;        /* fit_method: BiCGStab or FGMRES(restart) (Sec. IV, Fig. Iterative) */
+  int restart;       /* FGMRES restart length m (1..64); default 30 */
+  int precision;     /* fit_solve_precision: plain complex128 Krylov, or complex64 inner Krylov
+                        inside FP64 iterative refinement (true residual b - A x in FP64) */
+  int max_iter;      /* cap on Krylov iterations per system (summed over refinement steps) */
+  int max_outer;     /* cap on refinement steps (FIT_SOLVE_MIXED); default 20 */
+  double inner_tol;  /* relative tolerance of each inner complex64 solve; default 1e-4 */
+  int batch;         /* systems solved together in one batched launch; 0 = all nfreq */
+  int use_graph;     /* nonzero: run the Krylov loop as one CUDA graph with a device-side loop */
+  int precond;       /* fit_pc_kind applied as the right preconditioner (FGMRES) */
+  void* stream;      /* cudaStream_t (as void*) for all work; NULL = legacy default stream */
+} fit_solve_opts;
+
+typedef struct fit_solve_report {
+  int status;        /* fit_status of this system */
+  int iterations;    /* Krylov iterations (inner iterations summed over refinement steps) */
+  int outer;         /* refinement steps taken (0 for FIT_SOLVE_C128) */
+  double relres;     /* final true relative residual ||b - A x||_2 / ||b||_2, computed in FP64 */
+  double seconds;    /* wall time of the batch this system was solved in */
+} fit_solve_report;
+
+/* fit_solve_opts_default -- fill opts with the defaults named above. */
+void fit_solve_opts_default(fit_solve_opts* opts);
+
+/* fit_solve -- solve A(omega_f) x_f = rhs_f for f = 0 .. nfreq-1 to ||b - A x|| <= tol ||b||
+ * (Sec. IV stop criterion on the relative residual; the test is on the true residual).
+ *   nfreq    >= 1 systems (frequencies, right-hand sides) on this geometry
+ *   omega    HOST array of nfreq angular frequencies [rad/s]
+ *   rhs      DEVICE array of nfreq * n_e double2 (b = -j w j for an impressed current j, Eq. e2)
+ *   x        DEVICE array of nfreq * n_e double2, overwritten with the solutions (x0 = 0)
+ *   tol      relative residual target (> 0)
+ *   opts     NULL for defaults
+ *   report   HOST array of nfreq reports (may be NULL)
+ * Returns FIT_OK if every system converged, else the first non-OK per-system status, or an
+ * error.  Synchronous on opts->stream.  FIT_EBUDGET if the Krylov workspace for the batch does
+ * not fit the handle's HBM budget (checked before any allocation). */
+fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rhs, void* x,
+                     double tol, const fit_solve_opts* opts, fit_solve_report* report);
+
+/* fit_set_hbm_budget -- cap (bytes) on the device memory the handle may hold; 0 = no cap. */
+fit_status fit_set_hbm_budget(fit_grid* g, size_t bytes);
+
+/* fit_grid_info -- sizes: out[0..5] = nx, ny, nz, n_e, bytes held on the device, budget. */
+fit_status fit_grid_info(const fit_grid* g, long long* out6);
+
+/* fit_grid_destroy -- free the handle and all its device memory (NULL is a no-op). */
+void fit_grid_destroy(fit_grid* g);
+
+/* fit_status_str -- static English name of a status code. */
+const char* fit_status_str(fit_status s);
+
+/* fit_last_error -- message describing the last error on the calling host thread ("" if none). */
+const char* fit_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIT_GB300_H */

@@ -1,0 +1,368 @@
+// Grid handle, material assembly (Sec. II, Eq. Material) and the public apply entry point.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fit_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+void fit_set_error(const std::string& msg) { g_last_error = msg; }
+const char* fit_get_error() { return g_last_error.c_str(); }
+
+fit_status fit_dev_alloc(fit_grid* g, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return FIT_OK;
+  if (g->budget && g->bytes_held + bytes > g->budget) {
+    fit_set_error("device allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+    return FIT_EBUDGET;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    (void)cudaGetLastError();
+    fit_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return FIT_ENOMEM;
+  }
+  g->bytes_held += bytes;
+  return FIT_OK;
+}
+
+void fit_dev_free(fit_grid* g, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  g->bytes_held -= std::min(g->bytes_held, bytes);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Material assembly.  One thread per cell (i, j, k) gathers, for the x-, y- and z-edge leaving its
+// low node, the (up to) four cells that share the edge, and for its three primal facets the two
+// half cells on the dual edge through the facet.  Cells beyond a wall contribute nothing.
+//   M_eps  = eps0 * sum_c eps_r(c) * (h_u(c)/2)(h_v(c)/2) / h_w        (dual-facet average)
+//   M_kap  =        sum_c sigma(c) * (h_u(c)/2)(h_v(c)/2) / h_w
+//   M_nu   = sum_halves (h_w/2) inv_mu_r / mu0 / (h_u h_v)              (dual-edge average)
+// An edge is masked if it lies in a low wall plane or any cell sharing it is PEC.
+// ------------------------------------------------------------------------------------------------
+struct CellField {
+  const float* a;
+  int nx, ny, nz;
+  __device__ double at(int i, int j, int k) const {
+    if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return 0.0;
+    return (double)a[i + (long long)nx * (j + (long long)ny * k)];
+  }
+};
+
+__device__ inline double width(const double* d, int n, int i) { return (i >= 0 && i < n) ? d[i] : 0.0; }
+
+__global__ void assemble_kernel(const double* __restrict__ dx, const double* __restrict__ dy,
+                                const double* __restrict__ dz, const float* __restrict__ eps_r,
+                                const float* __restrict__ sigma, const float* __restrict__ inv_mu_r,
+                                const uint8_t* __restrict__ pec, int nx, int ny, int nz, int nxp,
+                                double* __restrict__ nu64, double* __restrict__ ek64, uint8_t* __restrict__ mask) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long ncell = (long long)nx * ny * nz;
+  if (t >= ncell) return;
+  int i = (int)(t % nx);
+  int j = (int)((t / nx) % ny);
+  int k = (int)(t / ((long long)nx * ny));
+  CellField E{eps_r, nx, ny, nz}, S{sigma, nx, ny, nz}, M{inv_mu_r, nx, ny, nz};
+  auto is_pec = [&](int a, int b, int c) -> bool {
+    if (!pec || a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) return false;
+    return pec[a + (long long)nx * (b + (long long)ny * c)] != 0;
+  };
+  long long cp = i + (long long)nxp * (j + (long long)ny * k);
+  double eps[3], kap[3];
+  uint8_t m = 0;
+  // x-edge: cells (i, j-1..j, k-1..k)
+  {
+    double se = 0, sk = 0;
+    bool p = false;
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int dk = -1; dk <= 0; ++dk) {
+        double a = 0.25 * width(dy, ny, j + dj) * width(dz, nz, k + dk);
+        se += E.at(i, j + dj, k + dk) * a;
+        sk += S.at(i, j + dj, k + dk) * a;
+        p = p || is_pec(i, j + dj, k + dk);
+      }
+    eps[0] = FIT_EPS0 * se / dx[i];
+    kap[0] = sk / dx[i];
+    if (j == 0 || k == 0 || p) m |= 1;
+  }
+  // y-edge: cells (i-1..i, j, k-1..k)
+  {
+    double se = 0, sk = 0;
+    bool p = false;
+    for (int di = -1; di <= 0; ++di)
+      for (int dk = -1; dk <= 0; ++dk) {
+        double a = 0.25 * width(dx, nx, i + di) * width(dz, nz, k + dk);
+        se += E.at(i + di, j, k + dk) * a;
+        sk += S.at(i + di, j, k + dk) * a;
+        p = p || is_pec(i + di, j, k + dk);
+      }
+    eps[1] = FIT_EPS0 * se / dy[j];
+    kap[1] = sk / dy[j];
+    if (i == 0 || k == 0 || p) m |= 2;
+  }
+  // z-edge: cells (i-1..i, j-1..j, k)
+  {
+    double se = 0, sk = 0;
+    bool p = false;
+    for (int di = -1; di <= 0; ++di)
+      for (int dj = -1; dj <= 0; ++dj) {
+        double a = 0.25 * width(dx, nx, i + di) * width(dy, ny, j + dj);
+        se += E.at(i + di, j + dj, k) * a;
+        sk += S.at(i + di, j + dj, k) * a;
+        p = p || is_pec(i + di, j + dj, k);
+      }
+    eps[2] = FIT_EPS0 * se / dz[k];
+    kap[2] = sk / dz[k];
+    if (i == 0 || j == 0 || p) m |= 4;
+  }
+  double nux = (0.5 * width(dx, nx, i - 1) * M.at(i - 1, j, k) + 0.5 * dx[i] * M.at(i, j, k)) / (FIT_MU0 * dy[j] * dz[k]);
+  double nuy = (0.5 * width(dy, ny, j - 1) * M.at(i, j - 1, k) + 0.5 * dy[j] * M.at(i, j, k)) / (FIT_MU0 * dx[i] * dz[k]);
+  double nuz = (0.5 * width(dz, nz, k - 1) * M.at(i, j, k - 1) + 0.5 * dz[k] * M.at(i, j, k)) / (FIT_MU0 * dx[i] * dy[j]);
+  nu64[3 * cp + 0] = nux;
+  nu64[3 * cp + 1] = nuy;
+  nu64[3 * cp + 2] = nuz;
+  for (int w = 0; w < 3; ++w) {
+    ek64[6 * cp + w] = eps[w];
+    ek64[6 * cp + 3 + w] = kap[w];
+  }
+  mask[cp] = m;
+}
+
+// max over facets of M_nu (positive doubles order like their bit patterns)
+__global__ void max_nu_kernel(const double* __restrict__ nu, long long n, unsigned long long* out) {
+  unsigned long long best = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = nu[t];
+    if (v > 0.0) best = max(best, (unsigned long long)__double_as_longlong(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+__global__ void to_c64_kernel(const double* __restrict__ nu64, const double* __restrict__ ek64, long long ncellp,
+                              double scale, float* __restrict__ nu32, float* __restrict__ ek32) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncellp; t += (long long)gridDim.x * blockDim.x) {
+    for (int w = 0; w < 3; ++w) nu32[3 * t + w] = (float)(scale * nu64[3 * t + w]);
+    for (int w = 0; w < 6; ++w) ek32[6 * t + w] = (float)(scale * ek64[6 * t + w]);
+  }
+}
+
+static fit_status finish_coefficients(fit_grid* g) {
+  unsigned long long* dmax = nullptr;
+  FIT_CHECK_CUDA(cudaMalloc(&dmax, sizeof(unsigned long long)));
+  cudaMemset(dmax, 0, sizeof(unsigned long long));
+  max_nu_kernel<<<1024, 256>>>(g->nu64, 3 * g->ncellp, dmax);
+  unsigned long long bits = 0;
+  cudaError_t e = cudaMemcpy(&bits, dmax, sizeof(bits), cudaMemcpyDeviceToHost);
+  cudaFree(dmax);
+  FIT_CHECK_CUDA(e);
+  double mx;
+  memcpy(&mx, &bits, sizeof(mx));
+  if (!(mx > 0.0) || !isfinite(mx)) {
+    fit_set_error("material matrices have no positive finite M_nu entry");
+    return FIT_EINVAL;
+  }
+  g->coef_scale = 1.0 / mx;
+  to_c64_kernel<<<1024, 256>>>(g->nu64, g->ek64, g->ncellp, g->coef_scale, g->nu32, g->ek32);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  FIT_CHECK_CUDA(cudaDeviceSynchronize());
+  g->has_materials = true;
+  return FIT_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* fit_status_str(fit_status s) {
+  switch (s) {
+    case FIT_OK: return "FIT_OK";
+    case FIT_NOT_CONVERGED: return "FIT_NOT_CONVERGED";
+    case FIT_BREAKDOWN: return "FIT_BREAKDOWN";
+    case FIT_EINVAL: return "FIT_EINVAL";
+    case FIT_ENOMEM: return "FIT_ENOMEM";
+    case FIT_ECUDA: return "FIT_ECUDA";
+    case FIT_ETIMEOUT: return "FIT_ETIMEOUT";
+    case FIT_EBUDGET: return "FIT_EBUDGET";
+    case FIT_ENAN: return "FIT_ENAN";
+  }
+  return "FIT_UNKNOWN";
+}
+
+const char* fit_last_error(void) { return fit_get_error(); }
+
+void fit_grid_destroy(fit_grid* g) {
+  if (!g) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(g->device);
+  void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  cudaSetDevice(cur);
+  delete g;
+}
+
+fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const double* dy, const double* dz,
+                           unsigned bc_flags, fit_grid** out) {
+  FIT_REQUIRE(out != nullptr, "fit_grid_create: out is NULL");
+  *out = nullptr;
+  FIT_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1, "fit_grid_create: nx, ny, nz must be >= 1");
+  FIT_REQUIRE((long long)nx * ny * nz <= (1LL << 33), "fit_grid_create: grid too large");
+  FIT_REQUIRE(dx && dy && dz, "fit_grid_create: null cell-width array");
+  FIT_REQUIRE(bc_flags == FIT_BC_PEC_ALL, "fit_grid_create: only PEC walls (FIT_BC_PEC_ALL) are supported");
+  for (int i = 0; i < nx; ++i) FIT_REQUIRE(dx[i] > 0 && isfinite(dx[i]), "fit_grid_create: dx must be positive");
+  for (int i = 0; i < ny; ++i) FIT_REQUIRE(dy[i] > 0 && isfinite(dy[i]), "fit_grid_create: dy must be positive");
+  for (int i = 0; i < nz; ++i) FIT_REQUIRE(dz[i] > 0 && isfinite(dz[i]), "fit_grid_create: dz must be positive");
+  fit_grid* g = new fit_grid();
+  FIT_CHECK_CUDA(cudaGetDevice(&g->device));
+  g->nx = nx;
+  g->ny = ny;
+  g->nz = nz;
+  g->nxp = (nx + FIT_PITCH_ALIGN - 1) / FIT_PITCH_ALIGN * FIT_PITCH_ALIGN;
+  g->ncell = (long long)nx * ny * nz;
+  g->ncellp = (long long)g->nxp * ny * nz;
+  g->ne = 3 * g->ncell;
+  fit_status st = FIT_OK;
+  size_t np = (size_t)g->ncellp;
+  if ((st = fit_dev_alloc(g, (void**)&g->dx, nx * sizeof(double))) ||
+      (st = fit_dev_alloc(g, (void**)&g->dy, ny * sizeof(double))) ||
+      (st = fit_dev_alloc(g, (void**)&g->dz, nz * sizeof(double))) ||
+      (st = fit_dev_alloc(g, (void**)&g->nu64, np * 3 * sizeof(double))) ||
+      (st = fit_dev_alloc(g, (void**)&g->ek64, np * 6 * sizeof(double))) ||
+      (st = fit_dev_alloc(g, (void**)&g->nu32, np * 3 * sizeof(float))) ||
+      (st = fit_dev_alloc(g, (void**)&g->ek32, np * 6 * sizeof(float))) ||
+      (st = fit_dev_alloc(g, (void**)&g->mask, np))) {
+    fit_grid_destroy(g);
+    return st;
+  }
+  cudaMemcpy(g->dx, dx, nx * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(g->dy, dy, ny * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(g->dz, dz, nz * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemset(g->nu64, 0, np * 3 * sizeof(double));
+  cudaMemset(g->ek64, 0, np * 6 * sizeof(double));
+  cudaMemset(g->nu32, 0, np * 3 * sizeof(float));
+  cudaMemset(g->ek32, 0, np * 6 * sizeof(float));
+  cudaMemset(g->mask, 0, np);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    fit_set_error(std::string("fit_grid_create: ") + cudaGetErrorString(e));
+    fit_grid_destroy(g);
+    return FIT_ECUDA;
+  }
+  *out = g;
+  return FIT_OK;
+}
+
+fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma, const float* inv_mu_r,
+                             const unsigned char* pec_cell) {
+  FIT_REQUIRE(g && eps_r && sigma && inv_mu_r, "fit_set_materials: null argument");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  size_t n = (size_t)g->ncell;
+  float *d_eps = nullptr, *d_sig = nullptr, *d_imu = nullptr;
+  uint8_t* d_pec = nullptr;
+  FIT_CHECK_CUDA(cudaMalloc(&d_eps, n * sizeof(float)));
+  FIT_CHECK_CUDA(cudaMalloc(&d_sig, n * sizeof(float)));
+  FIT_CHECK_CUDA(cudaMalloc(&d_imu, n * sizeof(float)));
+  if (pec_cell) FIT_CHECK_CUDA(cudaMalloc(&d_pec, n));
+  cudaMemcpy(d_eps, eps_r, n * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_sig, sigma, n * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_imu, inv_mu_r, n * sizeof(float), cudaMemcpyHostToDevice);
+  if (pec_cell) cudaMemcpy(d_pec, pec_cell, n, cudaMemcpyHostToDevice);
+  int threads = 256;
+  long long blocks = ((long long)n + threads - 1) / threads;
+  assemble_kernel<<<(unsigned)blocks, threads>>>(g->dx, g->dy, g->dz, d_eps, d_sig, d_imu, d_pec, g->nx, g->ny,
+                                                 g->nz, g->nxp, g->nu64, g->ek64, g->mask);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_eps);
+  cudaFree(d_sig);
+  cudaFree(d_imu);
+  if (d_pec) cudaFree(d_pec);
+  if (e != cudaSuccess) {
+    fit_set_error(std::string("fit_set_materials: ") + cudaGetErrorString(e));
+    return FIT_ECUDA;
+  }
+  return finish_coefficients(g);
+}
+
+fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const double* m_kappa, const double* m_nu,
+                                     const unsigned char* edge_mask) {
+  FIT_REQUIRE(g && m_eps && m_kappa && m_nu, "fit_set_material_matrices: null argument");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  size_t np = (size_t)g->ncellp;
+  std::vector<double> nu(np * 3, 0.0), ek(np * 6, 0.0);
+  std::vector<uint8_t> mk(np, 0);
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        size_t c = i + (size_t)g->nx * (j + (size_t)g->ny * k);
+        size_t cp = i + (size_t)g->nxp * (j + (size_t)g->ny * k);
+        uint8_t m = 0;
+        for (int w = 0; w < 3; ++w) {
+          nu[3 * cp + w] = m_nu[3 * c + w];
+          ek[6 * cp + w] = m_eps[3 * c + w];
+          ek[6 * cp + 3 + w] = m_kappa[3 * c + w];
+          if (edge_mask && edge_mask[3 * c + w]) m |= (uint8_t)(1u << w);
+        }
+        mk[cp] = m;
+      }
+  FIT_CHECK_CUDA(cudaMemcpy(g->nu64, nu.data(), np * 3 * sizeof(double), cudaMemcpyHostToDevice));
+  FIT_CHECK_CUDA(cudaMemcpy(g->ek64, ek.data(), np * 6 * sizeof(double), cudaMemcpyHostToDevice));
+  FIT_CHECK_CUDA(cudaMemcpy(g->mask, mk.data(), np, cudaMemcpyHostToDevice));
+  return finish_coefficients(g);
+}
+
+fit_status fit_set_hbm_budget(fit_grid* g, size_t bytes) {
+  FIT_REQUIRE(g, "fit_set_hbm_budget: null grid");
+  g->budget = bytes;
+  return FIT_OK;
+}
+
+fit_status fit_grid_info(const fit_grid* g, long long* out6) {
+  FIT_REQUIRE(g && out6, "fit_grid_info: null argument");
+  out6[0] = g->nx;
+  out6[1] = g->ny;
+  out6[2] = g->nz;
+  out6[3] = g->ne;
+  out6[4] = (long long)g->bytes_held;
+  out6[5] = (long long)g->budget;
+  return FIT_OK;
+}
+
+fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x, void* y, fit_prec prec,
+                     void* stream) {
+  FIT_REQUIRE(g && omega && x && y, "fit_apply: null argument");
+  FIT_REQUIRE(nbatch >= 1, "fit_apply: nbatch must be >= 1");
+  FIT_REQUIRE(prec == FIT_C64 || prec == FIT_C128, "fit_apply: unknown precision");
+  FIT_REQUIRE(g->has_materials, "fit_apply: materials not set");
+  for (int b = 0; b < nbatch; ++b) FIT_REQUIRE(isfinite(omega[b]), "fit_apply: omega must be finite");
+  size_t esz = prec == FIT_C64 ? sizeof(float2) : sizeof(double2);
+  size_t vbytes = (size_t)g->ne * esz * nbatch;
+  const char* xb = (const char*)x;
+  const char* yb = (const char*)y;
+  FIT_REQUIRE(xb + vbytes <= yb || yb + vbytes <= xb, "fit_apply: x and y overlap");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nbatch > g->omega_cap) {
+    if (g->omega_dev) fit_dev_free(g, g->omega_dev, g->omega_cap * sizeof(double));
+    g->omega_dev = nullptr;
+    g->omega_cap = 0;
+    int cap = std::max(nbatch, 64);
+    fit_status st = fit_dev_alloc(g, (void**)&g->omega_dev, cap * sizeof(double));
+    if (st != FIT_OK) return st;
+    g->omega_cap = cap;
+  }
+  FIT_CHECK_CUDA(cudaMemcpyAsync(g->omega_dev, omega, nbatch * sizeof(double), cudaMemcpyHostToDevice, s));
+  double out_scale = prec == FIT_C64 ? 1.0 / g->coef_scale : 1.0;
+  return fit_launch_apply(g, nbatch, g->omega_dev, x, y, prec, out_scale, s);
+}
+
+}  // extern "C"

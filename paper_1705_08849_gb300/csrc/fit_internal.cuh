@@ -1,0 +1,93 @@
+// Internal definitions shared by the translation units of the FIT library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fit.h"
+
+// Physical constants: mu0 = 4 pi 1e-7 H/m, c exact, eps0 = 1 / (mu0 c^2).
+#define FIT_MU0 (4.0e-7 * 3.141592653589793)
+#define FIT_C0 299792458.0
+#define FIT_EPS0 (1.0 / (FIT_MU0 * FIT_C0 * FIT_C0))
+
+// Row pitch (in cells) of the library's internal per-cell arrays is a multiple of this, so that
+// every row starts on a 16-byte boundary for the bulk tensor copies (TMA) of the fused kernel.
+#define FIT_PITCH_ALIGN 16
+
+struct fit_grid {
+  int nx = 0, ny = 0, nz = 0;
+  int nxp = 0;             // padded row pitch of internal arrays (cells)
+  long long ncell = 0;     // nx*ny*nz
+  long long ncellp = 0;    // nxp*ny*nz
+  long long ne = 0;        // 3*ncell
+  int device = 0;
+  double* dx = nullptr;    // device copies of the cell widths
+  double* dy = nullptr;
+  double* dz = nullptr;
+  // Material coefficients, padded layout: internal cell index cp = i + nxp*(j + ny*k).
+  double* nu64 = nullptr;  // [ncellp*3] M_nu facet values (SI)
+  double* ek64 = nullptr;  // [ncellp*6] M_eps (x,y,z) then M_kappa (x,y,z) edge values (SI)
+  float* nu32 = nullptr;   // [ncellp*3] coef_scale * M_nu
+  float* ek32 = nullptr;   // [ncellp*6] coef_scale * (M_eps, M_kappa)
+  uint8_t* mask = nullptr; // [ncellp] bit w set = w-edge of the cell is masked (PEC/wall)
+  double coef_scale = 1.0; // c64 coefficients are coef_scale * SI values (1 / max M_nu)
+  bool has_materials = false;
+  double* omega_dev = nullptr;  // per-batch angular frequencies for fit_apply
+  int omega_cap = 0;
+  size_t bytes_held = 0;
+  size_t budget = 0;       // 0 = unlimited
+  // autotuned launch shape of the fused c64 apply, keyed by batch (see fit_stencil.cu)
+  int tune_key_batch = -1;
+  int tune_variant = -1;
+};
+
+// Thread-local last-error message.
+void fit_set_error(const std::string& msg);
+const char* fit_get_error();
+
+#define FIT_CHECK_CUDA(call)                                                          \
+  do {                                                                                \
+    cudaError_t err__ = (call);                                                       \
+    if (err__ != cudaSuccess) {                                                       \
+      fit_set_error(std::string(#call) + ": " + cudaGetErrorString(err__));           \
+      return FIT_ECUDA;                                                               \
+    }                                                                                 \
+  } while (0)
+
+#define FIT_REQUIRE(cond, msg)      \
+  do {                              \
+    if (!(cond)) {                  \
+      fit_set_error(msg);           \
+      return FIT_EINVAL;            \
+    }                               \
+  } while (0)
+
+// Device allocation accounted against the handle's budget.
+fit_status fit_dev_alloc(fit_grid* g, void** p, size_t bytes);
+void fit_dev_free(fit_grid* g, void* p, size_t bytes);
+
+// Launch the operator apply: y_b = out_scale * A(omega_b) x_b.  omega_dev is a device array of
+// nbatch angular frequencies.  x/y are float2 (prec = FIT_C64) or double2 (FIT_C128).
+fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                            fit_prec prec, double out_scale, cudaStream_t stream);
+
+// ------------------------------------------------------------------------------------------------
+// complex helpers
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+
+__host__ __device__ inline float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ inline double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+template <typename V> __host__ __device__ inline V czero();
+template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }

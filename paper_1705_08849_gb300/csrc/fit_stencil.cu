@@ -1,0 +1,138 @@
+// Matrix-free FIT operator apply (Sec. III, Eq. e2t fused into one pass):
+//     y = out_scale * [ C^T M_nu C x - w^2 M_eps x + j w M_kappa x ]   on unmasked edges,
+//     y = x                                                            on masked edges,
+// where C^T M_nu C acts on the masked-out (zeroed) copy of x.  The curl of Eq. CP per facet:
+//     b_x(i,j,k) = e_y(i,j,k) - e_y(i,j,k+1) + e_z(i,j+1,k) - e_z(i,j,k)
+//     b_y(i,j,k) = e_z(i,j,k) - e_z(i+1,j,k) + e_x(i,j,k+1) - e_x(i,j,k)
+//     b_z(i,j,k) = e_x(i,j,k) - e_x(i,j+1,k) + e_y(i+1,j,k) - e_y(i,j,k)
+// h = M_nu b, and the dual curl C^T h per edge:
+//     (C^T h)_x = h_y(i,j,k-1) - h_y(i,j,k) + h_z(i,j,k) - h_z(i,j-1,k)
+//     (C^T h)_y = h_z(i-1,j,k) - h_z(i,j,k) + h_x(i,j,k) - h_x(i,j,k-1)
+//     (C^T h)_z = h_x(i,j-1,k) - h_x(i,j,k) + h_y(i,j,k) - h_y(i-1,j,k)
+// Values beyond the grid are zero (truncated forward differences, PEC high walls).
+//
+// This file holds the generic kernel: one thread per cell, operands read straight from global
+// memory (through L1), any grid size and batch.  It is the reference launch for the fused
+// shared-memory kernels in fit_fused.cu and the fallback for shapes they do not take.
+#include "fit_internal.cuh"
+
+template <typename T>
+struct ApplyArgs {
+  using V = typename cplx<T>::t;
+  const V* __restrict__ x;
+  V* __restrict__ y;
+  const T* __restrict__ nu;  // [ncellp*3]
+  const T* __restrict__ ek;  // [ncellp*6]
+  const uint8_t* __restrict__ mask;
+  const double* __restrict__ omega;
+  int nx, ny, nz, nxp;
+  long long ne;
+  int nbatch;
+  T out_scale;
+};
+
+template <typename T>
+struct GenericView {
+  using V = typename cplx<T>::t;
+  const ApplyArgs<T>& a;
+  const V* x;
+  __device__ bool inside(int i, int j, int k) const {
+    return i >= 0 && j >= 0 && k >= 0 && i < a.nx && j < a.ny && k < a.nz;
+  }
+  // masked-out voltage: zero beyond the grid and on masked edges
+  __device__ V e(int i, int j, int k, int w) const {
+    if (!inside(i, j, k)) return czero<V>();
+    long long cp = i + (long long)a.nxp * (j + (long long)a.ny * k);
+    if ((a.mask[cp] >> w) & 1) return czero<V>();
+    return x[3 * (i + (long long)a.nx * (j + (long long)a.ny * k)) + w];
+  }
+  __device__ T nu(int i, int j, int k, int w) const {
+    if (!inside(i, j, k)) return T(0);
+    return a.nu[3 * (i + (long long)a.nxp * (j + (long long)a.ny * k)) + w];
+  }
+  // facet fluxes times M_nu, per component
+  __device__ V hx(int i, int j, int k) const {
+    return nu(i, j, k, 0) * (e(i, j, k, 1) - e(i, j, k + 1, 1) + e(i, j + 1, k, 2) - e(i, j, k, 2));
+  }
+  __device__ V hy(int i, int j, int k) const {
+    return nu(i, j, k, 1) * (e(i, j, k, 2) - e(i + 1, j, k, 2) + e(i, j, k + 1, 0) - e(i, j, k, 0));
+  }
+  __device__ V hz(int i, int j, int k) const {
+    return nu(i, j, k, 2) * (e(i, j, k, 0) - e(i, j + 1, k, 0) + e(i + 1, j, k, 1) - e(i, j, k, 1));
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a) {
+  using V = typename cplx<T>::t;
+  int i = blockIdx.x * 32 + threadIdx.x;
+  int j = blockIdx.y * 8 + threadIdx.y;
+  for (long long zb = blockIdx.z; zb < (long long)a.nz * a.nbatch; zb += gridDim.z) {
+    int k = (int)(zb % a.nz);
+    int b = (int)(zb / a.nz);
+    if (i >= a.nx || j >= a.ny) return;
+    const V* x = a.x + (long long)b * a.ne;
+    V* y = a.y + (long long)b * a.ne;
+    GenericView<T> g{a, x};
+    V hx = g.hx(i, j, k), hy = g.hy(i, j, k), hz = g.hz(i, j, k);
+    V cx = g.hy(i, j, k - 1) - hy + hz - g.hz(i, j - 1, k);
+    V cy = g.hz(i - 1, j, k) - hz + hx - g.hx(i, j, k - 1);
+    V cz = g.hx(i, j - 1, k) - hx + hy - g.hy(i - 1, j, k);
+    long long c = i + (long long)a.nx * (j + (long long)a.ny * k);
+    long long cp = i + (long long)a.nxp * (j + (long long)a.ny * k);
+    uint8_t m = a.mask[cp];
+    T w = (T)a.omega[b];
+    T w2 = w * w;
+    V curl[3] = {cx, cy, cz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      V xv = x[3 * c + q];
+      V out;
+      if ((m >> q) & 1) {
+        out = xv;
+      } else {
+        T ar = -w2 * a.ek[6 * cp + q];  // -w^2 M_eps
+        T ai = w * a.ek[6 * cp + 3 + q];  // w M_kappa
+        out.x = a.out_scale * (curl[q].x + ar * xv.x - ai * xv.y);
+        out.y = a.out_scale * (curl[q].y + ar * xv.y + ai * xv.x);
+      }
+      y[3 * c + q] = out;
+    }
+  }
+}
+
+template <typename T>
+static fit_status launch_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                                 const T* nu, const T* ek, double out_scale, cudaStream_t s) {
+  ApplyArgs<T> a;
+  a.x = (const typename cplx<T>::t*)x;
+  a.y = (typename cplx<T>::t*)y;
+  a.nu = nu;
+  a.ek = ek;
+  a.mask = g->mask;
+  a.omega = omega_dev;
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nz = g->nz;
+  a.nxp = g->nxp;
+  a.ne = g->ne;
+  a.nbatch = nbatch;
+  a.out_scale = (T)out_scale;
+  dim3 block(32, 8, 1);
+  long long gz = (long long)g->nz * nbatch;
+  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (unsigned)(gz < 65535 ? gz : 65535));
+  apply_generic_kernel<T><<<grid, block, 0, s>>>(a);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_launch_apply_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                                    fit_prec prec, double out_scale, cudaStream_t s) {
+  if (prec == FIT_C64) return launch_generic<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, out_scale, s);
+  return launch_generic<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, out_scale, s);
+}
+
+fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                            fit_prec prec, double out_scale, cudaStream_t s) {
+  return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s);
+}

@@ -1,0 +1,232 @@
+"""Thin Python binding of the C ABI in include/fit.h (ctypes; argument marshalling only).
+
+Every numerical step runs in the CUDA library ``libfitgb300.so``; this module only checks
+argument shapes/dtypes, passes pointers and raises on error statuses.  Vectors are torch CUDA
+tensors (complex64 for FIT_C64, complex128 for FIT_C128) in the cell-by-cell ordering of the
+paper's Eq. e12Nxyz; material inputs are numpy arrays.  If the library is missing this module
+raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN = 0, 1, 2
+FIT_EINVAL, FIT_ENOMEM, FIT_ECUDA, FIT_ETIMEOUT, FIT_EBUDGET, FIT_ENAN = -1, -2, -3, -4, -5, -6
+FIT_C64, FIT_C128 = 0, 1
+FIT_BC_PEC_ALL = 0x3F
+FIT_BICGSTAB, FIT_FGMRES = 0, 1
+FIT_SOLVE_C128, FIT_SOLVE_MIXED = 0, 1
+FIT_PC_NONE, FIT_PC_JACOBI, FIT_PC_UNET = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfitgb300.so")
+_lib = None
+
+
+class FitError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_str(status)}: {msg}")
+        self.status = status
+
+
+class fit_solve_opts(ct.Structure):
+    _fields_ = [("method", ct.c_int), ("restart", ct.c_int), ("precision", ct.c_int), ("max_iter", ct.c_int),
+                ("max_outer", ct.c_int), ("inner_tol", ct.c_double), ("batch", ct.c_int),
+                ("use_graph", ct.c_int), ("precond", ct.c_int), ("stream", ct.c_void_p)]
+
+
+class fit_solve_report(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("iterations", ct.c_int), ("outer", ct.c_int), ("relres", ct.c_double),
+                ("seconds", ct.c_double)]
+
+
+def lib():
+    """Load libfitgb300.so (built by ``paper_1705_08849_gb300.build.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1705_08849_gb300.build.build() first")
+        L = ct.CDLL(LIB_PATH)
+        vp, i, d, u = ct.c_void_p, ct.c_int, ct.c_double, ct.c_uint
+        pd = ct.POINTER(ct.c_double)
+        pf = ct.POINTER(ct.c_float)
+        pu8 = ct.POINTER(ct.c_ubyte)
+        L.fit_grid_create.argtypes = [i, i, i, pd, pd, pd, u, ct.POINTER(vp)]
+        L.fit_set_materials.argtypes = [vp, pf, pf, pf, pu8]
+        L.fit_set_material_matrices.argtypes = [vp, pd, pd, pd, pu8]
+        L.fit_apply.argtypes = [vp, i, pd, vp, vp, i, vp]
+        L.fit_solve.argtypes = [vp, i, pd, vp, vp, d, ct.POINTER(fit_solve_opts), ct.POINTER(fit_solve_report)]
+        L.fit_solve_opts_default.argtypes = [ct.POINTER(fit_solve_opts)]
+        L.fit_solve_opts_default.restype = None
+        L.fit_set_hbm_budget.argtypes = [vp, ct.c_size_t]
+        L.fit_grid_info.argtypes = [vp, ct.POINTER(ct.c_longlong)]
+        L.fit_grid_destroy.argtypes = [vp]
+        L.fit_grid_destroy.restype = None
+        L.fit_status_str.argtypes = [i]
+        L.fit_status_str.restype = ct.c_char_p
+        L.fit_last_error.argtypes = []
+        L.fit_last_error.restype = ct.c_char_p
+        for name in ("fit_grid_create", "fit_set_materials", "fit_set_material_matrices", "fit_apply", "fit_solve",
+                     "fit_set_hbm_budget", "fit_grid_info"):
+            getattr(L, name).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def status_str(s):
+    try:
+        return lib().fit_status_str(int(s)).decode()
+    except Exception:
+        return str(s)
+
+
+def _check(st, what):
+    if st < 0:
+        raise FitError(st, f"{what}: {lib().fit_last_error().decode()}")
+    return st
+
+
+def _dptr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ct.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ct.c_void_p(stream)
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def fit_grid_create(nx, ny, nz, dx, dy, dz, bc_flags=FIT_BC_PEC_ALL):
+    """Create a grid handle on the current CUDA device; returns an opaque ctypes pointer."""
+    h = ct.c_void_p()
+    dx, pdx = _dptr(dx, np.float64)
+    dy, pdy = _dptr(dy, np.float64)
+    dz, pdz = _dptr(dz, np.float64)
+    if len(dx) != nx or len(dy) != ny or len(dz) != nz:
+        raise ValueError("cell-width arrays must have nx, ny, nz entries")
+    _check(lib().fit_grid_create(nx, ny, nz, pdx, pdy, pdz, bc_flags, ct.byref(h)), "fit_grid_create")
+    return h
+
+
+def fit_set_materials(g, eps_r, sigma, inv_mu_r, pec=None):
+    e, pe = _dptr(np.asarray(eps_r).ravel(), np.float32)
+    s, ps = _dptr(np.asarray(sigma).ravel(), np.float32)
+    m, pm = _dptr(np.asarray(inv_mu_r).ravel(), np.float32)
+    if pec is not None:
+        p, pp = _dptr(np.asarray(pec).ravel(), np.uint8)
+    else:
+        pp = None
+    _check(lib().fit_set_materials(g, pe, ps, pm, pp), "fit_set_materials")
+
+
+def fit_set_material_matrices(g, m_eps, m_kappa, m_nu, edge_mask=None):
+    a, pa = _dptr(m_eps, np.float64)
+    b, pb = _dptr(m_kappa, np.float64)
+    c, pc = _dptr(m_nu, np.float64)
+    if edge_mask is not None:
+        d, pdm = _dptr(edge_mask, np.uint8)
+    else:
+        pdm = None
+    _check(lib().fit_set_material_matrices(g, pa, pb, pc, pdm), "fit_set_material_matrices")
+
+
+def grid_info(g):
+    out = (ct.c_longlong * 6)()
+    _check(lib().fit_grid_info(g, out), "fit_grid_info")
+    return dict(nx=out[0], ny=out[1], nz=out[2], ne=out[3], bytes_held=out[4], budget=out[5])
+
+
+def _check_vec(t, ne, nbatch, prec, name):
+    import torch
+    want = torch.complex64 if prec == FIT_C64 else torch.complex128
+    if not (t.is_cuda and t.dtype == want and t.is_contiguous() and t.numel() == ne * nbatch):
+        raise ValueError(f"{name} must be a contiguous CUDA {want} tensor of {nbatch} x {ne} values")
+
+
+def fit_apply(g, omega, x, y, prec=FIT_C64, stream=None):
+    """y_b = A(omega_b) x_b for the batch of len(omega) vectors (torch CUDA tensors)."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    ne = grid_info(g)["ne"]
+    _check_vec(x, ne, len(om), prec, "x")
+    _check_vec(y, ne, len(om), prec, "y")
+    _check(lib().fit_apply(g, len(om), pom, ct.c_void_p(x.data_ptr()), ct.c_void_p(y.data_ptr()), prec,
+                           _stream_ptr(stream)), "fit_apply")
+
+
+def fit_solve_opts_default():
+    o = fit_solve_opts()
+    lib().fit_solve_opts_default(ct.byref(o))
+    return o
+
+
+def fit_solve(g, omega, rhs, x, tol, opts=None, **kw):
+    """Solve A(omega_f) x_f = rhs_f (complex128 CUDA tensors); returns (status, list of report dicts).
+    Keyword arguments override fields of the options struct."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    nf = len(om)
+    ne = grid_info(g)["ne"]
+    _check_vec(rhs, ne, nf, FIT_C128, "rhs")
+    _check_vec(x, ne, nf, FIT_C128, "x")
+    o = opts if opts is not None else fit_solve_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    if o.stream is None:
+        o.stream = _stream_ptr(None).value
+    reps = (fit_solve_report * nf)()
+    st = _check(lib().fit_solve(g, nf, pom, ct.c_void_p(rhs.data_ptr()), ct.c_void_p(x.data_ptr()), float(tol),
+                                ct.byref(o), reps), "fit_solve")
+    return st, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres, seconds=r.seconds)
+                for r in reps]
+
+
+def fit_set_hbm_budget(g, nbytes):
+    _check(lib().fit_set_hbm_budget(g, int(nbytes)), "fit_set_hbm_budget")
+
+
+def fit_grid_destroy(g):
+    lib().fit_grid_destroy(g)
+
+
+class Grid:
+    """Owning wrapper: ``with Grid.from_case(case) as g: ...`` (case dicts as drawn by ``fitgen``)."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz):
+        self.h = fit_grid_create(nx, ny, nz, dx, dy, dz)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.ne = 3 * nx * ny * nz
+
+    @classmethod
+    def from_case(cls, case):
+        g = cls(case["nx"], case["ny"], case["nz"], case["dx"], case["dy"], case["dz"])
+        fit_set_materials(g.h, case["eps_r"], case["sigma"], case["inv_mu_r"], case.get("pec"))
+        return g
+
+    def apply(self, omega, x, y, prec=FIT_C64, stream=None):
+        fit_apply(self.h, omega, x, y, prec, stream)
+
+    def solve(self, omega, rhs, x, tol, **kw):
+        return fit_solve(self.h, omega, rhs, x, tol, **kw)
+
+    def close(self):
+        if self.h is not None:
+            fit_grid_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every entry point that include/*.h declares; host
+argument checks that need no GPU return FIT_EINVAL without touching the device."""
+import ctypes as ct
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(fit_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1705_08849_gb300 import build, fit
+    build.build()
+    return fit.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert {"fit_grid_create", "fit_set_materials", "fit_apply", "fit_solve"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_status_strings(L):
+    from paper_1705_08849_gb300 import fit
+    for code, name in [(0, "FIT_OK"), (-1, "FIT_EINVAL"), (-5, "FIT_EBUDGET"), (2, "FIT_BREAKDOWN")]:
+        assert fit.status_str(code) == name
+
+
+def test_host_argument_checks_without_gpu(L):
+    from paper_1705_08849_gb300 import fit
+    h = ct.c_void_p()
+    d = (ct.c_double * 4)(1e-3, 1e-3, 1e-3, 1e-3)
+    assert L.fit_grid_create(0, 4, 4, d, d, d, 0x3F, ct.byref(h)) == fit.FIT_EINVAL
+    assert L.fit_grid_create(4, 4, 4, d, d, d, 0x01, ct.byref(h)) == fit.FIT_EINVAL
+    bad = (ct.c_double * 4)(1e-3, -1e-3, 1e-3, 1e-3)
+    assert L.fit_grid_create(4, 4, 4, bad, d, d, 0x3F, ct.byref(h)) == fit.FIT_EINVAL
+    assert b"dx" in L.fit_last_error()
+    assert L.fit_apply(None, 1, None, None, None, 0, None) == fit.FIT_EINVAL
+    o = fit.fit_solve_opts_default()
+    assert o.restart == 30 and o.inner_tol == 1e-4 and o.precision == fit.FIT_SOLVE_MIXED
+
+
+def test_library_has_no_oracle_dependency():
+    """The product package never imports the oracle (the two share no code)."""
+    for f in glob.glob(os.path.join(ROOT, "paper_1705_08849_gb300", "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            src = open(f).read()
+            assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", src), f
