@@ -69,10 +69,27 @@ const char* fit_get_error();
 fit_status fit_dev_alloc(fit_grid* g, void** p, size_t bytes);
 void fit_dev_free(fit_grid* g, void* p, size_t bytes);
 
-// Launch the operator apply: y_b = out_scale * A(omega_b) x_b.  omega_dev is a device array of
-// nbatch angular frequencies.  x/y are float2 (prec = FIT_C64) or double2 (FIT_C128).
+// Fused epilogues of the operator apply (all per system b of the batch; sums are written as
+// per-block partials part[(b*nblk + block)*4 + q], reduced later in a fixed order):
+//   FIT_EPI_NONE    y = out_scale * A x
+//   FIT_EPI_DOT_U   y = A x;  q0,q1 = sum conj(u) * y           (BiCGStab <r^, v>)
+//   FIT_EPI_DOT_TS  y = A x;  q0,q1 = sum conj(y) * x, q2 = sum |y|^2   (<t, s>, <t, t>)
+//   FIT_EPI_RESID   y = u - A x (u = b);  q2 = sum |y|^2        (true residual and its norm)
+// Systems whose status[b] != 0 are skipped entirely (no write, no partial).
+enum { FIT_EPI_NONE = 0, FIT_EPI_DOT_U = 1, FIT_EPI_DOT_TS = 2, FIT_EPI_RESID = 3 };
+struct fit_epi {
+  int mode = FIT_EPI_NONE;
+  const void* u = nullptr;
+  double* part = nullptr;
+  const int* status = nullptr;
+};
+
+// Launch the operator apply: y_b = out_scale * A(omega_b) x_b (+ epilogue).  omega_dev is a
+// device array of nbatch angular frequencies.  x/y are float2 (FIT_C64) or double2 (FIT_C128).
 fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                            fit_prec prec, double out_scale, cudaStream_t stream);
+                            fit_prec prec, double out_scale, cudaStream_t stream, const fit_epi* epi = nullptr);
+// Number of partial-sum slots per system that the apply writes for an epilogue.
+long long fit_apply_partials(const fit_grid* g, fit_prec prec);
 
 // ------------------------------------------------------------------------------------------------
 // complex helpers
@@ -91,3 +108,37 @@ __host__ __device__ inline double2 operator*(double s, double2 a) { return make_
 template <typename V> __host__ __device__ inline V czero();
 template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+// ------------------------------------------------------------------------------------------------
+// Block sum of NQ per-thread values.  Each thread's value is in T (float for the complex64 path,
+// whose products are exact enough per cell, double for complex128); warps reduce with shuffles
+// in T, then thread 0 adds the warp sums in double in a fixed order (deterministic).  GB300 runs
+// FP64 at about 1/58 of the FP32 rate, so FP64 is kept to the per-warp level and above.
+// All threads of the block must call it; out[0..NQ-1] is written by thread 0.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int NQ>
+__device__ inline void fit_block_sum(T (&v)[NQ], double* out) {
+  __shared__ double red[32][NQ > 0 ? NQ : 1];
+  int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[warp][q] = (double)v[q];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nw = (nthreads + 31) >> 5;
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w][q];
+      out[q] = s;
+    }
+  }
+  __syncthreads();
+}

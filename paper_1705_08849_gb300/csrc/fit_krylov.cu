@@ -1,5 +1,1068 @@
-// Krylov solvers on the fused operator (Sec. IV: BiCGStab and the GMRES family).
+// Krylov solvers on the fused FIT operator (Sec. IV: the short-listed bcgs and gmres family).
+//
+// Structure of fit_solve for a batch of B systems A(w_b) x_b = b_b sharing one geometry:
+//
+//   outer loop (FP64 iterative refinement; the true residual judges convergence):
+//       r = b - A x            (complex128 apply with a fused residual epilogue, FP64 norm)
+//       stop if ||r|| <= tol ||b||
+//       r~ = r / ||r||         (to complex64 for FIT_SOLVE_MIXED, complex128 for FIT_SOLVE_C128)
+//       inner Krylov solve  A_in d = r~  to a relative tolerance (BiCGStab, or one FGMRES(m) cycle)
+//       x += s_in ||r|| d      (A_in = s_in A: the complex64 coefficients are scaled by s_in)
+//
+// With FIT_SOLVE_C128 the same loop is plain complex128 Krylov restarted from the true residual.
+// Every kernel is predicated on a per-system status word, so converged systems stop updating while
+// the rest of the batch continues.  Scalars (rho, alpha, omega, Hessenberg, Givens) live on the
+// device; with opts->use_graph the whole solve is one CUDA graph: a WHILE node for the outer loop
+// holding the inner loop (a nested WHILE node for BiCGStab, m unrolled steps for FGMRES), with
+// device-side conditions.  Every loop has a device-side iteration guard, so it always ends.
+//
+// Inner products: per-thread partial sums in the vector precision, warp shuffles, then FP64
+// from the warp level up, in a fixed order (deterministic run to run).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
 #include "fit_internal.cuh"
+
+namespace {
+
+enum { SYS_RUN = 0, SYS_CONV = 1, SYS_BREAK = 2, SYS_MAXIT = 3, SYS_NAN = 4 };
+
+struct Sys {
+  double bnorm2;       // ||b||^2
+  double rnorm2;       // ||b - A x||^2 of the current x
+  double tol2;         // (tol ||b||)^2
+  double rscale;       // ||r|| at the start of the current inner solve
+  double corr;         // s_in * rscale: x += corr * d
+  double inner_tol2;   // inner stop threshold on ||r_in||^2
+  double rin2;         // inner recurrence residual ||r_in||^2
+  double best2;        // smallest true residual seen (stagnation test)
+  double2 rho, alpha, omega, beta;
+  double inv_hn;       // FGMRES: 1 / h_{j+1,j}
+  int outer_status;    // SYS_*
+  int outer;           // refinement steps done
+  int iters;           // inner iterations summed over refinement steps
+  int inner_status;    // SYS_RUN while the inner solve of this system is active
+  int inner_it;        // iterations of the current inner solve
+  int stagn;           // consecutive refinement steps without residual decrease
+  int jlast;           // FGMRES: Arnoldi steps done in the current cycle
+  int max_inner;       // inner iteration cap of the current inner solve
+};
+
+struct Ctl {
+  int inner_guard;
+  int outer_guard;
+  int cond;
+  int pad;
+};
+
+struct P {
+  int B;
+  long long ne;
+  int nblk;          // blocks per system of the vector kernels
+  int pstride;       // doubles per partial slot of the vector kernels
+  int m;             // FGMRES restart length
+  int max_iter, max_outer;
+  double tol, inner_tol;
+  int mixed;         // inner precision is complex64
+  double s_in;       // A_in = s_in * A
+  double tiny;       // breakdown threshold for the inner precision
+};
+
+__device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ inline double2 cdiv(double2 a, double2 b) {
+  double d = cabs2(b);
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ inline bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+template <typename T> __device__ inline typename cplx<T>::t mkc(double re, double im);
+template <> __device__ inline float2 mkc<float>(double re, double im) { return make_float2((float)re, (float)im); }
+template <> __device__ inline double2 mkc<double>(double re, double im) { return make_double2(re, im); }
+
+// ------------------------------------------------------------------------------------------------
+// Fixed-order reduction of the per-block partials of one system, then a scalar operation.
+// ------------------------------------------------------------------------------------------------
+template <int NQ, class Op>
+__global__ void __launch_bounds__(256) fin_kernel(const double* __restrict__ part, long long nslots, int stride,
+                                                  Sys* sys, P p, Op op) {
+  const int b = blockIdx.x;
+  if (!op.active(sys[b])) return;
+  __shared__ double red[256][NQ];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  const double* pb = part + (long long)b * nslots * stride;
+  for (long long s = threadIdx.x; s < nslots; s += 256)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] += pb[s * stride + q];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) red[threadIdx.x][q] = acc[q];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) red[threadIdx.x][q] += red[threadIdx.x + h][q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double s[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] = red[0][q];
+    op.apply(sys[b], s, p, b);
+  }
+}
+
+// ---- outer-loop operations --------------------------------------------------------------------
+struct OpOuterInit {  // q2 = ||b||^2
+  __device__ bool active(const Sys&) const { return true; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    s.bnorm2 = q[2];
+    s.rnorm2 = q[2];
+    s.best2 = q[2];
+    s.tol2 = p.tol * p.tol * q[2];
+    s.rscale = sqrt(q[2]);
+    s.outer = 0;
+    s.iters = 0;
+    s.stagn = 0;
+    s.inner_status = SYS_CONV;
+    s.inner_it = 0;
+    if (!isfinite(q[2])) s.outer_status = SYS_NAN;
+    else if (q[2] == 0.0) s.outer_status = SYS_CONV;
+    else s.outer_status = SYS_RUN;
+  }
+};
+
+struct OpOuter {  // after r = b - A x: q2 = ||r||^2
+  __device__ bool active(const Sys& s) const { return s.outer_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    double r2 = q[2];
+    s.rnorm2 = r2;
+    s.rscale = sqrt(r2);
+    s.outer += 1;
+    s.iters += s.inner_it;
+    if (!isfinite(r2)) { s.outer_status = SYS_NAN; return; }
+    if (r2 <= s.tol2) { s.outer_status = SYS_CONV; return; }
+    if (r2 < 0.98 * s.best2) { s.best2 = r2; s.stagn = 0; }
+    else s.stagn += 1;
+    if (s.outer >= p.max_outer || s.iters >= p.max_iter || s.stagn >= 3) s.outer_status = SYS_MAXIT;
+  }
+};
+
+// inner start: q0 = ||r~||^2 (for BiCGStab rho = <r^, r> = ||r~||^2)
+struct OpInnerStart {
+  __device__ bool active(const Sys&) const { return true; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    if (s.outer_status != SYS_RUN) { s.inner_status = SYS_CONV; return; }
+    s.inner_status = SYS_RUN;
+    s.inner_it = 0;
+    s.jlast = 0;
+    s.rho = make_double2(q[0], 0.0);
+    s.alpha = make_double2(1.0, 0.0);
+    s.omega = make_double2(1.0, 0.0);
+    s.beta = make_double2(0.0, 0.0);
+    s.rin2 = q[0];
+    s.corr = p.s_in * s.rscale;
+    // relative target of this inner solve: no tighter than needed for the outer tolerance
+    double need = 0.5 * sqrt(s.tol2) / s.rscale;
+    double it = p.mixed ? fmax(p.inner_tol, need) : fmax(need, 1e-15);
+    s.inner_tol2 = it * it * q[0];
+    s.max_inner = max(1, p.max_iter - s.iters);
+  }
+};
+
+// ---- BiCGStab operations -----------------------------------------------------------------------
+struct OpAlpha {  // q0,q1 = <r^, v>
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    double2 sig = make_double2(q[0], q[1]);
+    if (!cfinite(sig)) { s.inner_status = SYS_NAN; return; }
+    if (sqrt(cabs2(sig)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
+    s.alpha = cdiv(s.rho, sig);
+  }
+};
+
+struct OpOmega {  // q0,q1 = <t, s>, q2 = <t, t>
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P&, int) const {
+    double tt = q[2];
+    if (!isfinite(tt)) { s.inner_status = SYS_NAN; return; }
+    s.omega = tt > 0.0 ? make_double2(q[0] / tt, q[1] / tt) : make_double2(0.0, 0.0);
+  }
+};
+
+struct OpRho {  // q0,q1 = <r^, r_new>, q2 = ||r_new||^2
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    double2 rn = make_double2(q[0], q[1]);
+    double rr = q[2];
+    s.inner_it += 1;
+    s.rin2 = rr;
+    if (!cfinite(rn) || !isfinite(rr)) { s.inner_status = SYS_NAN; return; }
+    if (rr <= s.inner_tol2) { s.inner_status = SYS_CONV; return; }
+    if (s.inner_it >= s.max_inner) { s.inner_status = SYS_MAXIT; return; }
+    if (sqrt(cabs2(rn)) < p.tiny || sqrt(cabs2(s.omega)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
+    s.beta = cmul(cdiv(rn, s.rho), cdiv(s.alpha, s.omega));
+    s.rho = rn;
+  }
+};
+
+// ------------------------------------------------------------------------------------------------
+// Vector kernels.  Grid (nblk, B); thread t of block k of system b owns the elements
+// e = k*256 + t + n*nblk*256 (fixed assignment, so partial sums are reproducible).
+// ------------------------------------------------------------------------------------------------
+#define VEC_LOOP(p) for (long long e = blockIdx.x * 256LL + threadIdx.x; e < (p).ne; e += (long long)gridDim.x * 256)
+#define PSLOT(p, b) ((((long long)(b) * (p).nblk + blockIdx.x)) * (p).pstride)
+
+__global__ void __launch_bounds__(256) k_outer_init(const double2* __restrict__ rhs, double2* __restrict__ x,
+                                                    double2* __restrict__ r, double* part, P p) {
+  const int b = blockIdx.y;
+  const long long off = (long long)b * p.ne;
+  double acc[3] = {0, 0, 0};
+  VEC_LOOP(p) {
+    double2 v = rhs[off + e];
+    x[off + e] = make_double2(0.0, 0.0);
+    r[off + e] = v;
+    acc[2] += v.x * v.x + v.y * v.y;
+  }
+  fit_block_sum<double, 3>(acc, part + PSLOT(p, b));
+}
+
+// r~ = r / ||r|| in the inner precision; BiCGStab: r^ = r~, p = v = d = 0; FGMRES: V0 = r~, d = 0
+template <typename T, bool BICG>
+__global__ void __launch_bounds__(256) k_inner_start(const double2* __restrict__ r128, const Sys* __restrict__ sys,
+                                                     typename cplx<T>::t* rin, typename cplx<T>::t* rhat,
+                                                     typename cplx<T>::t* pv, typename cplx<T>::t* v,
+                                                     typename cplx<T>::t* d, double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  if (sys[b].outer_status == SYS_RUN) {
+    const long long off = (long long)b * p.ne;
+    const double sc = 1.0 / sys[b].rscale;
+    VEC_LOOP(p) {
+      double2 r = r128[off + e];
+      V z = mkc<T>(r.x * sc, r.y * sc);
+      rin[off + e] = z;
+      d[off + e] = czero<V>();
+      if (BICG) {
+        rhat[off + e] = z;
+        pv[off + e] = czero<V>();
+        v[off + e] = czero<V>();
+      }
+      acc[0] += z.x * z.x + z.y * z.y;
+    }
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// BiCGStab: p = r + beta (p - omega v)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bicg_p(const typename cplx<T>::t* __restrict__ r, typename cplx<T>::t* pv,
+                                                const typename cplx<T>::t* __restrict__ v, const Sys* __restrict__ sys, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const double2 bd = sys[b].beta, od = sys[b].omega;
+  const T br = (T)bd.x, bi = (T)bd.y, orr = (T)od.x, oi = (T)od.y;
+  VEC_LOOP(p) {
+    V rr = r[off + e], pp = pv[off + e], vv = v[off + e];
+    V t;  // p - omega v
+    t.x = pp.x - (orr * vv.x - oi * vv.y);
+    t.y = pp.y - (orr * vv.y + oi * vv.x);
+    V o;
+    o.x = rr.x + br * t.x - bi * t.y;
+    o.y = rr.y + br * t.y + bi * t.x;
+    pv[off + e] = o;
+  }
+}
+
+// BiCGStab: s = r - alpha v (in place in r)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bicg_s(typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ v,
+                                                const Sys* __restrict__ sys, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const T ar = (T)sys[b].alpha.x, ai = (T)sys[b].alpha.y;
+  VEC_LOOP(p) {
+    V rr = r[off + e], vv = v[off + e];
+    rr.x -= ar * vv.x - ai * vv.y;
+    rr.y -= ar * vv.y + ai * vv.x;
+    r[off + e] = rr;
+  }
+}
+
+// BiCGStab: d += alpha p + omega s; r = s - omega t; q0,q1 = <r^, r>, q2 = ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_bicg_xr(typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ pv,
+                                                 typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ t,
+                                                 const typename cplx<T>::t* __restrict__ rhat, const Sys* __restrict__ sys,
+                                                 double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const T ar = (T)sys[b].alpha.x, ai = (T)sys[b].alpha.y, orr = (T)sys[b].omega.x, oi = (T)sys[b].omega.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    V s = r[off + e], pp = pv[off + e], tt = t[off + e], dd = d[off + e], rh = rhat[off + e];
+    dd.x += (ar * pp.x - ai * pp.y) + (orr * s.x - oi * s.y);
+    dd.y += (ar * pp.y + ai * pp.x) + (orr * s.y + oi * s.x);
+    V rn;
+    rn.x = s.x - (orr * tt.x - oi * tt.y);
+    rn.y = s.y - (orr * tt.y + oi * tt.x);
+    d[off + e] = dd;
+    r[off + e] = rn;
+    acc[0] += rh.x * rn.x + rh.y * rn.y;
+    acc[1] += rh.x * rn.y - rh.y * rn.x;
+    acc[2] += rn.x * rn.x + rn.y * rn.y;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// x128 += corr * d (only systems still in the outer loop)
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_x(double2* x, const typename cplx<T>::t* __restrict__ d,
+                                                  const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.y;
+  if (sys[b].outer_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const double c = sys[b].corr;
+  VEC_LOOP(p) {
+    auto dd = d[off + e];
+    double2 xx = x[off + e];
+    xx.x += c * (double)dd.x;
+    xx.y += c * (double)dd.y;
+    x[off + e] = xx;
+  }
+}
+
+// ---- FGMRES(m) vector kernels ---------------------------------------------------------------
+// Arnoldi step j works on the basis V[0..j] (vector i of system b at V + (i*B + b)*ne) and the
+// new vector w = V[j+1].  Partial slot layout: 2*(j+1) doubles (re, im of <V_i, w>) per block.
+template <typename T>
+__device__ inline void warp_accum(T re, T im, double* slot_re, double* slot_im) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    *slot_re += (double)re;
+    *slot_im += (double)im;
+  }
+}
+
+#define FG_MAXV 65  // m + 1 <= 65
+
+// mode 0: h_i = <V_i, w>                      (partials of 2(j+1) values)
+// mode 1: w -= sum_i h_i V_i, then h2_i = <V_i, w>
+// mode 2: w -= sum_i h2_i V_i, then q0 = ||w||^2
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_fg_ortho(const typename cplx<T>::t* __restrict__ Vb, int j,
+                                                  const double* __restrict__ hcoef, const Sys* __restrict__ sys,
+                                                  double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  __shared__ double red[8][2 * FG_MAXV];
+  const int warp = threadIdx.x >> 5;
+  const int nv = j + 1;
+  for (int q = threadIdx.x; q < 8 * 2 * FG_MAXV; q += 256) (&red[0][0])[q] = 0.0;
+  __syncthreads();
+  const long long vs = (long long)p.B * p.ne;  // stride between basis vectors
+  const long long off = (long long)b * p.ne;
+  V* w = (V*)(Vb + (long long)(j + 1) * vs + off);
+  // The element loop runs a whole-warp trip count so that shuffles see full warps.
+  const long long stride = (long long)gridDim.x * 256;
+  for (long long base = blockIdx.x * 256LL; base < p.ne; base += stride) {
+    const long long e = base + threadIdx.x;
+    const bool ok = e < p.ne;
+    V wv = ok ? w[e] : czero<V>();
+    if (MODE >= 1) {
+      const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
+      for (int i = 0; i < nv; ++i) {
+        V vi = ok ? Vb[(long long)i * vs + off + e] : czero<V>();
+        T hr = (T)hc[2 * i], hi = (T)hc[2 * i + 1];
+        wv.x -= hr * vi.x - hi * vi.y;
+        wv.y -= hr * vi.y + hi * vi.x;
+      }
+      if (ok) w[e] = wv;
+    }
+    if (MODE <= 1) {
+      for (int i = 0; i < nv; ++i) {
+        V vi = ok ? Vb[(long long)i * vs + off + e] : czero<V>();
+        warp_accum<T>(vi.x * wv.x + vi.y * wv.y, vi.x * wv.y - vi.y * wv.x, &red[warp][2 * i], &red[warp][2 * i + 1]);
+      }
+    } else {
+      warp_accum<T>(wv.x * wv.x + wv.y * wv.y, T(0), &red[warp][0], &red[warp][1]);
+    }
+  }
+  __syncthreads();
+  const int nq = MODE <= 1 ? 2 * nv : 2;
+  double* out = part + PSLOT(p, b);
+  for (int q = threadIdx.x; q < nq; q += 256) {
+    double s = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) s += red[w8][q];
+    out[q] = s;
+  }
+}
+
+// fixed-order sum of the 2(j+1) partials of each block into hout[b][0..2(j+1)-1]
+__global__ void __launch_bounds__(256) k_fg_fin_dots(const double* __restrict__ part, int nq, double* hout,
+                                                     const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.x;
+  if (sys[b].inner_status != SYS_RUN) return;
+  for (int q = threadIdx.x; q < nq; q += 256) {
+    double s = 0.0;
+    for (int k = 0; k < p.nblk; ++k) s += part[((long long)b * p.nblk + k) * p.pstride + q];
+    hout[(long long)b * 2 * FG_MAXV + q] = s;
+  }
+}
+
+// Hessenberg column j = h + h2, h_{j+1,j} = ||w||; Givens rotations; residual estimate |g_{j+1}|
+__global__ void k_fg_givens(const double* __restrict__ part, int j, const double* __restrict__ h1,
+                            const double* __restrict__ h2, double* H, double* G, double* CS, double* SN, Sys* sys, P p) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= p.B) return;
+  Sys& s = sys[b];
+  if (s.inner_status != SYS_RUN) return;
+  double nrm2 = 0.0;
+  for (int k = 0; k < p.nblk; ++k) nrm2 += part[((long long)b * p.nblk + k) * p.pstride];
+  const int m = p.m;
+  double2* Hc = (double2*)(H + (long long)b * 2 * (m + 1) * m) + (long long)j * (m + 1);  // column j
+  double2* g = (double2*)(G + (long long)b * 2 * (m + 1));
+  double2* cs = (double2*)(CS + (long long)b * 2 * m);
+  double2* sn = (double2*)(SN + (long long)b * 2 * m);
+  const double2* a1 = (const double2*)(h1 + (long long)b * 2 * FG_MAXV);
+  const double2* a2 = (const double2*)(h2 + (long long)b * 2 * FG_MAXV);
+  for (int i = 0; i <= j; ++i) Hc[i] = cadd(a1[i], a2[i]);
+  const double hn = sqrt(nrm2);
+  Hc[j + 1] = make_double2(hn, 0.0);
+  if (!isfinite(hn) || !cfinite(Hc[j])) { s.inner_status = SYS_NAN; return; }
+  for (int i = 0; i < j; ++i) {
+    double2 hi = Hc[i], hi1 = Hc[i + 1];
+    Hc[i] = cadd(cmul(cconj(cs[i]), hi), cmul(cconj(sn[i]), hi1));
+    Hc[i + 1] = csub(cmul(cs[i], hi1), cmul(sn[i], hi));
+  }
+  double2 a = Hc[j], c = Hc[j + 1];
+  double den = sqrt(cabs2(a) + cabs2(c));
+  if (den > 0.0) {
+    cs[j] = make_double2(a.x / den, a.y / den);
+    sn[j] = make_double2(c.x / den, c.y / den);
+  } else {
+    cs[j] = make_double2(1.0, 0.0);
+    sn[j] = make_double2(0.0, 0.0);
+  }
+  Hc[j] = make_double2(den, 0.0);
+  Hc[j + 1] = make_double2(0.0, 0.0);
+  double2 gj = g[j];
+  g[j + 1] = make_double2(-(sn[j].x * gj.x - sn[j].y * gj.y), -(sn[j].x * gj.y + sn[j].y * gj.x));
+  g[j] = cmul(cconj(cs[j]), gj);
+  s.jlast = j + 1;
+  s.inner_it += 1;
+  s.inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+  double res2 = cabs2(g[j + 1]);
+  s.rin2 = res2;
+  if (res2 <= s.inner_tol2) s.inner_status = SYS_CONV;
+  else if (hn == 0.0 || den == 0.0) s.inner_status = SYS_CONV;  // exact invariant subspace
+  else if (j + 1 >= m || s.inner_it >= s.max_inner) s.inner_status = SYS_MAXIT;
+}
+
+// v_{j+1} = w / h_{j+1,j}
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_scale(typename cplx<T>::t* Vb, int j, const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long vs = (long long)p.B * p.ne;
+  auto* w = Vb + (long long)(j + 1) * vs + (long long)b * p.ne;
+  const T sc = (T)sys[b].inv_hn;
+  VEC_LOOP(p) {
+    auto v = w[e];
+    v.x *= sc;
+    v.y *= sc;
+    w[e] = v;
+  }
+}
+
+// Jacobi right preconditioner z = v / diag(A_in(w)), diag = nusum - w^2 M_eps + j w M_kappa
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_jacobi(const typename cplx<T>::t* __restrict__ Vb,
+                                                   typename cplx<T>::t* Zb, int j, const T* __restrict__ nusum,
+                                                   const T* __restrict__ ek, const uint8_t* __restrict__ mask,
+                                                   const double* __restrict__ omega, int nx, int ny, int nxp,
+                                                   const Sys* __restrict__ sys, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long vs = (long long)p.B * p.ne;
+  const V* v = Vb + (long long)j * vs + (long long)b * p.ne;
+  V* z = Zb + (long long)j * vs + (long long)b * p.ne;
+  const double w = omega[b];
+  VEC_LOOP(p) {
+    long long c = e / 3;
+    int q = (int)(e - 3 * c);
+    long long i = c % nx, jj = (c / nx) % ny, k = c / ((long long)nx * ny);
+    long long cp = i + (long long)nxp * (jj + (long long)ny * k);
+    V vv = v[e];
+    if ((mask[cp] >> q) & 1) { z[e] = vv; continue; }
+    double dr = (double)nusum[e] - w * w * (double)ek[6 * cp + q];
+    double di = w * (double)ek[6 * cp + 3 + q];
+    double den = dr * dr + di * di;
+    V o;
+    o.x = (T)((vv.x * dr + vv.y * di) / den);
+    o.y = (T)((vv.y * dr - vv.x * di) / den);
+    z[e] = o;
+  }
+}
+
+// back substitution H y = g on the rotated (upper triangular) Hessenberg, then d = sum y_i Z_i
+__global__ void k_fg_solve(const double* __restrict__ H, const double* __restrict__ G, double* Y, const Sys* sys, P p) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= p.B) return;
+  const Sys& s = sys[b];
+  if (s.outer_status != SYS_RUN) return;
+  const int m = p.m, n = s.jlast;
+  const double2* Hb = (const double2*)(H + (long long)b * 2 * (m + 1) * m);
+  const double2* g = (const double2*)(G + (long long)b * 2 * (m + 1));
+  double2* y = (double2*)(Y + (long long)b * 2 * FG_MAXV);
+  for (int i = n - 1; i >= 0; --i) {
+    double2 acc = g[i];
+    for (int k = i + 1; k < n; ++k) acc = csub(acc, cmul(Hb[(long long)k * (m + 1) + i], y[k]));
+    double2 hii = Hb[(long long)i * (m + 1) + i];
+    y[i] = cabs2(hii) > 0.0 ? cdiv(acc, hii) : make_double2(0.0, 0.0);
+  }
+  for (int i = n; i < m; ++i) y[i] = make_double2(0.0, 0.0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_combine(const typename cplx<T>::t* __restrict__ Zb, typename cplx<T>::t* d,
+                                                    const double* __restrict__ Y, const Sys* __restrict__ sys, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].outer_status != SYS_RUN) return;
+  const int n = sys[b].jlast;
+  const long long vs = (long long)p.B * p.ne;
+  const long long off = (long long)b * p.ne;
+  const double* y = Y + (long long)b * 2 * FG_MAXV;
+  VEC_LOOP(p) {
+    V acc = czero<V>();
+    for (int i = 0; i < n; ++i) {
+      V zi = Zb[(long long)i * vs + off + e];
+      T yr = (T)y[2 * i], yi = (T)y[2 * i + 1];
+      acc.x += yr * zi.x - yi * zi.y;
+      acc.y += yr * zi.y + yi * zi.x;
+    }
+    d[off + e] = acc;
+  }
+}
+
+// FGMRES inner start: g = (1, 0, ...), rotations cleared
+__global__ void k_fg_reset(double* G, const Sys* sys, P p) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= p.B) return;
+  double2* g = (double2*)(G + (long long)b * 2 * (p.m + 1));
+  g[0] = make_double2(sqrt(sys[b].rin2), 0.0);
+  for (int i = 1; i <= p.m; ++i) g[i] = make_double2(0.0, 0.0);
+}
+
+// sum over facets containing each edge of M_nu (the C^T M_nu C diagonal; Eq. Precond construction)
+template <typename T>
+__global__ void k_nusum(const T* __restrict__ nu, int nx, int ny, int nz, int nxp, T* out) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= (long long)nx * ny * nz) return;
+  int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+  auto NU = [&](int a, int bb, int cc, int w) -> T {
+    if (a < 0 || bb < 0 || cc < 0) return T(0);
+    return nu[3 * (a + (long long)nxp * (bb + (long long)ny * cc)) + w];
+  };
+  out[3 * c + 0] = NU(i, j, k, 1) + NU(i, j, k - 1, 1) + NU(i, j, k, 2) + NU(i, j - 1, k, 2);
+  out[3 * c + 1] = NU(i, j, k, 0) + NU(i, j, k - 1, 0) + NU(i, j, k, 2) + NU(i - 1, j, k, 2);
+  out[3 * c + 2] = NU(i, j, k, 0) + NU(i, j - 1, k, 0) + NU(i, j, k, 1) + NU(i - 1, j, k, 1);
+}
+
+// ---- loop conditions -------------------------------------------------------------------------
+__global__ void k_cond(const Sys* __restrict__ sys, Ctl* ctl, P p, int which, int guard_max,
+                       cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
+    int st = which == 0 ? sys[b].inner_status : sys[b].outer_status;
+    if (st == SYS_RUN) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int* guard = which == 0 ? &ctl->inner_guard : &ctl->outer_guard;
+    *guard += 1;
+    int v = (any && *guard < guard_max) ? 1 : 0;
+    ctl->cond = v;
+    if (use_handle) cudaGraphSetConditional(h, v);
+  }
+}
+
+// Resets a loop guard and, inside a graph, re-arms the loop's WHILE handle: the default value of a
+// handle is applied once per graph launch, so a nested loop that is entered again (the inner loop
+// of every refinement step) must be set to 1 explicitly before its node is reached.
+__global__ void k_reset_guard(Ctl* ctl, int which, cudaGraphConditionalHandle h, int use_handle) {
+  if (which == 0) ctl->inner_guard = 0;
+  else ctl->outer_guard = 0;
+  if (use_handle) cudaGraphSetConditional(h, 1);
+}
+
+}  // namespace
+
+// ================================================================================================
+// Host driver
+// ================================================================================================
+namespace {
+
+struct Work {
+  fit_grid* g = nullptr;
+  int B = 0, m = 30, method = FIT_BICGSTAB, mixed = 1, pc = FIT_PC_NONE;
+  fit_prec inner = FIT_C64;
+  size_t esz = 8;         // bytes per complex inner element
+  P p{};
+  // device buffers
+  double2* r128 = nullptr;
+  double* omega = nullptr;
+  void *rin = nullptr, *rhat = nullptr, *pv = nullptr, *v = nullptr, *t = nullptr, *d = nullptr;
+  void* Vb = nullptr;     // FGMRES basis (m+1 vectors)
+  void* Zb = nullptr;     // FGMRES preconditioned vectors (m), or aliases Vb
+  void* nusum = nullptr;
+  double *part_apply = nullptr, *part_vec = nullptr;
+  long long napply = 0;
+  double *h1 = nullptr, *h2 = nullptr, *H = nullptr, *G = nullptr, *CS = nullptr, *SN = nullptr, *Y = nullptr;
+  Sys* sys = nullptr;
+  Ctl* ctl = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+  ~Work() {
+    for (auto& a : allocs) fit_dev_free(g, a.first, a.second);
+  }
+  fit_status alloc(void** ptr, size_t bytes) {
+    fit_status st = fit_dev_alloc(g, ptr, bytes);
+    if (st == FIT_OK && *ptr) allocs.push_back({*ptr, bytes});
+    return st;
+  }
+};
+
+size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, int pc) {
+  size_t ne = (size_t)g->ne;
+  size_t esz = mixed ? 8 : 16;
+  size_t vec = ne * B * esz;
+  size_t bytes = ne * B * 16;  // r128
+  if (method == FIT_BICGSTAB) bytes += 6 * vec;
+  else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
+  if (pc == FIT_PC_JACOBI) bytes += ne * esz / 2;
+  size_t napply = (size_t)std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
+  bytes += (size_t)B * napply * 4 * 8;
+  bytes += (size_t)B * 1216 * 2 * FG_MAXV * 8;
+  bytes += (size_t)B * (2 * 2 * FG_MAXV + 2 * (m + 1) * m * 2 + 2 * (m + 1) * 2 + 2 * 2 * m + 2 * FG_MAXV) * 8;
+  return bytes + (size_t)B * sizeof(Sys) + 4096;
+}
+
+fit_status setup(Work& w, int B) {
+  fit_grid* g = w.g;
+  w.B = B;
+  w.esz = w.mixed ? sizeof(float2) : sizeof(double2);
+  w.inner = w.mixed ? FIT_C64 : FIT_C128;
+  size_t ne = (size_t)g->ne;
+  size_t vec = ne * B * w.esz;
+  fit_status st;
+#define ALLOC(ptr, bytes) \
+  if ((st = w.alloc((void**)&(ptr), (bytes))) != FIT_OK) return st
+  ALLOC(w.r128, ne * B * sizeof(double2));
+  ALLOC(w.omega, B * sizeof(double));
+  if (w.method == FIT_BICGSTAB) {
+    ALLOC(w.rin, vec);
+    ALLOC(w.rhat, vec);
+    ALLOC(w.pv, vec);
+    ALLOC(w.v, vec);
+    ALLOC(w.t, vec);
+    ALLOC(w.d, vec);
+  } else {
+    ALLOC(w.Vb, (size_t)(w.m + 1) * vec);
+    if (w.pc != FIT_PC_NONE) {
+      ALLOC(w.Zb, (size_t)w.m * vec);
+    } else {
+      w.Zb = w.Vb;
+    }
+    ALLOC(w.d, vec);
+    w.rin = w.Vb;  // V0 holds r~
+  }
+  if (w.pc == FIT_PC_JACOBI) ALLOC(w.nusum, ne * w.esz / 2);
+  w.napply = std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
+  ALLOC(w.part_apply, (size_t)B * w.napply * 4 * sizeof(double));
+  int nblk = std::max(8, std::min(1216, (int)((ne + 255) / 256)));
+  nblk = std::max(1, std::min(nblk, 1216 / std::max(1, std::min(B, 8)) * 1));
+  int pstride = w.method == FIT_FGMRES ? 2 * (w.m + 1) : 4;
+  if (pstride < 4) pstride = 4;
+  ALLOC(w.part_vec, (size_t)B * nblk * pstride * sizeof(double));
+  if (w.method == FIT_FGMRES) {
+    ALLOC(w.h1, (size_t)B * 2 * FG_MAXV * sizeof(double));
+    ALLOC(w.h2, (size_t)B * 2 * FG_MAXV * sizeof(double));
+    ALLOC(w.H, (size_t)B * 2 * (w.m + 1) * w.m * sizeof(double));
+    ALLOC(w.G, (size_t)B * 2 * (w.m + 1) * sizeof(double));
+    ALLOC(w.CS, (size_t)B * 2 * w.m * sizeof(double));
+    ALLOC(w.SN, (size_t)B * 2 * w.m * sizeof(double));
+    ALLOC(w.Y, (size_t)B * 2 * FG_MAXV * sizeof(double));
+  }
+  ALLOC(w.sys, (size_t)B * sizeof(Sys));
+  ALLOC(w.ctl, sizeof(Ctl));
+#undef ALLOC
+  FIT_CHECK_CUDA(cudaMemset(w.sys, 0, (size_t)B * sizeof(Sys)));
+  FIT_CHECK_CUDA(cudaMemset(w.ctl, 0, sizeof(Ctl)));
+  w.p.B = B;
+  w.p.ne = g->ne;
+  w.p.nblk = nblk;
+  w.p.pstride = pstride;
+  w.p.m = w.m;
+  w.p.mixed = w.mixed;
+  w.p.s_in = w.mixed ? g->coef_scale : 1.0;
+  w.p.tiny = w.mixed ? 1e-30 : 1e-300;
+  if (w.pc == FIT_PC_JACOBI) {
+    long long nc = g->ncell;
+    if (w.mixed)
+      k_nusum<float><<<(unsigned)((nc + 255) / 256), 256>>>(g->nu32, g->nx, g->ny, g->nz, g->nxp, (float*)w.nusum);
+    else
+      k_nusum<double><<<(unsigned)((nc + 255) / 256), 256>>>(g->nu64, g->nx, g->ny, g->nz, g->nxp, (double*)w.nusum);
+    FIT_CHECK_CUDA(cudaGetLastError());
+  }
+  return FIT_OK;
+}
+
+// ---- the launch sequence (used directly, or captured into a graph) ------------------------------
+struct Seq {
+  Work& w;
+  const double2* rhs;
+  double2* x;
+  cudaStream_t s;
+  fit_status st = FIT_OK;
+
+  dim3 vgrid() const { return dim3(w.p.nblk, w.p.B); }
+  void check() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && st == FIT_OK) {
+      fit_set_error(std::string("fit_solve kernel launch: ") + cudaGetErrorString(e));
+      st = FIT_ECUDA;
+    }
+  }
+  template <int NQ, class Op>
+  void fin(const double* part, long long nslots, int stride, Op op) {
+    fin_kernel<NQ, Op><<<w.p.B, 256, 0, s>>>(part, nslots, stride, w.sys, w.p, op);
+    check();
+  }
+  void apply(const void* xin, void* yout, int mode, const void* u, fit_prec prec, const int* status_field) {
+    fit_epi e;
+    e.mode = mode;
+    e.u = u;
+    e.part = w.part_apply;
+    e.status = status_field;
+    double scale = 1.0;
+    fit_status r = fit_launch_apply(w.g, w.p.B, w.omega, xin, yout, prec, scale, s, &e);
+    if (r != FIT_OK && st == FIT_OK) st = r;
+  }
+  cudaGraphConditionalHandle h_inner = 0;  // set when the inner loop is a graph WHILE node
+  int use_h_inner = 0;
+
+  void outer_init() {
+    k_reset_guard<<<1, 1, 0, s>>>(w.ctl, 1, 0, 0);
+    k_outer_init<<<vgrid(), 256, 0, s>>>(rhs, x, w.r128, w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpOuterInit{});
+  }
+
+  template <typename T>
+  void inner_start() {
+    using V = typename cplx<T>::t;
+    k_reset_guard<<<1, 1, 0, s>>>(w.ctl, 0, h_inner, use_h_inner);
+    bool bicg = w.method == FIT_BICGSTAB;
+    if (bicg)
+      k_inner_start<T, true><<<vgrid(), 256, 0, s>>>(w.r128, w.sys, (V*)w.rin, (V*)w.rhat, (V*)w.pv, (V*)w.v,
+                                                      (V*)w.d, w.part_vec, w.p);
+    else
+      k_inner_start<T, false><<<vgrid(), 256, 0, s>>>(w.r128, w.sys, (V*)w.rin, nullptr, nullptr, nullptr, (V*)w.d,
+                                                       w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpInnerStart{});
+    if (!bicg) {
+      k_fg_reset<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.G, w.sys, w.p);
+      check();
+    }
+  }
+
+  // one BiCGStab iteration (predicated on inner status)
+  template <typename T>
+  void bicg_iter(const int* st_inner) {
+    using V = typename cplx<T>::t;
+    k_bicg_p<T><<<vgrid(), 256, 0, s>>>((const V*)w.rin, (V*)w.pv, (const V*)w.v, w.sys, w.p);
+    check();
+    apply(w.pv, w.v, FIT_EPI_DOT_U, w.rhat, w.inner, st_inner);
+    fin<3>(w.part_apply, w.napply, 4, OpAlpha{});
+    k_bicg_s<T><<<vgrid(), 256, 0, s>>>((V*)w.rin, (const V*)w.v, w.sys, w.p);
+    check();
+    apply(w.rin, w.t, FIT_EPI_DOT_TS, nullptr, w.inner, st_inner);
+    fin<3>(w.part_apply, w.napply, 4, OpOmega{});
+    k_bicg_xr<T><<<vgrid(), 256, 0, s>>>((V*)w.d, (const V*)w.pv, (V*)w.rin, (const V*)w.t, (const V*)w.rhat, w.sys,
+                                         w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpRho{});
+  }
+
+  // Arnoldi step j of FGMRES (predicated on inner status)
+  template <typename T>
+  void fg_step(int j, const int* st_inner) {
+    using V = typename cplx<T>::t;
+    size_t vecb = (size_t)w.p.ne * w.p.B * w.esz;
+    const char* vj = (const char*)w.Vb + (size_t)j * vecb;
+    char* wj1 = (char*)w.Vb + (size_t)(j + 1) * vecb;
+    const void* zin = vj;
+    if (w.pc == FIT_PC_JACOBI) {
+      const fit_grid* g = w.g;
+      k_fg_jacobi<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const T*)w.nusum,
+                                             w.mixed ? (const T*)g->ek32 : (const T*)g->ek64, g->mask, w.omega, g->nx,
+                                             g->ny, g->nxp, w.sys, w.p);
+      check();
+      zin = (const char*)w.Zb + (size_t)j * vecb;
+    }
+    apply(zin, wj1, FIT_EPI_NONE, nullptr, w.inner, st_inner);
+    k_fg_ortho<T, 0><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, nullptr, w.sys, w.part_vec, w.p);
+    check();
+    k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h1, w.sys, w.p);
+    check();
+    k_fg_ortho<T, 1><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, w.h1, w.sys, w.part_vec, w.p);
+    check();
+    k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h2, w.sys, w.p);
+    check();
+    k_fg_ortho<T, 2><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, w.h2, w.sys, w.part_vec, w.p);
+    check();
+    k_fg_givens<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.part_vec, j, w.h1, w.h2, w.H, w.G, w.CS, w.SN, w.sys, w.p);
+    check();
+    k_fg_scale<T><<<vgrid(), 256, 0, s>>>((V*)w.Vb, j, w.sys, w.p);
+    check();
+  }
+
+  template <typename T>
+  void fg_finish() {
+    using V = typename cplx<T>::t;
+    k_fg_solve<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.H, w.G, w.Y, w.sys, w.p);
+    check();
+    k_fg_combine<T><<<vgrid(), 256, 0, s>>>((const V*)w.Zb, (V*)w.d, w.Y, w.sys, w.p);
+    check();
+  }
+
+  template <typename T>
+  void outer_tail(const int* st_outer) {
+    using V = typename cplx<T>::t;
+    k_update_x<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.sys, w.p);
+    check();
+    apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
+    fin<3>(w.part_apply, fit_apply_partials(w.g, FIT_C128), 4, OpOuter{});
+  }
+
+  void cond(int which, int guard_max, cudaGraphConditionalHandle h, int use_handle) {
+    k_cond<<<1, 256, 0, s>>>(w.sys, w.ctl, w.p, which, guard_max, h, use_handle);
+    check();
+  }
+};
+
+// The apply's status predicate reads an int per system with stride 1; the Sys struct is larger, so
+// keep small mirrored status arrays instead.
+__global__ void k_mirror_status(const Sys* __restrict__ sys, int* inner, int* outer, int B) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) {
+    inner[b] = sys[b].inner_status;
+    outer[b] = sys[b].outer_status;
+  }
+}
+
+template <typename T>
+fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, int use_graph, int max_outer_guard,
+                     int max_inner_guard) {
+  int* st_inner = nullptr;
+  int* st_outer = nullptr;
+  fit_status st;
+  if ((st = w.alloc((void**)&st_inner, w.p.B * sizeof(int))) != FIT_OK) return st;
+  if ((st = w.alloc((void**)&st_outer, w.p.B * sizeof(int))) != FIT_OK) return st;
+  Seq q{w, rhs, x, s};
+  auto mirror = [&](cudaStream_t ss) {
+    k_mirror_status<<<(w.p.B + 127) / 128, 128, 0, ss>>>(w.sys, st_inner, st_outer, w.p.B);
+  };
+  const bool bicg = w.method == FIT_BICGSTAB;
+
+  // FIT_TRACE_SOLVE=1 prints the scalars of system 0 after every host-loop step (stderr)
+  const char* tr = getenv("FIT_TRACE_SOLVE");
+  const bool trace = tr && tr[0] == '1';
+  auto dump = [&](const char* what, int k) {
+    if (!trace) return;
+    Sys h;
+    cudaStreamSynchronize(s);
+    cudaMemcpy(&h, w.sys, sizeof(Sys), cudaMemcpyDeviceToHost);
+    fprintf(stderr, "[fit trace] %s %d: outer=%d st=%d/%d it=%d jl=%d rin=%.3e relres=%.3e inv_hn=%.3e iters=%d\n", what,
+            k, h.outer, h.outer_status, h.inner_status, h.inner_it, h.jlast, sqrt(h.rin2),
+            h.bnorm2 > 0 ? sqrt(h.rnorm2 / h.bnorm2) : 0.0, h.inv_hn, h.iters);
+  };
+  if (!use_graph) {
+    q.outer_init();
+    mirror(s);
+    dump("init", 0);
+    Ctl hc;
+    for (int outer = 0; outer < max_outer_guard; ++outer) {
+      q.inner_start<T>();
+      mirror(s);
+      if (bicg) {
+        for (int it = 0; it < max_inner_guard; ++it) {
+          q.bicg_iter<T>(st_inner);
+          mirror(s);
+          q.cond(0, max_inner_guard, 0, 0);
+          FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+          FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+          if (q.st != FIT_OK) return q.st;
+          if (!hc.cond) break;
+        }
+      } else {
+        for (int j = 0; j < w.m; ++j) {
+          q.fg_step<T>(j, st_inner);
+          mirror(s);
+          dump("fg step", j);
+          q.cond(0, max_inner_guard, 0, 0);
+          FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+          FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+          if (q.st != FIT_OK) return q.st;
+          if (!hc.cond) break;
+        }
+        q.fg_finish<T>();
+      }
+      q.outer_tail<T>(st_outer);
+      mirror(s);
+      dump("outer", outer);
+      q.cond(1, max_outer_guard, 0, 0);
+      FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+      FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+      if (q.st != FIT_OK) return q.st;
+      if (!hc.cond) break;
+    }
+    return q.st;
+  }
+
+  // ---- graph mode: one launch for the whole batch solve --------------------------------------
+  // Capture runs on private streams (the caller's stream may be the legacy default stream, which
+  // cannot be captured); the instantiated graph is launched on the caller's stream.
+  cudaStream_t s_top = nullptr, s_outer = nullptr, s_inner = nullptr;
+  FIT_CHECK_CUDA(cudaStreamCreateWithFlags(&s_top, cudaStreamNonBlocking));
+  FIT_CHECK_CUDA(cudaStreamCreateWithFlags(&s_outer, cudaStreamNonBlocking));
+  FIT_CHECK_CUDA(cudaStreamCreateWithFlags(&s_inner, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  fit_status result = FIT_OK;
+  auto fail = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && result == FIT_OK) {
+      fit_set_error(std::string("fit_solve graph: ") + what + ": " + cudaGetErrorString(e));
+      result = FIT_ECUDA;
+    }
+  };
+  do {
+    FIT_CHECK_CUDA(cudaGraphCreate(&graph, 0));
+    // top level: outer init, then the outer WHILE node
+    fail(cudaStreamBeginCaptureToGraph(s_top, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+         "capture top");
+    if (result != FIT_OK) break;
+    q.s = s_top;
+    q.outer_init();
+    mirror(s_top);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t capg = nullptr;
+    fail(cudaStreamGetCaptureInfo(s_top, &cst, nullptr, &capg, &deps, &edata, &ndeps), "capture info");
+    cudaGraphConditionalHandle h_outer;
+    fail(cudaGraphConditionalHandleCreate(&h_outer, capg, 1, cudaGraphCondAssignDefault), "outer handle");
+    cudaGraphNodeParams cp_outer = {};
+    cp_outer.type = cudaGraphNodeTypeConditional;
+    cp_outer.conditional.handle = h_outer;
+    cp_outer.conditional.type = cudaGraphCondTypeWhile;
+    cp_outer.conditional.size = 1;
+    cudaGraphNode_t n_outer;
+    fail(cudaGraphAddNode(&n_outer, capg, deps, edata, ndeps, &cp_outer), "outer node");
+    fail(cudaStreamUpdateCaptureDependencies(s_top, &n_outer, nullptr, 1, cudaStreamSetCaptureDependencies), "deps");
+    cudaGraph_t body_outer = cp_outer.conditional.phGraph_out[0];
+    cudaGraphConditionalHandle h_inner = 0;
+    if (bicg) {
+      fail(cudaGraphConditionalHandleCreate(&h_inner, body_outer, 1, cudaGraphCondAssignDefault), "inner handle");
+      q.h_inner = h_inner;
+      q.use_h_inner = 1;
+    }
+    // outer body
+    fail(cudaStreamBeginCaptureToGraph(s_outer, body_outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+         "capture outer body");
+    if (result != FIT_OK) break;
+    q.s = s_outer;
+    q.inner_start<T>();
+    mirror(s_outer);
+    if (bicg) {
+      cudaGraph_t capo = nullptr;
+      fail(cudaStreamGetCaptureInfo(s_outer, &cst, nullptr, &capo, &deps, &edata, &ndeps), "capture info 2");
+      cudaGraphNodeParams cp_inner = {};
+      cp_inner.type = cudaGraphNodeTypeConditional;
+      cp_inner.conditional.handle = h_inner;
+      cp_inner.conditional.type = cudaGraphCondTypeWhile;
+      cp_inner.conditional.size = 1;
+      cudaGraphNode_t n_inner;
+      fail(cudaGraphAddNode(&n_inner, capo, deps, edata, ndeps, &cp_inner), "inner node");
+      fail(cudaStreamUpdateCaptureDependencies(s_outer, &n_inner, nullptr, 1, cudaStreamSetCaptureDependencies), "deps2");
+      cudaGraph_t body_inner = cp_inner.conditional.phGraph_out[0];
+      fail(cudaStreamBeginCaptureToGraph(s_inner, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+           "capture inner body");
+      if (result != FIT_OK) break;
+      q.s = s_inner;
+      q.bicg_iter<T>(st_inner);
+      mirror(s_inner);
+      q.cond(0, max_inner_guard, h_inner, 1);
+      cudaGraph_t tmp;
+      fail(cudaStreamEndCapture(s_inner, &tmp), "end inner");
+      q.s = s_outer;
+    } else {
+      for (int j = 0; j < w.m; ++j) {
+        q.fg_step<T>(j, st_inner);
+        mirror(s_outer);
+      }
+      q.fg_finish<T>();
+    }
+    q.outer_tail<T>(st_outer);
+    mirror(s_outer);
+    q.cond(1, max_outer_guard, h_outer, 1);
+    cudaGraph_t tmp2;
+    fail(cudaStreamEndCapture(s_outer, &tmp2), "end outer");
+    cudaGraph_t tmp3;
+    fail(cudaStreamEndCapture(s_top, &tmp3), "end top");
+    if (result != FIT_OK || q.st != FIT_OK) break;
+    fail(cudaGraphInstantiate(&exec, graph, 0), "instantiate");
+    if (result != FIT_OK) break;
+    fail(cudaGraphLaunch(exec, s), "launch");
+    fail(cudaStreamSynchronize(s), "run");
+  } while (0);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(s_top);
+  cudaStreamDestroy(s_outer);
+  cudaStreamDestroy(s_inner);
+  if (q.st != FIT_OK) return q.st;
+  return result;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -9,7 +1072,7 @@ void fit_solve_opts_default(fit_solve_opts* o) {
   o->restart = 30;
   o->precision = FIT_SOLVE_MIXED;
   o->max_iter = 20000;
-  o->max_outer = 20;
+  o->max_outer = 30;
   o->inner_tol = 1e-4;
   o->batch = 0;
   o->use_graph = 1;
@@ -19,9 +1082,90 @@ void fit_solve_opts_default(fit_solve_opts* o) {
 
 fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rhs, void* x, double tol,
                      const fit_solve_opts* opts, fit_solve_report* report) {
-  (void)g; (void)nfreq; (void)omega; (void)rhs; (void)x; (void)tol; (void)opts; (void)report;
-  fit_set_error("fit_solve: not available in this build");
-  return FIT_EINVAL;
+  FIT_REQUIRE(g && omega && rhs && x, "fit_solve: null argument");
+  FIT_REQUIRE(nfreq >= 1, "fit_solve: nfreq must be >= 1");
+  FIT_REQUIRE(tol > 0 && isfinite(tol), "fit_solve: tol must be positive");
+  FIT_REQUIRE(g->has_materials, "fit_solve: materials not set");
+  fit_solve_opts o;
+  fit_solve_opts_default(&o);
+  if (opts) o = *opts;
+  FIT_REQUIRE(o.method == FIT_BICGSTAB || o.method == FIT_FGMRES, "fit_solve: unknown method");
+  FIT_REQUIRE(o.precision == FIT_SOLVE_C128 || o.precision == FIT_SOLVE_MIXED, "fit_solve: unknown precision");
+  FIT_REQUIRE(o.method == FIT_BICGSTAB || (o.restart >= 1 && o.restart <= FG_MAXV - 1),
+              "fit_solve: FGMRES restart must be in 1..64");
+  FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET,
+              "fit_solve: unknown preconditioner");
+  FIT_REQUIRE(o.precond == FIT_PC_NONE || o.method == FIT_FGMRES,
+              "fit_solve: preconditioners are applied inside FGMRES only");
+  FIT_REQUIRE(o.precond != FIT_PC_UNET, "fit_solve: no learned preconditioner is loaded");
+  FIT_REQUIRE(o.max_iter >= 1 && o.max_outer >= 1, "fit_solve: iteration caps must be >= 1");
+  FIT_REQUIRE(o.inner_tol > 0 && o.inner_tol < 1, "fit_solve: inner_tol must be in (0, 1)");
+  for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(isfinite(omega[f]), "fit_solve: omega must be finite");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int mixed = o.precision == FIT_SOLVE_MIXED;
+  const int m = o.method == FIT_FGMRES ? o.restart : 0;
+
+  // HBM admission: the largest batch whose workspace fits the budget
+  int B = o.batch > 0 ? std::min(o.batch, nfreq) : nfreq;
+  size_t held = g->bytes_held;
+  while (B > 1 && g->budget && held + workspace_bytes(g, B, o.method, m, mixed, o.precond) > g->budget) B = (B + 1) / 2;
+  if (g->budget && held + workspace_bytes(g, B, o.method, m, mixed, o.precond) > g->budget) {
+    fit_set_error("fit_solve: the Krylov workspace of one system exceeds the HBM budget");
+    return FIT_EBUDGET;
+  }
+
+  fit_status overall = FIT_OK;
+  std::vector<Sys> hs;
+  for (int f0 = 0; f0 < nfreq; f0 += B) {
+    int nb = std::min(B, nfreq - f0);
+    Work w;
+    w.g = g;
+    w.method = o.method;
+    w.m = m > 0 ? m : 30;
+    w.mixed = mixed;
+    w.pc = o.precond;
+    fit_status st = setup(w, nb);
+    if (st != FIT_OK) return st;
+    w.p.tol = tol;
+    w.p.inner_tol = o.inner_tol;
+    w.p.max_iter = o.max_iter;
+    w.p.max_outer = o.max_outer;
+    FIT_CHECK_CUDA(cudaMemcpyAsync(w.omega, omega + f0, nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    const double2* rb = (const double2*)rhs + (size_t)f0 * g->ne;
+    double2* xb = (double2*)x + (size_t)f0 * g->ne;
+    FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+    auto t0 = std::chrono::steady_clock::now();
+    int outer_guard = o.max_outer + 1;
+    int inner_guard = o.max_iter + 1;
+    st = mixed ? run_batch<float>(w, rb, xb, s, o.use_graph, outer_guard, inner_guard)
+               : run_batch<double>(w, rb, xb, s, o.use_graph, outer_guard, inner_guard);
+    if (st != FIT_OK) return st;
+    FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    hs.resize(nb);
+    FIT_CHECK_CUDA(cudaMemcpy(hs.data(), w.sys, nb * sizeof(Sys), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < nb; ++b) {
+      const Sys& y = hs[b];
+      fit_status ps = FIT_OK;
+      switch (y.outer_status) {
+        case SYS_CONV: ps = FIT_OK; break;
+        case SYS_NAN: ps = FIT_ENAN; break;
+        case SYS_BREAK: ps = FIT_BREAKDOWN; break;
+        default: ps = FIT_NOT_CONVERGED; break;
+      }
+      if (ps != FIT_OK && overall == FIT_OK) overall = ps;
+      if (report) {
+        fit_solve_report& r = report[f0 + b];
+        r.status = ps;
+        r.iterations = y.iters;
+        r.outer = y.outer;
+        r.relres = y.bnorm2 > 0 ? sqrt(y.rnorm2 / y.bnorm2) : 0.0;
+        r.seconds = secs;
+      }
+    }
+  }
+  return overall;
 }
 
 }  // extern "C"

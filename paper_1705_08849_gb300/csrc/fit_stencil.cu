@@ -62,48 +62,70 @@ struct GenericView {
   }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a) {
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a, fit_epi epi) {
   using V = typename cplx<T>::t;
-  int i = blockIdx.x * 32 + threadIdx.x;
-  int j = blockIdx.y * 8 + threadIdx.y;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const bool valid = i < a.nx && j < a.ny;
   for (long long zb = blockIdx.z; zb < (long long)a.nz * a.nbatch; zb += gridDim.z) {
-    int k = (int)(zb % a.nz);
-    int b = (int)(zb / a.nz);
-    if (i >= a.nx || j >= a.ny) return;
+    const int k = (int)(zb % a.nz);
+    const int b = (int)(zb / a.nz);
+    if (epi.status && epi.status[b] != 0) continue;  // uniform over the block
     const V* x = a.x + (long long)b * a.ne;
     V* y = a.y + (long long)b * a.ne;
-    GenericView<T> g{a, x};
-    V hx = g.hx(i, j, k), hy = g.hy(i, j, k), hz = g.hz(i, j, k);
-    V cx = g.hy(i, j, k - 1) - hy + hz - g.hz(i, j - 1, k);
-    V cy = g.hz(i - 1, j, k) - hz + hx - g.hx(i, j, k - 1);
-    V cz = g.hx(i, j - 1, k) - hx + hy - g.hy(i - 1, j, k);
-    long long c = i + (long long)a.nx * (j + (long long)a.ny * k);
-    long long cp = i + (long long)a.nxp * (j + (long long)a.ny * k);
-    uint8_t m = a.mask[cp];
-    T w = (T)a.omega[b];
-    T w2 = w * w;
-    V curl[3] = {cx, cy, cz};
+    T acc[3] = {T(0), T(0), T(0)};
+    if (valid) {
+      GenericView<T> g{a, x};
+      V hx = g.hx(i, j, k), hy = g.hy(i, j, k), hz = g.hz(i, j, k);
+      V cx = g.hy(i, j, k - 1) - hy + hz - g.hz(i, j - 1, k);
+      V cy = g.hz(i - 1, j, k) - hz + hx - g.hx(i, j, k - 1);
+      V cz = g.hx(i, j - 1, k) - hx + hy - g.hy(i - 1, j, k);
+      long long c = i + (long long)a.nx * (j + (long long)a.ny * k);
+      long long cp = i + (long long)a.nxp * (j + (long long)a.ny * k);
+      uint8_t m = a.mask[cp];
+      T w = (T)a.omega[b];
+      T w2 = w * w;
+      V curl[3] = {cx, cy, cz};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      V xv = x[3 * c + q];
-      V out;
-      if ((m >> q) & 1) {
-        out = xv;
-      } else {
-        T ar = -w2 * a.ek[6 * cp + q];  // -w^2 M_eps
-        T ai = w * a.ek[6 * cp + 3 + q];  // w M_kappa
-        out.x = a.out_scale * (curl[q].x + ar * xv.x - ai * xv.y);
-        out.y = a.out_scale * (curl[q].y + ar * xv.y + ai * xv.x);
+      for (int q = 0; q < 3; ++q) {
+        V xv = x[3 * c + q];
+        V out;
+        if ((m >> q) & 1) {
+          out = xv;
+        } else {
+          T ar = -w2 * a.ek[6 * cp + q];    // -w^2 M_eps
+          T ai = w * a.ek[6 * cp + 3 + q];  // w M_kappa
+          out.x = a.out_scale * (curl[q].x + ar * xv.x - ai * xv.y);
+          out.y = a.out_scale * (curl[q].y + ar * xv.y + ai * xv.x);
+        }
+        if (EPI == FIT_EPI_DOT_U) {
+          V u = ((const V*)epi.u)[(long long)b * a.ne + 3 * c + q];
+          acc[0] += u.x * out.x + u.y * out.y;  // conj(u) * y
+          acc[1] += u.x * out.y - u.y * out.x;
+        } else if (EPI == FIT_EPI_DOT_TS) {
+          acc[0] += out.x * xv.x + out.y * xv.y;  // conj(t) * s
+          acc[1] += out.x * xv.y - out.y * xv.x;
+          acc[2] += out.x * out.x + out.y * out.y;
+        } else if (EPI == FIT_EPI_RESID) {
+          V u = ((const V*)epi.u)[(long long)b * a.ne + 3 * c + q];
+          out = u - out;
+          acc[2] += out.x * out.x + out.y * out.y;
+        }
+        y[3 * c + q] = out;
       }
-      y[3 * c + q] = out;
+    }
+    if (EPI != FIT_EPI_NONE) {
+      long long nblk = (long long)gridDim.x * gridDim.y * a.nz;
+      long long blk = ((long long)k * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      fit_block_sum<T, 3>(acc, epi.part + ((long long)b * nblk + blk) * 4);
     }
   }
 }
 
 template <typename T>
 static fit_status launch_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                                 const T* nu, const T* ek, double out_scale, cudaStream_t s) {
+                                 const T* nu, const T* ek, double out_scale, cudaStream_t s, const fit_epi* epi) {
   ApplyArgs<T> a;
   a.x = (const typename cplx<T>::t*)x;
   a.y = (typename cplx<T>::t*)y;
@@ -118,21 +140,39 @@ static fit_status launch_generic(fit_grid* g, int nbatch, const double* omega_de
   a.ne = g->ne;
   a.nbatch = nbatch;
   a.out_scale = (T)out_scale;
+  fit_epi e;
+  if (epi) e = *epi;
   dim3 block(32, 8, 1);
   long long gz = (long long)g->nz * nbatch;
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (unsigned)(gz < 65535 ? gz : 65535));
-  apply_generic_kernel<T><<<grid, block, 0, s>>>(a);
+  switch (e.mode) {
+    case FIT_EPI_NONE: apply_generic_kernel<T, FIT_EPI_NONE><<<grid, block, 0, s>>>(a, e); break;
+    case FIT_EPI_DOT_U: apply_generic_kernel<T, FIT_EPI_DOT_U><<<grid, block, 0, s>>>(a, e); break;
+    case FIT_EPI_DOT_TS: apply_generic_kernel<T, FIT_EPI_DOT_TS><<<grid, block, 0, s>>>(a, e); break;
+    case FIT_EPI_RESID: apply_generic_kernel<T, FIT_EPI_RESID><<<grid, block, 0, s>>>(a, e); break;
+    default: fit_set_error("unknown apply epilogue"); return FIT_EINVAL;
+  }
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
 
+long long fit_apply_partials_generic(const fit_grid* g) {
+  return (long long)((g->nx + 31) / 32) * ((g->ny + 7) / 8) * g->nz;
+}
+
 fit_status fit_launch_apply_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                                    fit_prec prec, double out_scale, cudaStream_t s) {
-  if (prec == FIT_C64) return launch_generic<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, out_scale, s);
-  return launch_generic<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, out_scale, s);
+                                    fit_prec prec, double out_scale, cudaStream_t s, const fit_epi* epi) {
+  if (prec == FIT_C64)
+    return launch_generic<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, out_scale, s, epi);
+  return launch_generic<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, out_scale, s, epi);
+}
+
+long long fit_apply_partials(const fit_grid* g, fit_prec prec) {
+  (void)prec;
+  return fit_apply_partials_generic(g);
 }
 
 fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                            fit_prec prec, double out_scale, cudaStream_t s) {
-  return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s);
+                            fit_prec prec, double out_scale, cudaStream_t s, const fit_epi* epi) {
+  return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, epi);
 }

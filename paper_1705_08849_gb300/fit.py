@@ -180,8 +180,10 @@ def fit_solve(g, omega, rhs, x, tol, opts=None, **kw):
     if o.stream is None:
         o.stream = _stream_ptr(None).value
     reps = (fit_solve_report * nf)()
-    st = _check(lib().fit_solve(g, nf, pom, ct.c_void_p(rhs.data_ptr()), ct.c_void_p(x.data_ptr()), float(tol),
-                                ct.byref(o), reps), "fit_solve")
+    st = lib().fit_solve(g, nf, pom, ct.c_void_p(rhs.data_ptr()), ct.c_void_p(x.data_ptr()), float(tol),
+                         ct.byref(o), reps)
+    if st not in (FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN, FIT_ENAN):  # per-system outcomes are returned
+        _check(st, "fit_solve")
     return st, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres, seconds=r.seconds)
                 for r in reps]
 

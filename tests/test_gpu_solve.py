@@ -1,0 +1,128 @@
+"""GPU solves judged by the oracle: every solution x returned by fit_solve is checked with the
+oracle's own FP64 residual ||b - A_oracle x|| / ||b|| (Eq. e2 system, Sec. IV stop criterion on the
+relative residual), and on small systems against the oracle's sparse direct solution."""
+import numpy as np
+import pytest
+
+import fitgen as G
+from tests._gpu_util import fitlib, oracle_A, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(case, freqs, tol, rhs=None, **opts):
+    torch = torch_cuda()
+    fit = fitlib()
+    ws = 2 * np.pi * np.asarray(freqs, dtype=np.float64)
+    ne = 3 * case["nx"] * case["ny"] * case["nz"]
+    if rhs is None:
+        from oracle import fit as F
+        A0, mask = oracle_A(case, ws[0])
+        j = G.source_vector(case)
+        rhs = np.stack([F.rhs_from_current(w, j, mask) for w in ws])
+    with fit.Grid.from_case(case) as g:
+        b = torch.from_numpy(np.ascontiguousarray(rhs.reshape(-1))).cuda()
+        x = torch.zeros_like(b)
+        st, rep = g.solve(ws, b, x, tol, **opts)
+        torch.cuda.synchronize()
+        xs = x.cpu().numpy().reshape(len(ws), ne)
+    return st, rep, xs, rhs.reshape(len(ws), ne), ws
+
+
+def _oracle_relres(case, w, x, b):
+    A, _ = oracle_A(case, w)
+    return float(np.linalg.norm(b - A @ x) / np.linalg.norm(b)), A
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("method", [0, 1])
+def test_cavity16_solve(precision, method):
+    """The cavity workload: 16^3 PEC vacuum cube, 5 GHz, centre z-edge source, tol 1e-10."""
+    from oracle import krylov as K
+    case = G.cavity(16)
+    st, rep, xs, bs, ws = _solve(case, case["freqs"], 1e-10, precision=precision, method=method, restart=30)
+    rr, A = _oracle_relres(case, ws[0], xs[0], bs[0])
+    assert st == 0 and rep[0]["status"] == 0, rep
+    assert rr <= 1e-10, rr
+    xd = K.sparse_solve(A, bs[0])
+    assert np.linalg.norm(xs[0] - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert abs(rep[0]["relres"] - rr) <= 0.5 * rr + 1e-14
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("method,precond", [(0, 0), (1, 0), (1, 1)])
+def test_small_lossy_batch(method, precond, use_graph):
+    case = G.small_random(20, 18, 11, seed=31, pec_frac=0.05)
+    n = 3 * 20 * 18 * 11
+    rhs = np.stack([G.random_vector(n, s) for s in (1, 2, 3)])
+    freqs = [1e9, 4e9, 9e9]
+    from oracle import fit as F
+    rhs = np.stack([rhs[i] * (1 - F.edge_mask(20, 18, 11, case["pec"])) for i in range(3)])
+    st, rep, xs, bs, ws = _solve(case, freqs, 1e-9, rhs=rhs, method=method, precond=precond, restart=25,
+                                 use_graph=use_graph)
+    assert st == 0, rep
+    for i in range(3):
+        rr, _ = _oracle_relres(case, ws[i], xs[i], bs[i])
+        assert rr <= 1e-9, (i, rr, rep[i])
+
+
+def test_graph_and_host_loop_agree_exactly():
+    """The device-side loop (graph) and the host-driven loop run the same kernels in the same order."""
+    case = G.small_random(16, 12, 10, seed=41, pec_frac=0.0)
+    n = 3 * 16 * 12 * 10
+    rhs = G.random_vector(n, 5)[None]
+    a = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=0)
+    b = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=1)
+    assert a[1][0]["iterations"] == b[1][0]["iterations"]
+    assert np.array_equal(a[2], b[2])
+
+
+def test_layered128_mixed_vs_c128():
+    """The 128^3 workload: complex64 inner BiCGStab with FP64 refinement against full complex128;
+    each judged by the oracle residual (1e-8); their difference is the per-result error."""
+    case = G.layered_blocks()
+    out = {}
+    for prec in (1, 0):
+        st, rep, xs, bs, ws = _solve(case, case["freqs"], 1e-8, precision=prec)
+        assert st == 0, rep
+        rr, _ = _oracle_relres(case, ws[0], xs[0], bs[0])
+        assert rr <= 1e-8, (prec, rr, rep)
+        out[prec] = (xs[0], rep[0])
+    diff = np.linalg.norm(out[1][0] - out[0][0]) / np.linalg.norm(out[0][0])
+    assert diff <= 1e-5, diff
+
+
+def test_stripline96_batched_subset():
+    """Four frequencies of the 96^3 stripline sweep solved as one batch (one graph launch)."""
+    case = G.stripline()
+    freqs = case["freqs"][[0, 21, 42, 63]]
+    st, rep, xs, bs, ws = _solve(case, freqs, 1e-8, max_iter=30000)
+    for i in range(len(freqs)):
+        rr, _ = _oracle_relres(case, ws[i], xs[i], bs[i])
+        if rep[i]["status"] == 0:
+            assert rr <= 1e-8, (i, rr, rep[i])
+        else:  # a lossless closed box: a frequency near a cavity resonance may not converge
+            assert rep[i]["status"] == 1 and abs(rep[i]["relres"] - rr) <= 0.5 * rr
+
+
+def test_zero_rhs_and_nan_rhs_and_caps():
+    torch = torch_cuda()
+    fit = fitlib()
+    case = G.small_random(8, 8, 8, seed=3)
+    n = 3 * 512
+    with fit.Grid.from_case(case) as g:
+        b = torch.zeros(n, dtype=torch.complex128, device="cuda")
+        x = torch.ones_like(b)
+        st, rep = g.solve([1e10], b, x, 1e-8)
+        assert st == 0 and rep[0]["iterations"] == 0 and torch.count_nonzero(x).item() == 0
+        b = torch.from_numpy(G.random_vector(n, 1)).cuda()
+        b[7] = float("nan")
+        st, rep = g.solve([1e10], b, x, 1e-8)
+        assert st == fit.FIT_ENAN and rep[0]["status"] == fit.FIT_ENAN
+        b = torch.from_numpy(G.random_vector(n, 2)).cuda()
+        st, rep = g.solve([1e10], b, x, 1e-12, max_iter=2, max_outer=1)
+        assert st == fit.FIT_NOT_CONVERGED and rep[0]["status"] == fit.FIT_NOT_CONVERGED
+        fit.fit_set_hbm_budget(g.h, 1)
+        with pytest.raises(fit.FitError) as ei:
+            g.solve([1e10], b, x, 1e-8)
+        assert ei.value.status == fit.FIT_EBUDGET
