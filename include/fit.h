@@ -104,7 +104,8 @@ typedef struct fit_solve_opts {
   int precision;     /* fit_solve_precision: plain complex128 Krylov, or complex64 inner Krylov
                         inside FP64 iterative refinement (true residual b - A x in FP64) */
   int max_iter;      /* cap on Krylov iterations per system (summed over refinement steps) */
-  int max_outer;     /* cap on refinement steps (FIT_SOLVE_MIXED); default 20 */
+  int max_outer;     /* cap on outer steps (refinement steps, or true-residual restarts of a
+                        complex128 solve); default 30 */
   double inner_tol;  /* relative tolerance of each inner complex64 solve; default 1e-4 */
   int batch;         /* systems solved together in one batched launch; 0 = all nfreq */
   int use_graph;     /* nonzero: run the Krylov loop as one CUDA graph with a device-side loop */
@@ -115,7 +116,7 @@ typedef struct fit_solve_opts {
 typedef struct fit_solve_report {
   int status;        /* fit_status of this system */
   int iterations;    /* Krylov iterations (inner iterations summed over refinement steps) */
-  int outer;         /* refinement steps taken (0 for FIT_SOLVE_C128) */
+  int outer;         /* outer steps taken (refinement steps / true-residual restarts) */
   double relres;     /* final true relative residual ||b - A x||_2 / ||b||_2, computed in FP64 */
   double seconds;    /* wall time of the batch this system was solved in */
 } fit_solve_report;
@@ -143,6 +144,19 @@ fit_status fit_set_hbm_budget(fit_grid* g, size_t bytes);
 
 /* fit_grid_info -- sizes: out[0..5] = nx, ny, nz, n_e, bytes held on the device, budget. */
 fit_status fit_grid_info(const fit_grid* g, long long* out6);
+
+/* fit_apply_variant_count -- number of launch shapes of the fused TMA stencil kernel for a precision
+ * (the candidates the autotuner times; see fit_apply_tuned). */
+int fit_apply_variant_count(fit_prec prec);
+
+/* fit_apply_tuned -- the apply kernel the autotuner picked for (prec, nbatch) on this grid:
+ *   out4[0] = -2 not tuned yet, -1 generic kernel, k >= 0 fused variant k
+ *   out4[1..3] = tile TX, TY and planes per CTA (TZ) of that kernel.
+ * The autotuner runs on the first fit_apply / fit_solve with a new (prec, nbatch); it times every
+ * candidate on the caller's stream (synchronising it) and caches the fastest in the handle.
+ * Tests and experiments can force a kernel with the environment variable
+ * FIT_APPLY_KERNEL=generic or FIT_APPLY_KERNEL=fused:<k>. */
+fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out4);
 
 /* fit_grid_destroy -- free the handle and all its device memory (NULL is a no-op). */
 void fit_grid_destroy(fit_grid* g);

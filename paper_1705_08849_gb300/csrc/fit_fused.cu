@@ -1,0 +1,647 @@
+// Fused TMA-staged stencil apply for sm_103a: one kernel, one pass over HBM.
+//
+// Computes the same operator as the generic kernel in fit_stencil.cu (Eq. e2 with the Eq. CP
+// curl, matrix-free as in Sec. III / Eq. e2t but fused: h = M_nu C e lives only in registers):
+//     y = out_scale * [ C^T M_nu C (P x) - w^2 M_eps x + j w M_kappa x ],   y = x on masked edges.
+//
+// Decomposition.  A CTA owns a tile of TX x TY cells in the (x, y) plane and a chunk of TZ planes
+// along z; one thread owns one (i, j) column and marches up the chunk.  For every plane the CTA
+// stages, with bulk tensor copies (cp.async.bulk.tensor, TMA) into a ring of S shared-memory
+// stages completed on mbarriers:
+//     e     (TX+4) x (TY+2) cells x 3 complex   (x from i0-2 so the copy starts 16-byte aligned)
+//     M_nu  (TX+4) x (TY+1) cells x 3           (x from i0-4, the same alignment rule)
+//     M_eps, M_kappa  TX x TY cells x 6         (own cells only)
+//     mask  (TX+32) x (TY+2) bytes              (x from i0-16)
+// Out-of-grid boxes are zero-filled by the copy engine, which is exactly the truncation of the
+// forward differences at the walls.  After a plane lands, masked edges of the staged e are zeroed
+// (the P in P C^T M_nu C P).  At plane k a thread needs e at planes k and k+1 and h at plane k-1 of
+// its own column, which it carries in registers from the previous step, together with e of its
+// own, its x-1 and its y-1 cell.  Output rows go through a per-warp shared-memory transpose so
+// that each warp writes its 32 x 3 complex values as three fully coalesced 256-byte stores.
+//
+// Fused epilogues (fit_epi): <u, y>, <y, x> and <y, y>, or y = u - A x with <y, y>, accumulated
+// per thread in the vector precision and reduced by fit_block_sum (FP64 from the warp level up).
+//
+// Every wait on an mbarrier is bounded; on timeout the CTA records an error code in the grid's
+// device error word, waits (bounded) for the copies it issued, and returns.
+#include <cuda.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "fit_internal.cuh"
+
+namespace {
+
+constexpr int TX = 32;  // one warp per tile row
+
+template <typename T, int TY>
+struct Layout {
+  using V = typename cplx<T>::t;
+  static constexpr int CE = sizeof(V) / 8;      // 8-byte copy elements per complex value
+  static constexpr int EW = 3 * (TX + 4);       // complex values per staged e row
+  static constexpr int ER = TY + 2;
+  static constexpr int NW = 3 * (TX + 4);       // T values per staged M_nu row
+  static constexpr int NR = TY + 1;
+  static constexpr int KW = 6 * TX;             // T values per staged M_eps/M_kappa row
+  static constexpr int MW = TX + 32;            // mask bytes per staged row
+  static constexpr int MR = TY + 2;
+  static constexpr int al(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int E_BYTES = EW * ER * (int)sizeof(V);
+  static constexpr int N_BYTES = NW * NR * (int)sizeof(T);
+  static constexpr int K_BYTES = KW * TY * (int)sizeof(T);
+  static constexpr int M_BYTES = MW * MR;
+  static constexpr int E_OFF = 0;
+  static constexpr int N_OFF = al(E_BYTES);
+  static constexpr int K_OFF = N_OFF + al(N_BYTES);
+  static constexpr int M_OFF = K_OFF + al(K_BYTES);
+  static constexpr int STAGE = M_OFF + al(M_BYTES);
+  static constexpr int TX_BYTES = E_BYTES + N_BYTES + K_BYTES + M_BYTES;
+  static constexpr int STG_BYTES = al(TY * 96 * (int)sizeof(V));
+  static int smem(int S) { return S * STAGE + STG_BYTES + 8 * S + 128; }
+};
+
+template <typename T>
+struct FusedArgs {
+  using V = typename cplx<T>::t;
+  const V* x;
+  V* y;
+  const double* omega;
+  int* err;
+  int nx, ny, nz, tz, nzc;
+  long long ne;
+  T out_scale;
+};
+
+// ---- PTX helpers: mbarrier and bulk tensor copies -----------------------------------------------
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after ~2^22 polls (the copy engine never needs that long for a few KB)
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+__device__ inline void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ inline void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename V> __device__ inline V ld_raw(const V* p) { return *p; }
+
+// ---- the kernel ----------------------------------------------------------------------------------
+template <typename T, int TY, int EPI, int S>
+__global__ void __launch_bounds__(TX* TY, TY <= 8 ? 2 : 1) fused_apply_kernel(const __grid_constant__ CUtensorMap tm_x,
+                                                             const __grid_constant__ CUtensorMap tm_nu,
+                                                             const __grid_constant__ CUtensorMap tm_ek,
+                                                             const __grid_constant__ CUtensorMap tm_mask,
+                                                             FusedArgs<T> a, fit_epi epi) {
+  using V = typename cplx<T>::t;
+  using L = Layout<T, TY>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int zc = blockIdx.z % a.nzc, b = blockIdx.z / a.nzc;
+  const int k0 = zc * a.tz, k1 = min(a.nz, k0 + a.tz);
+  if (epi.status && epi.status[b] != 0) return;  // uniform over the CTA
+
+  V* stg = (V*)(smem + S * L::STAGE) + ty * 96;
+  uint64_t* bars = (uint64_t*)(smem + S * L::STAGE + L::STG_BYTES);
+  const int nplanes = k1 - k0 + 2;  // planes k0-1 .. k1
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto stage = [&](int q) -> unsigned char* { return smem + (q % S) * L::STAGE; };
+  auto issue = [&](int q) {  // thread 0 only
+    const int p = k0 - 1 + q;
+    unsigned char* st = stage(q);
+    uint64_t* bar = &bars[q % S];
+    mbar_expect_tx(bar, L::TX_BYTES);
+    tma_load_4d(st + L::E_OFF, &tm_x, L::CE * 3 * (i0 - 2), j0 - 1, p, b, bar);
+    tma_load_3d(st + L::N_OFF, &tm_nu, 3 * (i0 - 4), j0 - 1, p, bar);
+    tma_load_3d(st + L::K_OFF, &tm_ek, 6 * i0, j0, p, bar);
+    tma_load_3d(st + L::M_OFF, &tm_mask, i0 - 16, j0 - 1, p, bar);
+  };
+  auto zero_pass = [&](int q) {  // P: zero masked components of the staged e plane
+    V* e = (V*)(stage(q) + L::E_OFF);
+    const uint8_t* m = stage(q) + L::M_OFF;
+    // warp w takes rows w, w + TY, ...; a row whose 36 staged mask bytes (cells i0-2 .. i0+33, at
+    // byte offsets 14 .. 49 of the 64-byte mask row) are all zero is skipped after one vote
+    for (int cy = ty; cy < TY + 2; cy += TY) {
+      const uint8_t* mrow = m + cy * L::MW;
+      const uint32_t word = tx < 16 ? reinterpret_cast<const uint32_t*>(mrow)[tx] : 0u;
+      const uint32_t sel = tx == 3 ? 0xFFFF0000u : (tx >= 4 && tx <= 11 ? 0xFFFFFFFFu : (tx == 12 ? 0x0000FFFFu : 0u));
+      if (!__any_sync(0xffffffffu, (word & sel) != 0u)) continue;
+      for (int cx = tx; cx < TX + 4; cx += 32) {
+        const uint8_t mb = mrow[cx + 14];
+        if (mb) {
+          V* ec = e + cy * L::EW + 3 * cx;
+          if (mb & 1) ec[0] = czero<V>();
+          if (mb & 2) ec[1] = czero<V>();
+          if (mb & 4) ec[2] = czero<V>();
+        }
+      }
+    }
+    fence_proxy_async();  // order these generic writes before later bulk copies into the stage
+  };
+
+  int issued = 0, waited = 0;
+  bool ok = true;
+  if (tid == 0)
+    for (int q = 0; q < min(S, nplanes); ++q) issue(q);
+  issued = min(S, nplanes);
+
+  const int i = i0 + tx, j = j0 + ty;
+  const bool valid = i < a.nx && j < a.ny;
+  // staged-plane accessors (row/column of this thread's cell inside the stage boxes)
+  const int er = (ty + 1) * L::EW + 3 * (tx + 2);
+  const int nr = (ty + 1) * L::NW + 3 * (tx + 4);
+  auto E = [&](int q, int dx, int dy, int w) -> V {
+    return ((const V*)(stage(q) + L::E_OFF))[er + dy * L::EW + 3 * dx + w];
+  };
+  auto NU = [&](int q, int dx, int dy, int w) -> T {
+    return ((const T*)(stage(q) + L::N_OFF))[nr + dy * L::NW + 3 * dx + w];
+  };
+
+  // prologue: planes k0-1 (q = 0) and k0 (q = 1); h(k0-1) of the own column
+  ok = mbar_wait(&bars[0], 0);
+  if (ok) zero_pass(0);
+  ok = ok && mbar_wait(&bars[1 % S], (1 / S) & 1);
+  if (ok) zero_pass(1);
+  ok = __syncthreads_and(ok) != 0;  // block-uniform
+  if (ok) waited = 2;
+  V e0[3], em[3], ejm[3];
+  V hxp, hyp;
+  {
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      e0[w] = E(1, 0, 0, w);
+      em[w] = E(1, -1, 0, w);
+      ejm[w] = E(1, 0, -1, w);
+    }
+    const V ey_m = E(0, 0, 0, 1), ez_m = E(0, 0, 0, 2), ex_m = E(0, 0, 0, 0);
+    hxp = NU(0, 0, 0, 0) * (ey_m - e0[1] + E(0, 0, 1, 2) - ez_m);
+    hyp = NU(0, 0, 0, 1) * (ez_m - E(0, 1, 0, 2) + e0[0] - ex_m);
+  }
+  __syncthreads();
+  if (tid == 0 && ok && S < nplanes) {
+    fence_proxy_async();
+    issue(S);
+  }
+  if (S < nplanes) issued = S + 1;
+
+  T acc[3] = {T(0), T(0), T(0)};
+  const double wd = a.omega[b];
+  const T w1 = (T)wd, w2 = (T)(wd * wd);
+  const long long boff = (long long)b * a.ne;
+  const V* xg = a.x + boff;
+  V* yg = a.y + boff;
+  const V* ug = (EPI == FIT_EPI_DOT_U || EPI == FIT_EPI_RESID) ? (const V*)epi.u + boff : nullptr;
+
+  for (int k = k0; k < k1 && ok; ++k) {
+    const int qk = k - k0 + 1, qn = qk + 1;
+    ok = mbar_wait(&bars[qn % S], (qn / S) & 1);
+    if (ok) zero_pass(qn);
+    ok = __syncthreads_and(ok) != 0;  // block-uniform
+    if (!ok) break;
+    waited = qn + 1;
+    if (qk >= 2 && qk - 1 + S < nplanes) {
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(qk - 1 + S);
+      }
+      issued = qk + S;
+    }
+    // ---- this thread's column at plane k ----
+    V e1[3], em1[3], ejm1[3];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      e1[w] = E(qn, 0, 0, w);
+      em1[w] = E(qn, -1, 0, w);
+      ejm1[w] = E(qn, 0, -1, w);
+    }
+    const V ez_jp = E(qk, 0, 1, 2), ex_jp = E(qk, 0, 1, 0);
+    const V ez_ip = E(qk, 1, 0, 2), ey_ip = E(qk, 1, 0, 1);
+    const V ex_imjp = E(qk, -1, 1, 0), ey_ipjm = E(qk, 1, -1, 1);
+    const V hx = NU(qk, 0, 0, 0) * (e0[1] - e1[1] + ez_jp - e0[2]);
+    const V hy = NU(qk, 0, 0, 1) * (e0[2] - ez_ip + e1[0] - e0[0]);
+    const V hz = NU(qk, 0, 0, 2) * (e0[0] - ex_jp + ey_ip - e0[1]);
+    const V hy_im = NU(qk, -1, 0, 1) * (em[2] - e0[2] + em1[0] - em[0]);
+    const V hz_im = NU(qk, -1, 0, 2) * (em[0] - ex_imjp + e0[1] - em[1]);
+    const V hx_jm = NU(qk, 0, -1, 0) * (ejm[1] - ejm1[1] + e0[2] - ejm[2]);
+    const V hz_jm = NU(qk, 0, -1, 2) * (ejm[0] - e0[0] + ey_ipjm - ejm[1]);
+    V curl[3];
+    curl[0] = hyp - hy + hz - hz_jm;
+    curl[1] = hz_im - hz + hx - hxp;
+    curl[2] = hx_jm - hx + hy - hy_im;
+    const T* ek = (const T*)(stage(qk) + L::K_OFF) + ty * L::KW + 6 * tx;
+    const uint8_t m = (stage(qk) + L::M_OFF)[(ty + 1) * L::MW + tx + 16];
+    const long long rowbase = 3 * (i0 + (long long)a.nx * (j + (long long)a.ny * k));
+    const int nvalid = 3 * max(0, min(TX, a.nx - i0));  // valid complex values of this warp row
+    const bool row_ok = j < a.ny;
+    V uv[3];
+    if (EPI == FIT_EPI_DOT_U || EPI == FIT_EPI_RESID) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int q = tx + 32 * r;
+        if (row_ok && q < nvalid) stg[q] = ug[rowbase + q];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int w = 0; w < 3; ++w) uv[w] = stg[3 * tx + w];
+      __syncwarp();
+    }
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      V out;
+      V xv = e0[w];
+      if ((m >> w) & 1) {
+        xv = valid ? xg[rowbase + 3 * tx + w] : czero<V>();  // raw x on a masked edge
+        out = xv;
+      } else {
+        const T ar = -w2 * ek[w], ai = w1 * ek[3 + w];
+        out.x = a.out_scale * (curl[w].x + ar * xv.x - ai * xv.y);
+        out.y = a.out_scale * (curl[w].y + ar * xv.y + ai * xv.x);
+      }
+      if (valid) {
+        if (EPI == FIT_EPI_DOT_U) {
+          acc[0] += uv[w].x * out.x + uv[w].y * out.y;
+          acc[1] += uv[w].x * out.y - uv[w].y * out.x;
+        } else if (EPI == FIT_EPI_DOT_TS) {
+          acc[0] += out.x * xv.x + out.y * xv.y;
+          acc[1] += out.x * xv.y - out.y * xv.x;
+          acc[2] += out.x * out.x + out.y * out.y;
+        } else if (EPI == FIT_EPI_RESID) {
+          out = uv[w] - out;
+          acc[2] += out.x * out.x + out.y * out.y;
+        }
+      }
+      stg[3 * tx + w] = out;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int q = tx + 32 * r;
+      if (row_ok && q < nvalid) yg[rowbase + q] = stg[q];
+    }
+    __syncwarp();
+    hxp = hx;
+    hyp = hy;
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      e0[w] = e1[w];
+      em[w] = em1[w];
+      ejm[w] = ejm1[w];
+    }
+  }
+
+  if (!ok) {  // a copy did not complete in time: record it and drain what was issued
+    if (tid == 0) atomicExch(a.err, 1);
+    for (int q = waited; q < issued; ++q) (void)mbar_wait(&bars[q % S], (q / S) & 1);
+    return;
+  }
+  if (EPI != FIT_EPI_NONE) {
+    const long long nblk = (long long)gridDim.x * gridDim.y * a.nzc;
+    const long long blk = ((long long)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    fit_block_sum<T, 3>(acc, epi.part + ((long long)b * nblk + blk) * 4);
+  }
+}
+
+// ---- host side -----------------------------------------------------------------------------------
+typedef CUresult (*encode_fn_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_fn_t encoder() {
+  static encode_fn_t fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (encode_fn_t)p;
+  }
+  return fn;
+}
+
+bool encode(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,
+            const cuuint64_t* strides, const cuuint32_t* box) {
+  encode_fn_t fn = encoder();
+  if (!fn) return false;
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(m, dt, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct Variant {
+  int ty, tz, stages;
+};
+// candidate launch shapes; the autotuner picks one per (grid, precision, batch)
+const Variant kVariants64[] = {{8, 16, 4}, {8, 32, 4}, {8, 8, 4}, {4, 32, 4}, {4, 16, 4}, {16, 16, 3}, {16, 32, 3},
+                               {8, 16, 3}, {8, 32, 3}, {4, 32, 3}, {4, 32, 6}, {4, 32, 8}, {4, 64, 8},
+                               {8, 32, 6}, {8, 64, 6}};
+const Variant kVariants128[] = {{4, 16, 3}, {4, 32, 3}, {8, 16, 3}, {8, 32, 3}};
+
+template <typename T, int TY, int S>
+fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
+                          const T* ek, double out_scale, cudaStream_t s, fit_epi& e, int tz) {
+  using L = Layout<T, TY>;
+  const bool c64 = sizeof(T) == 4;
+  CUtensorMap mx, mnu, mek, mmask;
+  const cuuint64_t ce = c64 ? 1 : 2;
+  {
+    cuuint64_t dims[4] = {3 * ce * (cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, (cuuint64_t)nbatch};
+    cuuint64_t rowb = 3 * ce * 8 * (cuuint64_t)g->nx;
+    cuuint64_t str[3] = {rowb, rowb * g->ny, rowb * g->ny * g->nz};
+    cuuint32_t box[4] = {(cuuint32_t)(3 * ce * (TX + 4)), TY + 2, 1, 1};
+    if (!encode(&mx, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, x, dims, str, box)) {
+      fit_set_error("fused apply: tensor map of x rejected");
+      return FIT_ECUDA;
+    }
+  }
+  const CUtensorMapDataType cdt = c64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  {
+    cuuint64_t dims[3] = {3 * (cuuint64_t)g->nxp, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
+    cuuint64_t rowb = 3 * sizeof(T) * (cuuint64_t)g->nxp;
+    cuuint64_t str[2] = {rowb, rowb * g->ny};
+    cuuint32_t box[3] = {3 * (TX + 4), TY + 1, 1};
+    if (!encode(&mnu, cdt, 3, nu, dims, str, box)) {
+      fit_set_error("fused apply: tensor map of M_nu rejected");
+      return FIT_ECUDA;
+    }
+  }
+  {
+    cuuint64_t dims[3] = {6 * (cuuint64_t)g->nxp, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
+    cuuint64_t rowb = 6 * sizeof(T) * (cuuint64_t)g->nxp;
+    cuuint64_t str[2] = {rowb, rowb * g->ny};
+    cuuint32_t box[3] = {6 * TX, TY, 1};
+    if (!encode(&mek, cdt, 3, ek, dims, str, box)) {
+      fit_set_error("fused apply: tensor map of M_eps/M_kappa rejected");
+      return FIT_ECUDA;
+    }
+  }
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)g->nxp, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
+    cuuint64_t str[2] = {(cuuint64_t)g->nxp, (cuuint64_t)g->nxp * g->ny};
+    cuuint32_t box[3] = {TX + 32, TY + 2, 1};
+    if (!encode(&mmask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, g->mask, dims, str, box)) {
+      fit_set_error("fused apply: tensor map of the mask rejected");
+      return FIT_ECUDA;
+    }
+  }
+  FusedArgs<T> a;
+  a.x = (const typename cplx<T>::t*)x;
+  a.y = (typename cplx<T>::t*)y;
+  a.omega = omega_dev;
+  a.err = g->err_dev;
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nz = g->nz;
+  a.tz = tz;
+  a.nzc = (g->nz + tz - 1) / tz;
+  a.ne = g->ne;
+  a.out_scale = (T)out_scale;
+  dim3 block(TX, TY, 1);
+  dim3 grid((g->nx + TX - 1) / TX, (g->ny + TY - 1) / TY, (unsigned)(a.nzc * nbatch));
+  e.nslots = (long long)grid.x * grid.y * a.nzc;
+  const int smem = L::smem(S);
+  auto run = [&](auto kern) -> fit_status {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    kern<<<grid, block, smem, s>>>(mx, mnu, mek, mmask, a, e);
+    FIT_CHECK_CUDA(cudaGetLastError());
+    return FIT_OK;
+  };
+  switch (e.mode) {
+    case FIT_EPI_NONE: return run(fused_apply_kernel<T, TY, FIT_EPI_NONE, S>);
+    case FIT_EPI_DOT_U: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_U, S>);
+    case FIT_EPI_DOT_TS: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_TS, S>);
+    case FIT_EPI_RESID: return run(fused_apply_kernel<T, TY, FIT_EPI_RESID, S>);
+  }
+  fit_set_error("fused apply: unknown epilogue");
+  return FIT_EINVAL;
+}
+
+template <typename T>
+fit_status launch_fused(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
+                        const T* ek, double out_scale, cudaStream_t s, fit_epi& e, const Variant& v) {
+  if (v.ty == 4 && v.stages == 4) return launch_variant<T, 4, 4>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+  if (v.ty == 8 && v.stages == 4) return launch_variant<T, 8, 4>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+  if (v.ty == 16 && v.stages == 3) return launch_variant<T, 16, 3>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+  if (v.ty == 4 && v.stages == 3) return launch_variant<T, 4, 3>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+  if (v.ty == 8 && v.stages == 3) return launch_variant<T, 8, 3>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+  if constexpr (sizeof(T) == 4) {  // deeper rings: more planes in flight per CTA (complex64 only)
+    if (v.ty == 4 && v.stages == 6) return launch_variant<T, 4, 6>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+    if (v.ty == 4 && v.stages == 8) return launch_variant<T, 4, 8>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+    if (v.ty == 8 && v.stages == 6) return launch_variant<T, 8, 6>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+  }
+  fit_set_error("fused apply: no such variant");
+  return FIT_EINVAL;
+}
+
+const Variant* variants(fit_prec prec, int* n) {
+  if (prec == FIT_C64) {
+    *n = (int)(sizeof(kVariants64) / sizeof(Variant));
+    return kVariants64;
+  }
+  *n = (int)(sizeof(kVariants128) / sizeof(Variant));
+  return kVariants128;
+}
+
+// Kernel selection override for tests and experiments: FIT_APPLY_KERNEL=generic forces the generic
+// kernel, FIT_APPLY_KERNEL=fused:<k> forces fused variant k.  Returns 0 (automatic), 1 (generic)
+// or 2 (fused; *variant set).
+int kernel_override(int* variant) {
+  const char* s = getenv("FIT_APPLY_KERNEL");
+  *variant = 0;
+  if (!s) return 0;
+  if (!strcmp(s, "generic")) return 1;
+  if (!strncmp(s, "fused", 5)) {
+    if (s[5] == ':') *variant = atoi(s + 6);
+    return 2;
+  }
+  return 0;
+}
+
+bool fused_supported(const fit_grid* g, fit_prec prec) {
+  // copies of x start on 16-byte boundaries only if a grid row holds a whole number of 16-byte units
+  if (prec == FIT_C64 && (g->nx % 2) != 0) return false;
+  return encoder() != nullptr;
+}
+
+bool fused_fits(const fit_grid* g, int nbatch, const Variant& v) {
+  return (long long)((g->nz + v.tz - 1) / v.tz) * nbatch <= 65535;
+}
+
+}  // namespace
+
+fit_status fit_launch_apply_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                                    fit_prec prec, double out_scale, cudaStream_t s, fit_epi* epi);
+long long fit_apply_partials_generic(const fit_grid* g);
+
+long long fit_apply_partials(const fit_grid* g, fit_prec prec) {
+  long long best = fit_apply_partials_generic(g);
+  int n = 0;
+  const Variant* v = variants(prec, &n);
+  for (int k = 0; k < n; ++k) {
+    long long p = (long long)((g->nx + TX - 1) / TX) * ((g->ny + v[k].ty - 1) / v[k].ty) * ((g->nz + v[k].tz - 1) / v[k].tz);
+    best = std::max(best, p);
+  }
+  return best;
+}
+
+static fit_status launch_choice(fit_grid* g, int choice, int nbatch, const double* omega_dev, const void* x, void* y,
+                                fit_prec prec, double out_scale, cudaStream_t s, fit_epi& e) {
+  if (choice < 0) return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, &e);
+  int n = 0;
+  const Variant* v = variants(prec, &n);
+  if (choice >= n || !fused_fits(g, nbatch, v[choice]))
+    return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, &e);
+  if (prec == FIT_C64) return launch_fused<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, out_scale, s, e, v[choice]);
+  return launch_fused<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, out_scale, s, e, v[choice]);
+}
+
+// Autotuner: time every candidate (and the generic kernel) on the caller's buffers, keep the
+// fastest per (precision, batch).  Runs on the first apply with a new key outside stream capture.
+fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, fit_prec prec,
+                          cudaStream_t s) {
+  const long long key = (long long)nbatch * 2 + (prec == FIT_C64 ? 0 : 1);
+  if (g->tuned.count(key)) return FIT_OK;
+  if (!fused_supported(g, prec)) {
+    g->tuned[key] = -1;
+    return FIT_OK;
+  }
+  int n = 0;
+  variants(prec, &n);
+  cudaEvent_t e0, e1;
+  FIT_CHECK_CUDA(cudaEventCreate(&e0));
+  FIT_CHECK_CUDA(cudaEventCreate(&e1));
+  fit_epi none;
+  float best_ms = 1e30f;
+  int best = -1;
+  for (int c = -1; c < n; ++c) {
+    fit_status st = launch_choice(g, c, nbatch, omega_dev, x, y, prec, 1.0, s, none);  // warm-up
+    if (st != FIT_OK) continue;
+    float tmin = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, s);
+      launch_choice(g, c, nbatch, omega_dev, x, y, prec, 1.0, s, none);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (tmin < best_ms) {
+      best_ms = tmin;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  g->tuned[key] = best;
+  return FIT_OK;
+}
+
+fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, fit_prec prec,
+                            double out_scale, cudaStream_t s, fit_epi* epi) {
+  fit_epi local;
+  fit_epi& e = epi ? *epi : local;
+  int forced = 0;
+  const int ov = kernel_override(&forced);
+  const bool aligned = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+  if (ov == 1 || !aligned || !fused_supported(g, prec))
+    return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, &e);
+  if (ov == 2) return launch_choice(g, forced, nbatch, omega_dev, x, y, prec, out_scale, s, e);
+  const long long key = (long long)nbatch * 2 + (prec == FIT_C64 ? 0 : 1);
+  auto it = g->tuned.find(key);
+  if (it == g->tuned.end()) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusNone && epi == nullptr) {
+      fit_status st = fit_tune_apply(g, nbatch, omega_dev, x, y, prec, s);
+      if (st != FIT_OK) return st;
+      it = g->tuned.find(key);
+    }
+  }
+  const int choice = it != g->tuned.end() ? it->second : 0;
+  return launch_choice(g, choice, nbatch, omega_dev, x, y, prec, out_scale, s, e);
+}
+
+int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out4) {
+  const long long key = (long long)nbatch * 2 + (prec == FIT_C64 ? 0 : 1);
+  auto it = g->tuned.find(key);
+  int c = it == g->tuned.end() ? -2 : it->second;
+  out4[0] = c;
+  if (c >= 0) {
+    int n = 0;
+    const Variant* v = variants(prec, &n);
+    out4[1] = TX;
+    out4[2] = v[c].ty;
+    out4[3] = v[c].tz;
+  } else {
+    out4[1] = 32;
+    out4[2] = 8;
+    out4[3] = 1;
+  }
+  return c;
+}
+
+extern "C" {
+
+int fit_apply_variant_count(fit_prec prec) {
+  int n = 0;
+  variants(prec, &n);
+  return n;
+}
+
+fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out4) {
+  FIT_REQUIRE(g && out4 && nbatch >= 1, "fit_apply_tuned: bad argument");
+  fit_tuned_choice(g, prec, nbatch, out4);
+  return FIT_OK;
+}
+
+}  // extern "C"

@@ -203,7 +203,7 @@ void fit_grid_destroy(fit_grid* g) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(g->device);
-  void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev};
+  void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev, g->err_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);
@@ -239,7 +239,8 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
       (st = fit_dev_alloc(g, (void**)&g->ek64, np * 6 * sizeof(double))) ||
       (st = fit_dev_alloc(g, (void**)&g->nu32, np * 3 * sizeof(float))) ||
       (st = fit_dev_alloc(g, (void**)&g->ek32, np * 6 * sizeof(float))) ||
-      (st = fit_dev_alloc(g, (void**)&g->mask, np))) {
+      (st = fit_dev_alloc(g, (void**)&g->mask, np)) ||
+      (st = fit_dev_alloc(g, (void**)&g->err_dev, sizeof(int)))) {
     fit_grid_destroy(g);
     return st;
   }
@@ -251,6 +252,7 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
   cudaMemset(g->nu32, 0, np * 3 * sizeof(float));
   cudaMemset(g->ek32, 0, np * 6 * sizeof(float));
   cudaMemset(g->mask, 0, np);
+  cudaMemset(g->err_dev, 0, sizeof(int));
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     fit_set_error(std::string("fit_grid_create: ") + cudaGetErrorString(e));

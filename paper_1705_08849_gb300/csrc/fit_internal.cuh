@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 
 #include "../../include/fit.h"
@@ -39,9 +40,9 @@ struct fit_grid {
   int omega_cap = 0;
   size_t bytes_held = 0;
   size_t budget = 0;       // 0 = unlimited
-  // autotuned launch shape of the fused c64 apply, keyed by batch (see fit_stencil.cu)
-  int tune_key_batch = -1;
-  int tune_variant = -1;
+  // autotuned apply kernel per (batch, precision): -1 = generic kernel, k >= 0 = fused variant k
+  std::map<long long, int> tuned;
+  int* err_dev = nullptr;  // device error word: a bounded wait in a kernel ran out
 };
 
 // Thread-local last-error message.
@@ -82,12 +83,19 @@ struct fit_epi {
   const void* u = nullptr;
   double* part = nullptr;
   const int* status = nullptr;
+  long long nslots = 0;  // set by the launcher: partial slots per system this launch writes
 };
 
 // Launch the operator apply: y_b = out_scale * A(omega_b) x_b (+ epilogue).  omega_dev is a
 // device array of nbatch angular frequencies.  x/y are float2 (FIT_C64) or double2 (FIT_C128).
 fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                            fit_prec prec, double out_scale, cudaStream_t stream, const fit_epi* epi = nullptr);
+                            fit_prec prec, double out_scale, cudaStream_t stream, fit_epi* epi = nullptr);
+// Time the apply variants for (nbatch, prec) on the given buffers and cache the fastest; no-op if
+// already tuned.  Must not be called while the stream is being captured.
+fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, fit_prec prec,
+                          cudaStream_t s);
+// The cached choice: out4 = {choice (-1 generic, -2 untuned, >= 0 fused variant), TX, TY, TZ}.
+int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out4);
 // Number of partial-sum slots per system that the apply writes for an epilogue.
 long long fit_apply_partials(const fit_grid* g, fit_prec prec);
 

@@ -51,6 +51,10 @@ struct Sys {
   int stagn;           // consecutive refinement steps without residual decrease
   int jlast;           // FGMRES: Arnoldi steps done in the current cycle
   int max_inner;       // inner iteration cap of the current inner solve
+  double rin_min2;     // smallest inner recurrence residual of the current inner solve
+  double rin0;         // inner residual at the start of the current inner solve
+  int rin_min_it;      // iteration at which it was reached
+  int pad_;
 };
 
 struct Ctl {
@@ -71,6 +75,8 @@ struct P {
   int mixed;         // inner precision is complex64
   double s_in;       // A_in = s_in * A
   double tiny;       // breakdown threshold for the inner precision
+  int stall;         // inner solve stops after this many iterations without a new minimum
+  int precond;       // right preconditioner of the inner solve (FIT_PC_*)
 };
 
 __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -151,9 +157,9 @@ struct OpOuter {  // after r = b - A x: q2 = ||r||^2
     s.iters += s.inner_it;
     if (!isfinite(r2)) { s.outer_status = SYS_NAN; return; }
     if (r2 <= s.tol2) { s.outer_status = SYS_CONV; return; }
-    if (r2 < 0.98 * s.best2) { s.best2 = r2; s.stagn = 0; }
+    if (r2 < 0.99 * s.best2) { s.best2 = r2; s.stagn = 0; }
     else s.stagn += 1;
-    if (s.outer >= p.max_outer || s.iters >= p.max_iter || s.stagn >= 3) s.outer_status = SYS_MAXIT;
+    if (s.outer >= p.max_outer || s.iters >= p.max_iter || s.stagn >= 5) s.outer_status = SYS_MAXIT;
   }
 };
 
@@ -170,6 +176,9 @@ struct OpInnerStart {
     s.omega = make_double2(1.0, 0.0);
     s.beta = make_double2(0.0, 0.0);
     s.rin2 = q[0];
+    s.rin_min2 = q[0];
+    s.rin0 = q[0];
+    s.rin_min_it = 0;
     s.corr = p.s_in * s.rscale;
     // relative target of this inner solve: no tighter than needed for the outer tolerance
     double need = 0.5 * sqrt(s.tol2) / s.rscale;
@@ -209,6 +218,15 @@ struct OpRho {  // q0,q1 = <r^, r_new>, q2 = ||r_new||^2
     if (!cfinite(rn) || !isfinite(rr)) { s.inner_status = SYS_NAN; return; }
     if (rr <= s.inner_tol2) { s.inner_status = SYS_CONV; return; }
     if (s.inner_it >= s.max_inner) { s.inner_status = SYS_MAXIT; return; }
+    if (rr < s.rin_min2) { s.rin_min2 = rr; s.rin_min_it = s.inner_it; }
+    // a stalled or diverging inner solve hands back to the refinement loop, which restarts it
+    // from the true residual
+    if (s.inner_it - s.rin_min_it > p.stall || rr > 1e8 * s.rin_min2) {  // 1e4 in norm
+      s.inner_status = SYS_MAXIT;
+      // an inner solve that ends above its starting residual would make x worse: drop it
+      if (rr > s.rin0) s.corr = 0.0;
+      return;
+    }
     if (sqrt(cabs2(rn)) < p.tiny || sqrt(cabs2(s.omega)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
     s.beta = cmul(cdiv(rn, s.rho), cdiv(s.alpha, s.omega));
     s.rho = rn;
@@ -264,10 +282,20 @@ __global__ void __launch_bounds__(256) k_inner_start(const double2* __restrict__
   fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
 }
 
-// BiCGStab: p = r + beta (p - omega v)
+template <typename V>
+__device__ inline V cmulv(V a, V b) {
+  V o;
+  o.x = a.x * b.x - a.y * b.y;
+  o.y = a.x * b.y + a.y * b.x;
+  return o;
+}
+
+// BiCGStab: p = r + beta (p - omega v); with a right preconditioner also p^ = D^-1 p
 template <typename T>
 __global__ void __launch_bounds__(256) k_bicg_p(const typename cplx<T>::t* __restrict__ r, typename cplx<T>::t* pv,
-                                                const typename cplx<T>::t* __restrict__ v, const Sys* __restrict__ sys, P p) {
+                                                const typename cplx<T>::t* __restrict__ v,
+                                                const typename cplx<T>::t* __restrict__ dinv,
+                                                typename cplx<T>::t* phat, const Sys* __restrict__ sys, P p) {
   using V = typename cplx<T>::t;
   const int b = blockIdx.y;
   if (sys[b].inner_status != SYS_RUN) return;
@@ -283,13 +311,15 @@ __global__ void __launch_bounds__(256) k_bicg_p(const typename cplx<T>::t* __res
     o.x = rr.x + br * t.x - bi * t.y;
     o.y = rr.y + br * t.y + bi * t.x;
     pv[off + e] = o;
+    if (dinv) phat[off + e] = cmulv(dinv[off + e], o);
   }
 }
 
-// BiCGStab: s = r - alpha v (in place in r)
+// BiCGStab: s = r - alpha v (in place in r); with a right preconditioner also s^ = D^-1 s
 template <typename T>
 __global__ void __launch_bounds__(256) k_bicg_s(typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ v,
-                                                const Sys* __restrict__ sys, P p) {
+                                                const typename cplx<T>::t* __restrict__ dinv,
+                                                typename cplx<T>::t* shat, const Sys* __restrict__ sys, P p) {
   using V = typename cplx<T>::t;
   const int b = blockIdx.y;
   if (sys[b].inner_status != SYS_RUN) return;
@@ -300,13 +330,58 @@ __global__ void __launch_bounds__(256) k_bicg_s(typename cplx<T>::t* r, const ty
     rr.x -= ar * vv.x - ai * vv.y;
     rr.y -= ar * vv.y + ai * vv.x;
     r[off + e] = rr;
+    if (dinv) shat[off + e] = cmulv(dinv[off + e], rr);
   }
+}
+
+// D^-1 of the Jacobi preconditioner per system: diag(A_in(w_b)) = nusum - w^2 M_eps + j w M_kappa
+// (the Eq. Precond column-sum construction on the unsymmetrised operator); masked edges: 1
+template <typename T>
+__global__ void __launch_bounds__(256) k_dinv(const T* __restrict__ nusum, const T* __restrict__ ek,
+                                              const uint8_t* __restrict__ mask, const double* __restrict__ omega,
+                                              int nx, int ny, int nxp, typename cplx<T>::t* dinv, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  const double w = omega[b];
+  const long long off = (long long)b * p.ne;
+  VEC_LOOP(p) {
+    long long c = e / 3;
+    int q = (int)(e - 3 * c);
+    long long i = c % nx, jj = (c / nx) % ny, k = c / ((long long)nx * ny);
+    long long cp = i + (long long)nxp * (jj + (long long)ny * k);
+    V o;
+    if ((mask[cp] >> q) & 1) {
+      o.x = T(1);
+      o.y = T(0);
+    } else {
+      double dr = (double)nusum[e] - w * w * (double)ek[6 * cp + q];
+      double di = w * (double)ek[6 * cp + 3 + q];
+      double den = dr * dr + di * di;
+      o.x = (T)(dr / den);
+      o.y = (T)(-di / den);
+    }
+    dinv[off + e] = o;
+  }
+}
+
+// z = D^-1 v for FGMRES basis vector j
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_precond_diag(const typename cplx<T>::t* __restrict__ Vb,
+                                                         typename cplx<T>::t* Zb, int j,
+                                                         const typename cplx<T>::t* __restrict__ dinv,
+                                                         const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long vs = (long long)p.B * p.ne;
+  const long long off = (long long)b * p.ne;
+  VEC_LOOP(p) { Zb[(long long)j * vs + off + e] = cmulv(dinv[off + e], Vb[(long long)j * vs + off + e]); }
 }
 
 // BiCGStab: d += alpha p + omega s; r = s - omega t; q0,q1 = <r^, r>, q2 = ||r||^2
 template <typename T>
 __global__ void __launch_bounds__(256) k_bicg_xr(typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ pv,
                                                  typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ t,
+                                                 const typename cplx<T>::t* __restrict__ shat,
                                                  const typename cplx<T>::t* __restrict__ rhat, const Sys* __restrict__ sys,
                                                  double* part, P p) {
   using V = typename cplx<T>::t;
@@ -317,8 +392,9 @@ __global__ void __launch_bounds__(256) k_bicg_xr(typename cplx<T>::t* d, const t
   T acc[3] = {T(0), T(0), T(0)};
   VEC_LOOP(p) {
     V s = r[off + e], pp = pv[off + e], tt = t[off + e], dd = d[off + e], rh = rhat[off + e];
-    dd.x += (ar * pp.x - ai * pp.y) + (orr * s.x - oi * s.y);
-    dd.y += (ar * pp.y + ai * pp.x) + (orr * s.y + oi * s.x);
+    const V sx = shat ? shat[off + e] : s;  // the update uses the preconditioned s
+    dd.x += (ar * pp.x - ai * pp.y) + (orr * sx.x - oi * sx.y);
+    dd.y += (ar * pp.y + ai * pp.x) + (orr * sx.y + oi * sx.x);
     V rn;
     rn.x = s.x - (orr * tt.x - oi * tt.y);
     rn.y = s.y - (orr * tt.y + oi * tt.x);
@@ -327,6 +403,25 @@ __global__ void __launch_bounds__(256) k_bicg_xr(typename cplx<T>::t* d, const t
     acc[0] += rh.x * rn.x + rh.y * rn.y;
     acc[1] += rh.x * rn.y - rh.y * rn.x;
     acc[2] += rn.x * rn.x + rn.y * rn.y;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// q0,q1 = <t, s>, q2 = <t, t> (BiCGStab omega with a right preconditioner)
+template <typename T>
+__global__ void __launch_bounds__(256) k_dots_ts(const typename cplx<T>::t* __restrict__ t,
+                                                 const typename cplx<T>::t* __restrict__ sv, const Sys* __restrict__ sys,
+                                                 double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    V tt = t[off + e], ss = sv[off + e];
+    acc[0] += tt.x * ss.x + tt.y * ss.y;
+    acc[1] += tt.x * ss.y - tt.y * ss.x;
+    acc[2] += tt.x * tt.x + tt.y * tt.y;
   }
   fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
 }
@@ -369,50 +464,77 @@ __device__ inline void warp_accum(T re, T im, double* slot_re, double* slot_im) 
 // mode 0: h_i = <V_i, w>                      (partials of 2(j+1) values)
 // mode 1: w -= sum_i h_i V_i, then h2_i = <V_i, w>
 // mode 2: w -= sum_i h2_i V_i, then q0 = ||w||^2
-template <typename T, int MODE>
+// MAXV >= j+1 basis vectors are handled with fully unrolled, predicated loops: every V_i load of
+// an element is issued before it is used (one trip's loads all in flight) and the per-vector dot
+// accumulators stay in registers until a single warp reduction at the end.
+template <typename T, int MODE, int MAXV>
 __global__ void __launch_bounds__(256) k_fg_ortho(const typename cplx<T>::t* __restrict__ Vb, int j,
                                                   const double* __restrict__ hcoef, const Sys* __restrict__ sys,
                                                   double* part, P p) {
   using V = typename cplx<T>::t;
   const int b = blockIdx.y;
   if (sys[b].inner_status != SYS_RUN) return;
-  __shared__ double red[8][2 * FG_MAXV];
-  const int warp = threadIdx.x >> 5;
+  __shared__ double red[8][2 * MAXV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nv = j + 1;
-  for (int q = threadIdx.x; q < 8 * 2 * FG_MAXV; q += 256) (&red[0][0])[q] = 0.0;
-  __syncthreads();
   const long long vs = (long long)p.B * p.ne;  // stride between basis vectors
   const long long off = (long long)b * p.ne;
   V* w = (V*)(Vb + (long long)(j + 1) * vs + off);
-  // The element loop runs a whole-warp trip count so that shuffles see full warps.
-  const long long stride = (long long)gridDim.x * 256;
-  for (long long base = blockIdx.x * 256LL; base < p.ne; base += stride) {
-    const long long e = base + threadIdx.x;
-    const bool ok = e < p.ne;
-    V wv = ok ? w[e] : czero<V>();
+  __shared__ T hs[2 * MAXV];  // projection coefficients, read as broadcasts
+  if (MODE >= 1) {
+    const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
+    for (int q = threadIdx.x; q < 2 * MAXV; q += 256) hs[q] = q < 2 * nv ? (T)hc[q] : T(0);
+    __syncthreads();
+  }
+  T ar[MAXV], ai[MAXV];
+#pragma unroll
+  for (int i = 0; i < MAXV; ++i) {
+    ar[i] = T(0);
+    ai[i] = T(0);
+  }
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < p.ne; e += (long long)gridDim.x * 256) {
+    V vi[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) vi[i] = i < nv ? Vb[(long long)i * vs + off + e] : czero<V>();
+    V wv = w[e];
     if (MODE >= 1) {
-      const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
-      for (int i = 0; i < nv; ++i) {
-        V vi = ok ? Vb[(long long)i * vs + off + e] : czero<V>();
-        T hr = (T)hc[2 * i], hi = (T)hc[2 * i + 1];
-        wv.x -= hr * vi.x - hi * vi.y;
-        wv.y -= hr * vi.y + hi * vi.x;
+#pragma unroll
+      for (int i = 0; i < MAXV; ++i) {
+        const T hr = hs[2 * i], hi = hs[2 * i + 1];
+        wv.x -= hr * vi[i].x - hi * vi[i].y;
+        wv.y -= hr * vi[i].y + hi * vi[i].x;
       }
-      if (ok) w[e] = wv;
+      w[e] = wv;
     }
     if (MODE <= 1) {
-      for (int i = 0; i < nv; ++i) {
-        V vi = ok ? Vb[(long long)i * vs + off + e] : czero<V>();
-        warp_accum<T>(vi.x * wv.x + vi.y * wv.y, vi.x * wv.y - vi.y * wv.x, &red[warp][2 * i], &red[warp][2 * i + 1]);
+#pragma unroll
+      for (int i = 0; i < MAXV; ++i) {
+        ar[i] += vi[i].x * wv.x + vi[i].y * wv.y;
+        ai[i] += vi[i].x * wv.y - vi[i].y * wv.x;
       }
     } else {
-      warp_accum<T>(wv.x * wv.x + wv.y * wv.y, T(0), &red[warp][0], &red[warp][1]);
+      ar[0] += wv.x * wv.x + wv.y * wv.y;
+    }
+  }
+  const int nq = MODE <= 1 ? nv : 1;
+#pragma unroll
+  for (int i = 0; i < MAXV; ++i) {
+    if (i < nq) {
+      T x = ar[i], y = ai[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) {
+        red[warp][2 * i] = (double)x;
+        red[warp][2 * i + 1] = (double)y;
+      }
     }
   }
   __syncthreads();
-  const int nq = MODE <= 1 ? 2 * nv : 2;
   double* out = part + PSLOT(p, b);
-  for (int q = threadIdx.x; q < nq; q += 256) {
+  for (int q = threadIdx.x; q < 2 * nq; q += 256) {
     double s = 0.0;
     for (int w8 = 0; w8 < 8; ++w8) s += red[w8][q];
     out[q] = s;
@@ -496,37 +618,6 @@ __global__ void __launch_bounds__(256) k_fg_scale(typename cplx<T>::t* Vb, int j
   }
 }
 
-// Jacobi right preconditioner z = v / diag(A_in(w)), diag = nusum - w^2 M_eps + j w M_kappa
-template <typename T>
-__global__ void __launch_bounds__(256) k_fg_jacobi(const typename cplx<T>::t* __restrict__ Vb,
-                                                   typename cplx<T>::t* Zb, int j, const T* __restrict__ nusum,
-                                                   const T* __restrict__ ek, const uint8_t* __restrict__ mask,
-                                                   const double* __restrict__ omega, int nx, int ny, int nxp,
-                                                   const Sys* __restrict__ sys, P p) {
-  using V = typename cplx<T>::t;
-  const int b = blockIdx.y;
-  if (sys[b].inner_status != SYS_RUN) return;
-  const long long vs = (long long)p.B * p.ne;
-  const V* v = Vb + (long long)j * vs + (long long)b * p.ne;
-  V* z = Zb + (long long)j * vs + (long long)b * p.ne;
-  const double w = omega[b];
-  VEC_LOOP(p) {
-    long long c = e / 3;
-    int q = (int)(e - 3 * c);
-    long long i = c % nx, jj = (c / nx) % ny, k = c / ((long long)nx * ny);
-    long long cp = i + (long long)nxp * (jj + (long long)ny * k);
-    V vv = v[e];
-    if ((mask[cp] >> q) & 1) { z[e] = vv; continue; }
-    double dr = (double)nusum[e] - w * w * (double)ek[6 * cp + q];
-    double di = w * (double)ek[6 * cp + 3 + q];
-    double den = dr * dr + di * di;
-    V o;
-    o.x = (T)((vv.x * dr + vv.y * di) / den);
-    o.y = (T)((vv.y * dr - vv.x * di) / den);
-    z[e] = o;
-  }
-}
-
 // back substitution H y = g on the rotated (upper triangular) Hessenberg, then d = sum y_i Z_i
 __global__ void k_fg_solve(const double* __restrict__ H, const double* __restrict__ G, double* Y, const Sys* sys, P p) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -546,7 +637,7 @@ __global__ void k_fg_solve(const double* __restrict__ H, const double* __restric
   for (int i = n; i < m; ++i) y[i] = make_double2(0.0, 0.0);
 }
 
-template <typename T>
+template <typename T, int MAXV>
 __global__ void __launch_bounds__(256) k_fg_combine(const typename cplx<T>::t* __restrict__ Zb, typename cplx<T>::t* d,
                                                     const double* __restrict__ Y, const Sys* __restrict__ sys, P p) {
   using V = typename cplx<T>::t;
@@ -556,13 +647,21 @@ __global__ void __launch_bounds__(256) k_fg_combine(const typename cplx<T>::t* _
   const long long vs = (long long)p.B * p.ne;
   const long long off = (long long)b * p.ne;
   const double* y = Y + (long long)b * 2 * FG_MAXV;
+  T yr[MAXV], yi[MAXV];
+#pragma unroll
+  for (int i = 0; i < MAXV; ++i) {
+    yr[i] = i < n ? (T)y[2 * i] : T(0);
+    yi[i] = i < n ? (T)y[2 * i + 1] : T(0);
+  }
   VEC_LOOP(p) {
     V acc = czero<V>();
-    for (int i = 0; i < n; ++i) {
-      V zi = Zb[(long long)i * vs + off + e];
-      T yr = (T)y[2 * i], yi = (T)y[2 * i + 1];
-      acc.x += yr * zi.x - yi * zi.y;
-      acc.y += yr * zi.y + yi * zi.x;
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) {
+      if (i < n) {
+        V zi = Zb[(long long)i * vs + off + e];
+        acc.x += yr[i] * zi.x - yi[i] * zi.y;
+        acc.y += yr[i] * zi.y + yi[i] * zi.x;
+      }
     }
     d[off + e] = acc;
   }
@@ -641,6 +740,8 @@ struct Work {
   void* Vb = nullptr;     // FGMRES basis (m+1 vectors)
   void* Zb = nullptr;     // FGMRES preconditioned vectors (m), or aliases Vb
   void* nusum = nullptr;
+  void* dinv = nullptr;   // Jacobi D^-1 per system (inner precision)
+  void *phat = nullptr, *shat = nullptr;  // BiCGStab: preconditioned p and s
   double *part_apply = nullptr, *part_vec = nullptr;
   long long napply = 0;
   double *h1 = nullptr, *h2 = nullptr, *H = nullptr, *G = nullptr, *CS = nullptr, *SN = nullptr, *Y = nullptr;
@@ -662,9 +763,9 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   size_t esz = mixed ? 8 : 16;
   size_t vec = ne * B * esz;
   size_t bytes = ne * B * 16;  // r128
-  if (method == FIT_BICGSTAB) bytes += 6 * vec;
+  if (method == FIT_BICGSTAB) bytes += 6 * vec + (pc != FIT_PC_NONE ? 2 * vec : 0);
   else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
-  if (pc == FIT_PC_JACOBI) bytes += ne * esz / 2;
+  if (pc == FIT_PC_JACOBI) bytes += ne * esz / 2 + vec;
   size_t napply = (size_t)std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
   bytes += (size_t)B * napply * 4 * 8;
   bytes += (size_t)B * 1216 * 2 * FG_MAXV * 8;
@@ -691,6 +792,10 @@ fit_status setup(Work& w, int B) {
     ALLOC(w.v, vec);
     ALLOC(w.t, vec);
     ALLOC(w.d, vec);
+    if (w.pc != FIT_PC_NONE) {
+      ALLOC(w.phat, vec);
+      ALLOC(w.shat, vec);
+    }
   } else {
     ALLOC(w.Vb, (size_t)(w.m + 1) * vec);
     if (w.pc != FIT_PC_NONE) {
@@ -701,7 +806,10 @@ fit_status setup(Work& w, int B) {
     ALLOC(w.d, vec);
     w.rin = w.Vb;  // V0 holds r~
   }
-  if (w.pc == FIT_PC_JACOBI) ALLOC(w.nusum, ne * w.esz / 2);
+  if (w.pc == FIT_PC_JACOBI) {
+    ALLOC(w.nusum, ne * w.esz / 2);
+    ALLOC(w.dinv, vec);
+  }
   w.napply = std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
   ALLOC(w.part_apply, (size_t)B * w.napply * 4 * sizeof(double));
   int nblk = std::max(8, std::min(1216, (int)((ne + 255) / 256)));
@@ -731,6 +839,8 @@ fit_status setup(Work& w, int B) {
   w.p.mixed = w.mixed;
   w.p.s_in = w.mixed ? g->coef_scale : 1.0;
   w.p.tiny = w.mixed ? 1e-30 : 1e-300;
+  w.p.stall = 1000;
+  w.p.precond = w.pc;
   if (w.pc == FIT_PC_JACOBI) {
     long long nc = g->ncell;
     if (w.mixed)
@@ -763,15 +873,20 @@ struct Seq {
     fin_kernel<NQ, Op><<<w.p.B, 256, 0, s>>>(part, nslots, stride, w.sys, w.p, op);
     check();
   }
-  void apply(const void* xin, void* yout, int mode, const void* u, fit_prec prec, const int* status_field) {
+  // launches the apply and returns the number of partial slots per system it writes
+  long long apply(const void* xin, void* yout, int mode, const void* u, fit_prec prec, const int* status_field) {
     fit_epi e;
     e.mode = mode;
     e.u = u;
     e.part = w.part_apply;
     e.status = status_field;
-    double scale = 1.0;
-    fit_status r = fit_launch_apply(w.g, w.p.B, w.omega, xin, yout, prec, scale, s, &e);
+    fit_status r = fit_launch_apply(w.g, w.p.B, w.omega, xin, yout, prec, 1.0, s, &e);
     if (r != FIT_OK && st == FIT_OK) st = r;
+    if (e.nslots > w.napply && st == FIT_OK) {
+      fit_set_error("fit_solve: apply wrote more partial slots than were allocated");
+      st = FIT_ECUDA;
+    }
+    return e.nslots;
   }
   cudaGraphConditionalHandle h_inner = 0;  // set when the inner loop is a graph WHILE node
   int use_h_inner = 0;
@@ -806,18 +921,40 @@ struct Seq {
   template <typename T>
   void bicg_iter(const int* st_inner) {
     using V = typename cplx<T>::t;
-    k_bicg_p<T><<<vgrid(), 256, 0, s>>>((const V*)w.rin, (V*)w.pv, (const V*)w.v, w.sys, w.p);
+    const bool pc = w.dinv != nullptr;
+    k_bicg_p<T><<<vgrid(), 256, 0, s>>>((const V*)w.rin, (V*)w.pv, (const V*)w.v, (const V*)w.dinv, (V*)w.phat,
+                                        w.sys, w.p);
     check();
-    apply(w.pv, w.v, FIT_EPI_DOT_U, w.rhat, w.inner, st_inner);
-    fin<3>(w.part_apply, w.napply, 4, OpAlpha{});
-    k_bicg_s<T><<<vgrid(), 256, 0, s>>>((V*)w.rin, (const V*)w.v, w.sys, w.p);
+    long long n1 = apply(pc ? w.phat : w.pv, w.v, FIT_EPI_DOT_U, w.rhat, w.inner, st_inner);
+    fin<3>(w.part_apply, n1, 4, OpAlpha{});
+    k_bicg_s<T><<<vgrid(), 256, 0, s>>>((V*)w.rin, (const V*)w.v, (const V*)w.dinv, (V*)w.shat, w.sys, w.p);
     check();
-    apply(w.rin, w.t, FIT_EPI_DOT_TS, nullptr, w.inner, st_inner);
-    fin<3>(w.part_apply, w.napply, 4, OpOmega{});
-    k_bicg_xr<T><<<vgrid(), 256, 0, s>>>((V*)w.d, (const V*)w.pv, (V*)w.rin, (const V*)w.t, (const V*)w.rhat, w.sys,
-                                         w.part_vec, w.p);
+    // <t, s> and <t, t> with t = A s^: the epilogue's <y, x> uses the apply input, so with a
+    // preconditioner the dots are taken in k_bicg_dots_ts instead
+    long long n2 = apply(pc ? w.shat : w.rin, w.t, pc ? FIT_EPI_NONE : FIT_EPI_DOT_TS, nullptr, w.inner, st_inner);
+    if (pc) {
+      k_dots_ts<T><<<vgrid(), 256, 0, s>>>((const V*)w.t, (const V*)w.rin, w.sys, w.part_vec, w.p);
+      check();
+      fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpOmega{});
+    } else {
+      fin<3>(w.part_apply, n2, 4, OpOmega{});
+    }
+    k_bicg_xr<T><<<vgrid(), 256, 0, s>>>((V*)w.d, (const V*)(pc ? w.phat : w.pv), (V*)w.rin, (const V*)w.t,
+                                         (const V*)(pc ? w.shat : nullptr), (const V*)w.rhat, w.sys, w.part_vec, w.p);
     check();
     fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpRho{});
+  }
+
+  // CGS2 pass over V[0..j]; the unrolled width is the smallest of 8/16/32/64 that holds j+1
+  template <typename T, int MODE>
+  void ortho(int j, const double* h) {
+    using V = typename cplx<T>::t;
+    const int nv = j + 1;
+    if (nv <= 8) k_fg_ortho<T, MODE, 8><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    else if (nv <= 16) k_fg_ortho<T, MODE, 16><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    else if (nv <= 32) k_fg_ortho<T, MODE, 32><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    else k_fg_ortho<T, MODE, 64><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    check();
   }
 
   // Arnoldi step j of FGMRES (predicated on inner status)
@@ -829,24 +966,18 @@ struct Seq {
     char* wj1 = (char*)w.Vb + (size_t)(j + 1) * vecb;
     const void* zin = vj;
     if (w.pc == FIT_PC_JACOBI) {
-      const fit_grid* g = w.g;
-      k_fg_jacobi<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const T*)w.nusum,
-                                             w.mixed ? (const T*)g->ek32 : (const T*)g->ek64, g->mask, w.omega, g->nx,
-                                             g->ny, g->nxp, w.sys, w.p);
+      k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
     }
     apply(zin, wj1, FIT_EPI_NONE, nullptr, w.inner, st_inner);
-    k_fg_ortho<T, 0><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, nullptr, w.sys, w.part_vec, w.p);
-    check();
+    ortho<T, 0>(j, nullptr);
     k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h1, w.sys, w.p);
     check();
-    k_fg_ortho<T, 1><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, w.h1, w.sys, w.part_vec, w.p);
-    check();
+    ortho<T, 1>(j, w.h1);
     k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h2, w.sys, w.p);
     check();
-    k_fg_ortho<T, 2><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, w.h2, w.sys, w.part_vec, w.p);
-    check();
+    ortho<T, 2>(j, w.h2);
     k_fg_givens<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.part_vec, j, w.h1, w.h2, w.H, w.G, w.CS, w.SN, w.sys, w.p);
     check();
     k_fg_scale<T><<<vgrid(), 256, 0, s>>>((V*)w.Vb, j, w.sys, w.p);
@@ -858,7 +989,9 @@ struct Seq {
     using V = typename cplx<T>::t;
     k_fg_solve<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.H, w.G, w.Y, w.sys, w.p);
     check();
-    k_fg_combine<T><<<vgrid(), 256, 0, s>>>((const V*)w.Zb, (V*)w.d, w.Y, w.sys, w.p);
+    if (w.m <= 16) k_fg_combine<T, 16><<<vgrid(), 256, 0, s>>>((const V*)w.Zb, (V*)w.d, w.Y, w.sys, w.p);
+    else if (w.m <= 32) k_fg_combine<T, 32><<<vgrid(), 256, 0, s>>>((const V*)w.Zb, (V*)w.d, w.Y, w.sys, w.p);
+    else k_fg_combine<T, 64><<<vgrid(), 256, 0, s>>>((const V*)w.Zb, (V*)w.d, w.Y, w.sys, w.p);
     check();
   }
 
@@ -867,8 +1000,8 @@ struct Seq {
     using V = typename cplx<T>::t;
     k_update_x<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.sys, w.p);
     check();
-    apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
-    fin<3>(w.part_apply, fit_apply_partials(w.g, FIT_C128), 4, OpOuter{});
+    long long n3 = apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
+    fin<3>(w.part_apply, n3, 4, OpOuter{});
   }
 
   void cond(int which, int guard_max, cudaGraphConditionalHandle h, int use_handle) {
@@ -896,6 +1029,22 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
   if ((st = w.alloc((void**)&st_inner, w.p.B * sizeof(int))) != FIT_OK) return st;
   if ((st = w.alloc((void**)&st_outer, w.p.B * sizeof(int))) != FIT_OK) return st;
   Seq q{w, rhs, x, s};
+  if (w.pc == FIT_PC_JACOBI) {  // D^-1 per system, once per solve
+    const fit_grid* g = w.g;
+    k_dinv<T><<<dim3(w.p.nblk, w.p.B), 256, 0, s>>>((const T*)w.nusum, w.mixed ? (const T*)g->ek32 : (const T*)g->ek64,
+                                                     g->mask, w.omega, g->nx, g->ny, g->nxp,
+                                                     (typename cplx<T>::t*)w.dinv, w.p);
+    FIT_CHECK_CUDA(cudaGetLastError());
+  }
+  // pick the apply kernels (autotuner) now: timing cannot run inside a stream capture
+  {
+    void* ti = w.method == FIT_BICGSTAB ? w.pv : w.Vb;
+    void* to = w.method == FIT_BICGSTAB ? w.v : w.d;
+    FIT_CHECK_CUDA(cudaMemsetAsync(ti, 0, (size_t)w.p.ne * w.p.B * w.esz, s));
+    fit_status ts = fit_tune_apply(w.g, w.p.B, w.omega, ti, to, w.inner, s);
+    if (ts == FIT_OK) ts = fit_tune_apply(w.g, w.p.B, w.omega, rhs, w.r128, FIT_C128, s);
+    if (ts != FIT_OK) return ts;
+  }
   auto mirror = [&](cudaStream_t ss) {
     k_mirror_status<<<(w.p.B + 127) / 128, 128, 0, ss>>>(w.sys, st_inner, st_outer, w.p.B);
   };
@@ -925,6 +1074,7 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
         for (int it = 0; it < max_inner_guard; ++it) {
           q.bicg_iter<T>(st_inner);
           mirror(s);
+          if (it % 100 == 99) dump("bicg it", it + 1);
           q.cond(0, max_inner_guard, 0, 0);
           FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
           FIT_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -1095,8 +1245,6 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
               "fit_solve: FGMRES restart must be in 1..64");
   FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET,
               "fit_solve: unknown preconditioner");
-  FIT_REQUIRE(o.precond == FIT_PC_NONE || o.method == FIT_FGMRES,
-              "fit_solve: preconditioners are applied inside FGMRES only");
   FIT_REQUIRE(o.precond != FIT_PC_UNET, "fit_solve: no learned preconditioner is loaded");
   FIT_REQUIRE(o.max_iter >= 1 && o.max_outer >= 1, "fit_solve: iteration caps must be >= 1");
   FIT_REQUIRE(o.inner_tol > 0 && o.inner_tol < 1, "fit_solve: inner_tol must be in (0, 1)");

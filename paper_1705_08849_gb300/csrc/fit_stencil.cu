@@ -161,18 +161,10 @@ long long fit_apply_partials_generic(const fit_grid* g) {
 }
 
 fit_status fit_launch_apply_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                                    fit_prec prec, double out_scale, cudaStream_t s, const fit_epi* epi) {
+                                    fit_prec prec, double out_scale, cudaStream_t s, fit_epi* epi) {
+  if (epi) epi->nslots = fit_apply_partials_generic(g);
   if (prec == FIT_C64)
     return launch_generic<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, out_scale, s, epi);
   return launch_generic<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, out_scale, s, epi);
 }
 
-long long fit_apply_partials(const fit_grid* g, fit_prec prec) {
-  (void)prec;
-  return fit_apply_partials_generic(g);
-}
-
-fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
-                            fit_prec prec, double out_scale, cudaStream_t s, const fit_epi* epi) {
-  return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, epi);
-}

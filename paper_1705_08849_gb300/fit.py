@@ -67,6 +67,10 @@ def lib():
         L.fit_grid_destroy.restype = None
         L.fit_status_str.argtypes = [i]
         L.fit_status_str.restype = ct.c_char_p
+        L.fit_apply_variant_count.argtypes = [i]
+        L.fit_apply_variant_count.restype = ct.c_int
+        L.fit_apply_tuned.argtypes = [vp, i, i, ct.POINTER(ct.c_int)]
+        L.fit_apply_tuned.restype = ct.c_int
         L.fit_last_error.argtypes = []
         L.fit_last_error.restype = ct.c_char_p
         for name in ("fit_grid_create", "fit_set_materials", "fit_set_material_matrices", "fit_apply", "fit_solve",
@@ -186,6 +190,18 @@ def fit_solve(g, omega, rhs, x, tol, opts=None, **kw):
         _check(st, "fit_solve")
     return st, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres, seconds=r.seconds)
                 for r in reps]
+
+
+def fit_apply_variant_count(prec):
+    return int(lib().fit_apply_variant_count(prec))
+
+
+def fit_apply_tuned(g, prec, nbatch):
+    """The autotuner's pick for (prec, nbatch): dict(choice, tx, ty, tz); choice -1 = generic kernel,
+    -2 = not tuned yet, k >= 0 = fused variant k."""
+    out = (ct.c_int * 4)()
+    _check(lib().fit_apply_tuned(g, prec, nbatch, out), "fit_apply_tuned")
+    return dict(choice=out[0], tx=out[1], ty=out[2], tz=out[3])
 
 
 def fit_set_hbm_budget(g, nbytes):

@@ -22,6 +22,14 @@ def _apply(fit, torch, g, omegas, xs, prec):
     return y.cpu().numpy().astype(np.complex128).reshape(len(omegas), -1)
 
 
+@pytest.fixture(params=["auto", "generic", "fused:0"])
+def kernel(request, monkeypatch):
+    """Runs a test with the autotuned kernel, and with the generic / first fused kernel forced."""
+    if request.param != "auto":
+        monkeypatch.setenv("FIT_APPLY_KERNEL", request.param)
+    return request.param
+
+
 def _check_case(case, omegas, prec, use_matrices=False, seed=0):
     torch = torch_cuda()
     fit = fitlib()
@@ -50,25 +58,25 @@ def _check_case(case, omegas, prec, use_matrices=False, seed=0):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_apply_cavity16(prec):
+def test_apply_cavity16(prec, kernel):
     _check_case(G.cavity(16), [2 * np.pi * 5e9], prec)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("shape", [(37, 21, 19), (64, 9, 5), (33, 40, 3)])
-def test_apply_random_ragged_batched(prec, shape):
+@pytest.mark.parametrize("shape", [(37, 21, 19), (34, 21, 19), (66, 9, 5), (48, 40, 3), (33, 40, 3)])
+def test_apply_random_ragged_batched(prec, shape, kernel):
     case = G.small_random(*shape, seed=sum(shape), pec_frac=0.08)
     _check_case(case, [2 * np.pi * 1e9, 2 * np.pi * 7.5e9, 2 * np.pi * 20e9], prec, seed=1)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_apply_with_loaded_matrices(prec):
+def test_apply_with_loaded_matrices(prec, kernel):
     case = G.small_random(20, 18, 11, seed=77, pec_frac=0.1)
     _check_case(case, [2 * np.pi * 3e9, 2 * np.pi * 9e9], prec, use_matrices=True, seed=2)
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 1), (2, 1, 7), (3, 3, 1)])
-def test_apply_degenerate_shapes(shape):
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 1), (2, 1, 7), (3, 3, 1), (2, 2, 2)])
+def test_apply_degenerate_shapes(shape, kernel):
     case = G.small_random(*shape, seed=5, pec_frac=0.0)
     _check_case(case, [2 * np.pi * 2e9], 1)
     _check_case(case, [2 * np.pi * 2e9], 0)
@@ -109,17 +117,40 @@ def _sampled_rows(case, omega, prec, nsample=200, seed=3):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_apply_sampled_layered128(prec):
+def test_apply_sampled_layered128(prec, kernel):
     case = G.layered_blocks()
     _sampled_rows(case, 2 * np.pi * case["freqs"][0], prec)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_apply_sampled_stripline96(prec):
+def test_apply_sampled_stripline96(prec, kernel):
     case = G.stripline()
     _sampled_rows(case, 2 * np.pi * case["freqs"][-1], prec)
 
 
-def test_apply_sampled_package256_c64():
+def test_apply_sampled_package256_c64(kernel):
     case = G.package()
     _sampled_rows(case, 2 * np.pi * case["freqs"][3], 0, nsample=300)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_fused_variant(prec, monkeypatch):
+    """Each launch shape the autotuner may pick, forced in turn, on a ragged batched grid."""
+    fit = fitlib()
+    case = G.small_random(70, 27, 37, seed=8, pec_frac=0.07)
+    for k in range(fit.fit_apply_variant_count(prec)):
+        monkeypatch.setenv("FIT_APPLY_KERNEL", f"fused:{k}")
+        _check_case(case, [2 * np.pi * 2e9, 2 * np.pi * 11e9], prec, seed=k)
+
+
+def test_autotuner_records_a_choice():
+    torch = torch_cuda()
+    fit = fitlib()
+    case = G.small_random(64, 32, 40, seed=9)
+    with fit.Grid.from_case(case) as g:
+        x = torch.randn(g.ne, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        assert fit.fit_apply_tuned(g.h, 0, 1)["choice"] == -2
+        g.apply([1e10], x, y, 0)
+        t = fit.fit_apply_tuned(g.h, 0, 1)
+        assert t["choice"] >= -1 and t["tx"] == 32
