@@ -159,6 +159,31 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_solves(fit, torch, case, kinds, max_iter):
+    """Seconds per frequency to a 1e-8 true residual: FGMRES(30) with the Jacobi (Eq. Precond diagonal)
+    right preconditioner, complex64 inner + FP64 refinement ("mixed") or complex128 throughout ("c128").
+    Inputs are resident on the device; the timed region is the fit_solve call."""
+    import fitgen as G
+    w = 2 * np.pi * float(case["freqs"][0])
+    j = torch.from_numpy(G.source_vector(case)).cuda()
+    out = {}
+    with fit.Grid.from_case(case) as g:
+        b = (-1j * w) * j  # b = -j w j (masked source edges carry no current in these workloads)
+        for kind in kinds:
+            x = torch.zeros_like(b)
+            prec = fit.FIT_SOLVE_MIXED if kind == "mixed" else fit.FIT_SOLVE_C128
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, rep = g.solve([w], b, x, 1e-8, precision=prec, method=fit.FIT_FGMRES, restart=30,
+                              precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[kind] = {"s_per_freq": dt, "iterations": rep[0]["iterations"], "outer": rep[0]["outer"],
+                         "relres": rep[0]["relres"], "status": fit.status_str(rep[0]["status"]),
+                         "method": "FGMRES(30)+Jacobi", "tol": 1e-8}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +192,10 @@ def main():
     ap.add_argument("--impl", default="fit", choices=["fit", "reference"])
     ap.add_argument("--workload", default="layered128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve"],
+                    help="apply: the operator-apply metric (default); solve: only the solve measurement")
+    ap.add_argument("--solve", default="mixed", help="comma list of solves to time: mixed, c128, none")
+    ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -191,6 +220,13 @@ def main():
     fit.lib()
 
     case = _workload(args.workload)
+    kinds = [k for k in args.solve.split(",") if k in ("mixed", "c128")]
+    if args.mode == "solve":
+        res = time_solves(fit, torch, case, kinds, args.max_iter)
+        if rank == 0:
+            print(json.dumps({"metric": "solve s/freq to 1e-8", "unit": "s", "workload": args.workload,
+                              "solves": res}), flush=True)
+        return
     ne = 3 * case["nx"] * case["ny"] * case["nz"]
     w = 2 * np.pi * float(case["freqs"][0])
     g = fit.Grid.from_case(case)
@@ -225,6 +261,7 @@ def main():
         dist.barrier()
     times_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(times_ms)
+    step_stats = {"min_ms": min(times_ms), "median_ms": statistics.median(times_ms), "max_ms": max(times_ms)}
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -268,15 +305,17 @@ def main():
                        "omega_hz": float(case["freqs"][0]), "l2": "flushed between timed applies (512 MiB write "
                        "then 512 MiB read)", "parallelism": f"replicas{world}",
                        "autotuned_tile": [tuned["tx"], tuned["ty"], tuned["tz"]], "kernel_choice": tuned["choice"]},
-            "roofline": roof, "clocks": clk.summary(),
+            "roofline": roof, "clocks": clk.summary(), "step_stats": step_stats,
             "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ne, "d2h_bytes_per_step": 8 * ne},
             "gpu_launches": args.steps}
 
+    g.close()
+    if kinds:
+        line["solve"] = time_solves(fit, torch, case, kinds, args.max_iter)
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_oracle_apply(case, target_s=10.0)
         cv = r["ne"] * len(r["times"]) / sum(r["times"]) / 1e9
         line["cpu_baseline"] = {"value": cv, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": r["sample"]}
-    g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -16,8 +16,8 @@
 // forward differences at the walls.  After a plane lands, masked edges of the staged e are zeroed
 // (the P in P C^T M_nu C P).  At plane k a thread needs e at planes k and k+1 and h at plane k-1 of
 // its own column, which it carries in registers from the previous step, together with e of its
-// own, its x-1 and its y-1 cell.  Output rows go through a per-warp shared-memory transpose so
-// that each warp writes its 32 x 3 complex values as three fully coalesced 256-byte stores.
+// own, its x-1 and its y-1 cell.  The output plane of the tile is staged in shared memory (two
+// buffers) and written with a bulk tensor store; CTAs are persistent (one wave) and loop over tiles.
 //
 // Fused epilogues (fit_epi): <u, y>, <y, x> and <y, y>, or y = u - A x with <y, y>, accumulated
 // per thread in the vector precision and reduced by fit_block_sum (FP64 from the warp level up).
@@ -39,7 +39,7 @@ namespace {
 
 constexpr int TX = 32;  // one warp per tile row
 
-template <typename T, int TY>
+template <typename T, int TY, bool KU = false>  // KU: the stage also holds the epilogue vector u
 struct Layout {
   using V = typename cplx<T>::t;
   static constexpr int CE = sizeof(V) / 8;      // 8-byte copy elements per complex value
@@ -50,29 +50,31 @@ struct Layout {
   static constexpr int KW = 6 * TX;             // T values per staged M_eps/M_kappa row
   static constexpr int MW = TX + 32;            // mask bytes per staged row
   static constexpr int MR = TY + 2;
+  static constexpr int OW = 3 * TX;             // complex values per output / u row
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
   static constexpr int E_BYTES = EW * ER * (int)sizeof(V);
   static constexpr int N_BYTES = NW * NR * (int)sizeof(T);
   static constexpr int K_BYTES = KW * TY * (int)sizeof(T);
   static constexpr int M_BYTES = MW * MR;
+  static constexpr int U_BYTES = OW * TY * (int)sizeof(V);  // also the size of one output buffer
   static constexpr int E_OFF = 0;
   static constexpr int N_OFF = al(E_BYTES);
   static constexpr int K_OFF = N_OFF + al(N_BYTES);
   static constexpr int M_OFF = K_OFF + al(K_BYTES);
-  static constexpr int STAGE = M_OFF + al(M_BYTES);
-  static constexpr int TX_BYTES = E_BYTES + N_BYTES + K_BYTES + M_BYTES;
-  static constexpr int STG_BYTES = al(TY * 96 * (int)sizeof(V));
-  static int smem(int S) { return S * STAGE + STG_BYTES + 8 * S + 128; }
+  static constexpr int U_OFF = M_OFF + al(M_BYTES);
+  static constexpr int STAGE = U_OFF + (KU ? al(U_BYTES) : 0);
+  static constexpr int TX_BYTES = E_BYTES + N_BYTES + K_BYTES + M_BYTES;  // + U_BYTES when u is staged
+  static constexpr int O_BYTES = al(U_BYTES);   // one output staging buffer
+  static int smem(int S) { return S * STAGE + 2 * O_BYTES + 8 * S + 128; }
 };
 
 template <typename T>
 struct FusedArgs {
   using V = typename cplx<T>::t;
   const V* x;
-  V* y;
   const double* omega;
   int* err;
-  int nx, ny, nz, tz, nzc;
+  int nx, ny, nz, tz, nzc, ntx, nty, ntiles;
   long long ne;
   T out_scale;
 };
@@ -119,231 +121,246 @@ __device__ inline void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int
       ::"r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-
-template <typename V> __device__ inline V ld_raw(const V* p) { return *p; }
+// bulk tensor store from shared memory (coordinates are never negative here)
+__device__ inline void tma_store_4d(const CUtensorMap* tm, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+               ::"l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ inline void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // ---- the kernel ----------------------------------------------------------------------------------
+// Persistent: the grid holds one wave of CTAs; CTA c processes tiles c, c + gridDim.x, ...
+// (tile = x-tile, y-tile, z-chunk, system; x fastest).  The plane counter G and the output counter
+// O run across tiles, so ring-stage parities and output buffers stay consistent.
 template <typename T, int TY, int EPI, int S>
-__global__ void __launch_bounds__(TX* TY, TY <= 8 ? 2 : 1) fused_apply_kernel(const __grid_constant__ CUtensorMap tm_x,
-                                                             const __grid_constant__ CUtensorMap tm_nu,
-                                                             const __grid_constant__ CUtensorMap tm_ek,
-                                                             const __grid_constant__ CUtensorMap tm_mask,
-                                                             FusedArgs<T> a, fit_epi epi) {
+__global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused_apply_kernel(const __grid_constant__ CUtensorMap tm_x,
+                                                                const __grid_constant__ CUtensorMap tm_y,
+                                                                const __grid_constant__ CUtensorMap tm_u,
+                                                                const __grid_constant__ CUtensorMap tm_nu,
+                                                                const __grid_constant__ CUtensorMap tm_ek,
+                                                                const __grid_constant__ CUtensorMap tm_mask,
+                                                                FusedArgs<T> a, fit_epi epi) {
   using V = typename cplx<T>::t;
-  using L = Layout<T, TY>;
+  constexpr bool kU = (EPI == FIT_EPI_DOT_U || EPI == FIT_EPI_RESID);
+  using L = Layout<T, TY, kU>;
+  constexpr uint32_t kTx = L::TX_BYTES + (kU ? L::U_BYTES : 0);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  V* obuf = (V*)(smem + S * L::STAGE);  // two output staging buffers of O_BYTES
+  uint64_t* bars = (uint64_t*)(smem + S * L::STAGE + 2 * L::O_BYTES);
+  __shared__ int bad;
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int zc = blockIdx.z % a.nzc, b = blockIdx.z / a.nzc;
-  const int k0 = zc * a.tz, k1 = min(a.nz, k0 + a.tz);
-  if (epi.status && epi.status[b] != 0) return;  // uniform over the CTA
-
-  V* stg = (V*)(smem + S * L::STAGE) + ty * 96;
-  uint64_t* bars = (uint64_t*)(smem + S * L::STAGE + L::STG_BYTES);
-  const int nplanes = k1 - k0 + 2;  // planes k0-1 .. k1
-
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
+    bad = 0;
   }
   __syncthreads();
 
-  auto stage = [&](int q) -> unsigned char* { return smem + (q % S) * L::STAGE; };
-  auto issue = [&](int q) {  // thread 0 only
-    const int p = k0 - 1 + q;
-    unsigned char* st = stage(q);
-    uint64_t* bar = &bars[q % S];
-    mbar_expect_tx(bar, L::TX_BYTES);
-    tma_load_4d(st + L::E_OFF, &tm_x, L::CE * 3 * (i0 - 2), j0 - 1, p, b, bar);
-    tma_load_3d(st + L::N_OFF, &tm_nu, 3 * (i0 - 4), j0 - 1, p, bar);
-    tma_load_3d(st + L::K_OFF, &tm_ek, 6 * i0, j0, p, bar);
-    tma_load_3d(st + L::M_OFF, &tm_mask, i0 - 16, j0 - 1, p, bar);
-  };
-  auto zero_pass = [&](int q) {  // P: zero masked components of the staged e plane
-    V* e = (V*)(stage(q) + L::E_OFF);
-    const uint8_t* m = stage(q) + L::M_OFF;
-    // warp w takes rows w, w + TY, ...; a row whose 36 staged mask bytes (cells i0-2 .. i0+33, at
-    // byte offsets 14 .. 49 of the 64-byte mask row) are all zero is skipped after one vote
-    for (int cy = ty; cy < TY + 2; cy += TY) {
-      const uint8_t* mrow = m + cy * L::MW;
-      const uint32_t word = tx < 16 ? reinterpret_cast<const uint32_t*>(mrow)[tx] : 0u;
-      const uint32_t sel = tx == 3 ? 0xFFFF0000u : (tx >= 4 && tx <= 11 ? 0xFFFFFFFFu : (tx == 12 ? 0x0000FFFFu : 0u));
-      if (!__any_sync(0xffffffffu, (word & sel) != 0u)) continue;
-      for (int cx = tx; cx < TX + 4; cx += 32) {
-        const uint8_t mb = mrow[cx + 14];
-        if (mb) {
-          V* ec = e + cy * L::EW + 3 * cx;
-          if (mb & 1) ec[0] = czero<V>();
-          if (mb & 2) ec[1] = czero<V>();
-          if (mb & 4) ec[2] = czero<V>();
-        }
-      }
-    }
-    fence_proxy_async();  // order these generic writes before later bulk copies into the stage
-  };
-
-  int issued = 0, waited = 0;
-  bool ok = true;
-  if (tid == 0)
-    for (int q = 0; q < min(S, nplanes); ++q) issue(q);
-  issued = min(S, nplanes);
-
-  const int i = i0 + tx, j = j0 + ty;
-  const bool valid = i < a.nx && j < a.ny;
-  // staged-plane accessors (row/column of this thread's cell inside the stage boxes)
+  unsigned G = 0, O = 0;        // planes issued into the ring / output planes written, this CTA
+  bool pend = false;            // an output plane is staged but not yet stored (thread 0's view)
+  int pi0 = 0, pj0 = 0, pk = 0, pb = 0;
+  auto stage = [&](unsigned gq) -> unsigned char* { return smem + (gq % S) * L::STAGE; };
   const int er = (ty + 1) * L::EW + 3 * (tx + 2);
   const int nr = (ty + 1) * L::NW + 3 * (tx + 4);
-  auto E = [&](int q, int dx, int dy, int w) -> V {
-    return ((const V*)(stage(q) + L::E_OFF))[er + dy * L::EW + 3 * dx + w];
-  };
-  auto NU = [&](int q, int dx, int dy, int w) -> T {
-    return ((const T*)(stage(q) + L::N_OFF))[nr + dy * L::NW + 3 * dx + w];
-  };
 
-  // prologue: planes k0-1 (q = 0) and k0 (q = 1); h(k0-1) of the own column
-  ok = mbar_wait(&bars[0], 0);
-  if (ok) zero_pass(0);
-  ok = ok && mbar_wait(&bars[1 % S], (1 / S) & 1);
-  if (ok) zero_pass(1);
-  ok = __syncthreads_and(ok) != 0;  // block-uniform
-  if (ok) waited = 2;
-  V e0[3], em[3], ejm[3];
-  V hxp, hyp;
-  {
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      e0[w] = E(1, 0, 0, w);
-      em[w] = E(1, -1, 0, w);
-      ejm[w] = E(1, 0, -1, w);
-    }
-    const V ey_m = E(0, 0, 0, 1), ez_m = E(0, 0, 0, 2), ex_m = E(0, 0, 0, 0);
-    hxp = NU(0, 0, 0, 0) * (ey_m - e0[1] + E(0, 0, 1, 2) - ez_m);
-    hyp = NU(0, 0, 0, 1) * (ez_m - E(0, 1, 0, 2) + e0[0] - ex_m);
-  }
-  __syncthreads();
-  if (tid == 0 && ok && S < nplanes) {
-    fence_proxy_async();
-    issue(S);
-  }
-  if (S < nplanes) issued = S + 1;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const int bx = t % a.ntx, by = (t / a.ntx) % a.nty;
+    const int zc = (t / (a.ntx * a.nty)) % a.nzc, b = t / (a.ntx * a.nty * a.nzc);
+    if (epi.status && epi.status[b] != 0) continue;  // uniform over the CTA
+    const int i0 = bx * TX, j0 = by * TY;
+    const int k0 = zc * a.tz, k1 = min(a.nz, k0 + a.tz);
+    const int nplanes = k1 - k0 + 2;  // planes k0-1 .. k1
+    const unsigned G0 = G;
 
-  T acc[3] = {T(0), T(0), T(0)};
-  const double wd = a.omega[b];
-  const T w1 = (T)wd, w2 = (T)(wd * wd);
-  const long long boff = (long long)b * a.ne;
-  const V* xg = a.x + boff;
-  V* yg = a.y + boff;
-  const V* ug = (EPI == FIT_EPI_DOT_U || EPI == FIT_EPI_RESID) ? (const V*)epi.u + boff : nullptr;
-
-  for (int k = k0; k < k1 && ok; ++k) {
-    const int qk = k - k0 + 1, qn = qk + 1;
-    ok = mbar_wait(&bars[qn % S], (qn / S) & 1);
-    if (ok) zero_pass(qn);
-    ok = __syncthreads_and(ok) != 0;  // block-uniform
-    if (!ok) break;
-    waited = qn + 1;
-    if (qk >= 2 && qk - 1 + S < nplanes) {
-      if (tid == 0) {
-        fence_proxy_async();
-        issue(qk - 1 + S);
+    auto issue = [&](int q) {  // thread 0 only
+      const int p = k0 - 1 + q;
+      unsigned char* st = stage(G0 + q);
+      uint64_t* bar = &bars[(G0 + q) % S];
+      mbar_expect_tx(bar, kTx);
+      tma_load_4d(st + L::E_OFF, &tm_x, L::CE * 3 * (i0 - 2), j0 - 1, p, b, bar);
+      tma_load_3d(st + L::N_OFF, &tm_nu, 3 * (i0 - 4), j0 - 1, p, bar);
+      tma_load_3d(st + L::K_OFF, &tm_ek, 6 * i0, j0, p, bar);
+      tma_load_3d(st + L::M_OFF, &tm_mask, i0 - 16, j0 - 1, p, bar);
+      if (kU) tma_load_4d(st + L::U_OFF, &tm_u, L::CE * 3 * i0, j0, p, b, bar);
+    };
+    auto wait = [&](int q) {
+      if (!mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1)) {
+        atomicExch(a.err, 1);
+        bad = 1;
       }
-      issued = qk + S;
-    }
-    // ---- this thread's column at plane k ----
-    V e1[3], em1[3], ejm1[3];
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      e1[w] = E(qn, 0, 0, w);
-      em1[w] = E(qn, -1, 0, w);
-      ejm1[w] = E(qn, 0, -1, w);
-    }
-    const V ez_jp = E(qk, 0, 1, 2), ex_jp = E(qk, 0, 1, 0);
-    const V ez_ip = E(qk, 1, 0, 2), ey_ip = E(qk, 1, 0, 1);
-    const V ex_imjp = E(qk, -1, 1, 0), ey_ipjm = E(qk, 1, -1, 1);
-    const V hx = NU(qk, 0, 0, 0) * (e0[1] - e1[1] + ez_jp - e0[2]);
-    const V hy = NU(qk, 0, 0, 1) * (e0[2] - ez_ip + e1[0] - e0[0]);
-    const V hz = NU(qk, 0, 0, 2) * (e0[0] - ex_jp + ey_ip - e0[1]);
-    const V hy_im = NU(qk, -1, 0, 1) * (em[2] - e0[2] + em1[0] - em[0]);
-    const V hz_im = NU(qk, -1, 0, 2) * (em[0] - ex_imjp + e0[1] - em[1]);
-    const V hx_jm = NU(qk, 0, -1, 0) * (ejm[1] - ejm1[1] + e0[2] - ejm[2]);
-    const V hz_jm = NU(qk, 0, -1, 2) * (ejm[0] - e0[0] + ey_ipjm - ejm[1]);
-    V curl[3];
-    curl[0] = hyp - hy + hz - hz_jm;
-    curl[1] = hz_im - hz + hx - hxp;
-    curl[2] = hx_jm - hx + hy - hy_im;
-    const T* ek = (const T*)(stage(qk) + L::K_OFF) + ty * L::KW + 6 * tx;
-    const uint8_t m = (stage(qk) + L::M_OFF)[(ty + 1) * L::MW + tx + 16];
-    const long long rowbase = 3 * (i0 + (long long)a.nx * (j + (long long)a.ny * k));
-    const int nvalid = 3 * max(0, min(TX, a.nx - i0));  // valid complex values of this warp row
-    const bool row_ok = j < a.ny;
-    V uv[3];
-    if (EPI == FIT_EPI_DOT_U || EPI == FIT_EPI_RESID) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const int q = tx + 32 * r;
-        if (row_ok && q < nvalid) stg[q] = ug[rowbase + q];
-      }
-      __syncwarp();
-#pragma unroll
-      for (int w = 0; w < 3; ++w) uv[w] = stg[3 * tx + w];
-      __syncwarp();
-    }
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      V out;
-      V xv = e0[w];
-      if ((m >> w) & 1) {
-        xv = valid ? xg[rowbase + 3 * tx + w] : czero<V>();  // raw x on a masked edge
-        out = xv;
-      } else {
-        const T ar = -w2 * ek[w], ai = w1 * ek[3 + w];
-        out.x = a.out_scale * (curl[w].x + ar * xv.x - ai * xv.y);
-        out.y = a.out_scale * (curl[w].y + ar * xv.y + ai * xv.x);
-      }
-      if (valid) {
-        if (EPI == FIT_EPI_DOT_U) {
-          acc[0] += uv[w].x * out.x + uv[w].y * out.y;
-          acc[1] += uv[w].x * out.y - uv[w].y * out.x;
-        } else if (EPI == FIT_EPI_DOT_TS) {
-          acc[0] += out.x * xv.x + out.y * xv.y;
-          acc[1] += out.x * xv.y - out.y * xv.x;
-          acc[2] += out.x * out.x + out.y * out.y;
-        } else if (EPI == FIT_EPI_RESID) {
-          out = uv[w] - out;
-          acc[2] += out.x * out.x + out.y * out.y;
+    };
+    auto zero_pass = [&](int q) {  // P: zero masked components of the staged e plane
+      V* e = (V*)(stage(G0 + q) + L::E_OFF);
+      const uint8_t* m = stage(G0 + q) + L::M_OFF;
+      // warp w takes rows w, w + TY, ...; a row whose 36 staged mask bytes (cells i0-2 .. i0+33,
+      // byte offsets 14 .. 49 of the 64-byte mask row) are all zero is skipped after one vote
+      for (int cy = ty; cy < TY + 2; cy += TY) {
+        const uint8_t* mrow = m + cy * L::MW;
+        const uint32_t word = tx < 16 ? reinterpret_cast<const uint32_t*>(mrow)[tx] : 0u;
+        const uint32_t sel = tx == 3 ? 0xFFFF0000u : (tx >= 4 && tx <= 11 ? 0xFFFFFFFFu : (tx == 12 ? 0x0000FFFFu : 0u));
+        if (!__any_sync(0xffffffffu, (word & sel) != 0u)) continue;
+        for (int cx = tx; cx < TX + 4; cx += 32) {
+          const uint8_t mb = mrow[cx + 14];
+          if (mb) {
+            V* ec = e + cy * L::EW + 3 * cx;
+            if (mb & 1) ec[0] = czero<V>();
+            if (mb & 2) ec[1] = czero<V>();
+            if (mb & 4) ec[2] = czero<V>();
+          }
         }
       }
-      stg[3 * tx + w] = out;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int q = tx + 32 * r;
-      if (row_ok && q < nvalid) yg[rowbase + q] = stg[q];
-    }
-    __syncwarp();
-    hxp = hx;
-    hyp = hy;
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      e0[w] = e1[w];
-      em[w] = em1[w];
-      ejm[w] = ejm1[w];
-    }
-  }
+      fence_proxy_async();  // order these generic writes before later bulk copies into the stage
+    };
 
-  if (!ok) {  // a copy did not complete in time: record it and drain what was issued
-    if (tid == 0) atomicExch(a.err, 1);
-    for (int q = waited; q < issued; ++q) (void)mbar_wait(&bars[q % S], (q / S) & 1);
-    return;
+    if (tid == 0)
+      for (int q = 0; q < min(S, nplanes); ++q) issue(q);
+    int issued = min(S, nplanes);
+    auto drain = [&]() {  // bounded waits for every copy this tile issued
+      for (int q = 0; q < issued; ++q) (void)mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1);
+    };
+
+    // prologue: planes k0-1 (q = 0) and k0 (q = 1); h(k0-1) of the own column
+    wait(0);
+    zero_pass(0);
+    wait(1);
+    zero_pass(1);
+    __syncthreads();
+    if (bad) {
+      drain();
+      break;
+    }
+    V e0[3], em[3], ejm[3];
+    V hxp, hyp;
+    {
+      const V* p0 = (const V*)(stage(G0) + L::E_OFF) + er;
+      const V* p1 = (const V*)(stage(G0 + 1) + L::E_OFF) + er;
+      const T* n0 = (const T*)(stage(G0) + L::N_OFF) + nr;
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        e0[w] = p1[w];
+        em[w] = p1[w - 3];
+        ejm[w] = p1[w - L::EW];
+      }
+      hxp = n0[0] * (p0[1] - e0[1] + p0[L::EW + 2] - p0[2]);
+      hyp = n0[1] * (p0[2] - p0[3 + 2] + e0[0] - p0[0]);
+    }
+
+    T acc[3] = {T(0), T(0), T(0)};
+    const double wd = a.omega[b];
+    const T w1 = (T)wd, w2 = (T)(wd * wd);
+    const V* xg = a.x + (long long)b * a.ne;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool valid = i < a.nx && j < a.ny;
+
+    for (int k = k0; k < k1; ++k) {
+      const int qk = k - k0 + 1, qn = qk + 1;
+      wait(qn);
+      zero_pass(qn);
+      if (tid == 0) bulk_wait_read_all();  // the output buffer written this step is free again
+      __syncthreads();
+      if (bad) break;
+      if (tid == 0) {
+        if (pend) tma_store_4d(&tm_y, obuf + (size_t)((O - 1) & 1) * (L::O_BYTES / sizeof(V)),
+                               L::CE * 3 * pi0, pj0, pk, pb);
+        if (qk - 1 + S < nplanes) issue(qk - 1 + S);  // plane qk-1 is released by the barrier above
+      }
+      pend = false;
+      if (qk - 1 + S < nplanes) issued = qk + S;
+      // ---- this thread's column at plane k ----
+      const unsigned char* s0 = stage(G0 + qk);
+      const V* p0 = (const V*)(s0 + L::E_OFF) + er;
+      const V* p1 = (const V*)(stage(G0 + qn) + L::E_OFF) + er;
+      const T* nn = (const T*)(s0 + L::N_OFF) + nr;
+      V e1[3], em1[3], ejm1[3];
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        e1[w] = p1[w];
+        em1[w] = p1[w - 3];
+        ejm1[w] = p1[w - L::EW];
+      }
+      const V ez_jp = p0[L::EW + 2], ex_jp = p0[L::EW];
+      const V ez_ip = p0[3 + 2], ey_ip = p0[3 + 1];
+      const V ex_imjp = p0[L::EW - 3], ey_ipjm = p0[3 + 1 - L::EW];
+      const V hx = nn[0] * (e0[1] - e1[1] + ez_jp - e0[2]);
+      const V hy = nn[1] * (e0[2] - ez_ip + e1[0] - e0[0]);
+      const V hz = nn[2] * (e0[0] - ex_jp + ey_ip - e0[1]);
+      const V hy_im = nn[1 - 3] * (em[2] - e0[2] + em1[0] - em[0]);
+      const V hz_im = nn[2 - 3] * (em[0] - ex_imjp + e0[1] - em[1]);
+      const V hx_jm = nn[0 - L::NW] * (ejm[1] - ejm1[1] + e0[2] - ejm[2]);
+      const V hz_jm = nn[2 - L::NW] * (ejm[0] - e0[0] + ey_ipjm - ejm[1]);
+      V curl[3];
+      curl[0] = hyp - hy + hz - hz_jm;
+      curl[1] = hz_im - hz + hx - hxp;
+      curl[2] = hx_jm - hx + hy - hy_im;
+      const T* ek = (const T*)(s0 + L::K_OFF) + ty * L::KW + 6 * tx;
+      const uint8_t m = (s0 + L::M_OFF)[(ty + 1) * L::MW + tx + 16];
+      const V* uv = (const V*)(s0 + L::U_OFF) + ty * L::OW + 3 * tx;
+      V* ob = obuf + (size_t)(O & 1) * (L::O_BYTES / sizeof(V)) + ty * L::OW + 3 * tx;
+      const long long cbase = 3 * (i + (long long)a.nx * (j + (long long)a.ny * k));
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        V out;
+        V xv = e0[w];
+        if ((m >> w) & 1) {
+          xv = valid ? xg[cbase + w] : czero<V>();  // raw x on a masked edge
+          out = xv;
+        } else {
+          const T ar = -w2 * ek[w], ai = w1 * ek[3 + w];
+          out.x = a.out_scale * (curl[w].x + ar * xv.x - ai * xv.y);
+          out.y = a.out_scale * (curl[w].y + ar * xv.y + ai * xv.x);
+        }
+        if (EPI == FIT_EPI_RESID) out = uv[w] - out;
+        if (valid) {
+          if (EPI == FIT_EPI_DOT_U) {
+            acc[0] += uv[w].x * out.x + uv[w].y * out.y;
+            acc[1] += uv[w].x * out.y - uv[w].y * out.x;
+          } else if (EPI == FIT_EPI_DOT_TS) {
+            acc[0] += out.x * xv.x + out.y * xv.y;
+            acc[1] += out.x * xv.y - out.y * xv.x;
+            acc[2] += out.x * out.x + out.y * out.y;
+          } else if (EPI == FIT_EPI_RESID) {
+            acc[2] += out.x * out.x + out.y * out.y;
+          }
+        }
+        ob[w] = out;
+      }
+      fence_proxy_async();  // the bulk store issued after the next barrier reads these values
+      pend = true;
+      pi0 = i0;
+      pj0 = j0;
+      pk = k;
+      pb = b;
+      ++O;
+      hxp = hx;
+      hyp = hy;
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        e0[w] = e1[w];
+        em[w] = em1[w];
+        ejm[w] = ejm1[w];
+      }
+    }
+    if (bad) {  // a copy did not complete in time: drain what this tile issued and stop
+      drain();
+      break;
+    }
+    G += nplanes;
+    __syncthreads();  // stages free for the next tile; the last output plane is staged
+    if (tid == 0 && pend) tma_store_4d(&tm_y, obuf + (size_t)((O - 1) & 1) * (L::O_BYTES / sizeof(V)),
+                                       L::CE * 3 * pi0, pj0, pk, pb);
+    pend = false;
+    if (EPI != FIT_EPI_NONE) {
+      const long long nblk = (long long)a.ntx * a.nty * a.nzc;
+      const long long blk = ((long long)zc * a.nty + by) * a.ntx + bx;
+      fit_block_sum<T, 3>(acc, epi.part + ((long long)b * nblk + blk) * 4);
+    }
   }
-  if (EPI != FIT_EPI_NONE) {
-    const long long nblk = (long long)gridDim.x * gridDim.y * a.nzc;
-    const long long blk = ((long long)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    fit_block_sum<T, 3>(acc, epi.part + ((long long)b * nblk + blk) * 4);
-  }
+  if (tid == 0) bulk_wait_all();  // every output store has landed before the CTA retires
 }
 
 // ---- host side -----------------------------------------------------------------------------------
@@ -380,15 +397,15 @@ struct Variant {
   int ty, tz, stages;
 };
 // candidate launch shapes; the autotuner picks one per (grid, precision, batch)
+// tz = 0: chunk length chosen at launch so that the tiles fill the resident CTAs in one balanced wave
 const Variant kVariants64[] = {{8, 16, 4}, {8, 32, 4}, {8, 8, 4}, {4, 32, 4}, {4, 16, 4}, {16, 16, 3}, {16, 32, 3},
                                {8, 16, 3}, {8, 32, 3}, {4, 32, 3}, {4, 32, 6}, {4, 32, 8}, {4, 64, 8},
-                               {8, 32, 6}, {8, 64, 6}};
-const Variant kVariants128[] = {{4, 16, 3}, {4, 32, 3}, {8, 16, 3}, {8, 32, 3}};
+                               {8, 32, 6}, {8, 64, 6}, {4, 0, 3}, {4, 0, 4}, {8, 0, 3}, {8, 0, 4}, {16, 0, 3}};
+const Variant kVariants128[] = {{4, 16, 3}, {4, 32, 3}, {8, 16, 3}, {8, 32, 3}, {4, 0, 3}, {8, 0, 3}};
 
 template <typename T, int TY, int S>
 fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
                           const T* ek, double out_scale, cudaStream_t s, fit_epi& e, int tz) {
-  using L = Layout<T, TY>;
   const bool c64 = sizeof(T) == 4;
   CUtensorMap mx, mnu, mek, mmask;
   const cuuint64_t ce = c64 ? 1 : 2;
@@ -432,25 +449,56 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
       return FIT_ECUDA;
     }
   }
+  // y (bulk tensor store, box of the own cells) and the epilogue vector u (same shape as x)
+  CUtensorMap my, mu;
+  {
+    cuuint64_t dims[4] = {3 * ce * (cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz, (cuuint64_t)nbatch};
+    cuuint64_t rowb = 3 * ce * 8 * (cuuint64_t)g->nx;
+    cuuint64_t str[3] = {rowb, rowb * g->ny, rowb * g->ny * g->nz};
+    cuuint32_t box[4] = {(cuuint32_t)(3 * ce * TX), TY, 1, 1};
+    if (!encode(&my, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, y, dims, str, box)) {
+      fit_set_error("fused apply: tensor map of y rejected");
+      return FIT_ECUDA;
+    }
+    const void* ub = (e.mode == FIT_EPI_DOT_U || e.mode == FIT_EPI_RESID) ? e.u : x;
+    if (((uintptr_t)ub & 15) != 0 || !encode(&mu, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, ub, dims, str, box)) {
+      fit_set_error("fused apply: tensor map of the epilogue vector rejected");
+      return FIT_ECUDA;
+    }
+  }
   FusedArgs<T> a;
   a.x = (const typename cplx<T>::t*)x;
-  a.y = (typename cplx<T>::t*)y;
   a.omega = omega_dev;
   a.err = g->err_dev;
   a.nx = g->nx;
   a.ny = g->ny;
   a.nz = g->nz;
-  a.tz = tz;
-  a.nzc = (g->nz + tz - 1) / tz;
+  a.ntx = (g->nx + TX - 1) / TX;
+  a.nty = (g->ny + TY - 1) / TY;
   a.ne = g->ne;
   a.out_scale = (T)out_scale;
   dim3 block(TX, TY, 1);
-  dim3 grid((g->nx + TX - 1) / TX, (g->ny + TY - 1) / TY, (unsigned)(a.nzc * nbatch));
-  e.nslots = (long long)grid.x * grid.y * a.nzc;
-  const int smem = L::smem(S);
+  const bool ku = e.mode == FIT_EPI_DOT_U || e.mode == FIT_EPI_RESID;
+  const int smem = ku ? Layout<T, TY, true>::smem(S) : Layout<T, TY, false>::smem(S);
   auto run = [&](auto kern) -> fit_status {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<grid, block, smem, s>>>(mx, mnu, mek, mmask, a, e);
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
+    const long long slots = (long long)std::max(1, per_sm) * nsm;
+    int tzz = tz;
+    if (tzz <= 0) {  // balanced: as many equal z-chunks per column tile as the resident CTAs allow
+      const long long cols = (long long)a.ntx * a.nty * nbatch;
+      const long long per_col = std::max(1LL, slots / std::max(1LL, cols));
+      tzz = (int)std::max(2LL, ((long long)g->nz + per_col - 1) / per_col);
+    }
+    a.tz = tzz;
+    a.nzc = (g->nz + tzz - 1) / tzz;
+    a.ntiles = a.ntx * a.nty * a.nzc * nbatch;
+    e.nslots = (long long)a.ntx * a.nty * a.nzc;
+    const int grid = (int)std::max(1LL, std::min((long long)a.ntiles, slots));  // one persistent wave
+    kern<<<grid, block, smem, s>>>(mx, my, mu, mnu, mek, mmask, a, e);
     FIT_CHECK_CUDA(cudaGetLastError());
     return FIT_OK;
   };
@@ -512,7 +560,10 @@ bool fused_supported(const fit_grid* g, fit_prec prec) {
 }
 
 bool fused_fits(const fit_grid* g, int nbatch, const Variant& v) {
-  return (long long)((g->nz + v.tz - 1) / v.tz) * nbatch <= 65535;
+  // the persistent loop indexes tiles with int
+  const int tz = v.tz > 0 ? v.tz : 2;
+  return (long long)((g->nx + TX - 1) / TX) * ((g->ny + v.ty - 1) / v.ty) * ((g->nz + tz - 1) / tz) * nbatch <
+         (1LL << 30);
 }
 
 }  // namespace
@@ -526,7 +577,8 @@ long long fit_apply_partials(const fit_grid* g, fit_prec prec) {
   int n = 0;
   const Variant* v = variants(prec, &n);
   for (int k = 0; k < n; ++k) {
-    long long p = (long long)((g->nx + TX - 1) / TX) * ((g->ny + v[k].ty - 1) / v[k].ty) * ((g->nz + v[k].tz - 1) / v[k].tz);
+    const int tz = v[k].tz > 0 ? v[k].tz : 2;  // auto chunks are at least 2 planes long
+    long long p = (long long)((g->nx + TX - 1) / TX) * ((g->ny + v[k].ty - 1) / v[k].ty) * ((g->nz + tz - 1) / tz);
     best = std::max(best, p);
   }
   return best;
