@@ -109,8 +109,13 @@ typedef struct fit_solve_opts {
   double inner_tol;  /* relative tolerance of each inner complex64 solve; default 1e-4 */
   int batch;         /* systems solved together in one batched launch; 0 = all nfreq */
   int use_graph;     /* nonzero: run the Krylov loop as one CUDA graph with a device-side loop */
-  int precond;       /* fit_pc_kind applied as the right preconditioner (FGMRES) */
+  int precond;       /* fit_pc_kind applied as the right preconditioner (BiCGStab: Jacobi only) */
   void* stream;      /* cudaStream_t (as void*) for all work; NULL = legacy default stream */
+  void* history;     /* optional DEVICE buffer of history_len * nfreq * n_e double2: the iterate x
+                        after every history_every-th outer step, slot h of system f at
+                        (h * nfreq + f) * n_e (used to harvest training pairs); NULL = off */
+  int history_len;   /* slots in history (per system) */
+  int history_every; /* outer steps between snapshots (>= 1) */
 } fit_solve_opts;
 
 typedef struct fit_solve_report {
@@ -119,6 +124,7 @@ typedef struct fit_solve_report {
   int outer;         /* outer steps taken (refinement steps / true-residual restarts) */
   double relres;     /* final true relative residual ||b - A x||_2 / ||b||_2, computed in FP64 */
   double seconds;    /* wall time of the batch this system was solved in */
+  int snapshots;     /* history slots written for this system */
 } fit_solve_report;
 
 /* fit_solve_opts_default -- fill opts with the defaults named above. */
@@ -157,6 +163,59 @@ int fit_apply_variant_count(fit_prec prec);
  * Tests and experiments can force a kernel with the environment variable
  * FIT_APPLY_KERNEL=generic or FIT_APPLY_KERNEL=fused:<k>. */
 fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out4);
+
+/* ---- learned right preconditioner (3-level 3D U-Net) ---------------------------------------------
+ * Not in the paper: its matrix-free operator "cannot use black-box preconditioners" (Sec. I), and
+ * Sec. III builds only the diagonal one (Eq. Precond).  The network maps a residual to a correction:
+ * z = rms(v) U(v / rms(v)) approximates A_in^{-1} v for the scaled complex64 operator of the inner
+ * FGMRES.  Layers: two 3x3x3 convs + ReLU per level (16, 32, 64 channels), 2x average pooling,
+ * 2x2x2 transposed convs up, skip concatenation, 1x1x1 head to 6 channels.  Activations and conv
+ * weights are bf16 with FP32 accumulation on the tensor cores; master weights and Adam are FP32.
+ * Tensors are NDHWC on the device (voxel x + nx*(y + ny*z), channels innermost); grid sizes must be
+ * multiples of 4.  Input: 16 bf16 channels (Re/Im of the three residual components, then eps_r/10,
+ * log10(1+sigma)/8, 1/mu_r, cell size [mm], then 6 zero channels).  Output: 6 FP32 channels. */
+typedef struct fit_unet fit_unet;
+
+/* fit_unet_create -- network with He-initialised weights drawn from a counter-based generator. */
+fit_status fit_unet_create(unsigned long long seed, fit_unet** out);
+void fit_unet_destroy(fit_unet* net);
+/* number of FP32 parameters; get/set copy them to/from a HOST array (checkpointing, tests) */
+long long fit_unet_param_count(void);
+fit_status fit_unet_get_params(const fit_unet* net, float* host, long long n);
+fit_status fit_unet_set_params(fit_unet* net, const float* host, long long n);
+/* forward: in16 (device bf16 [N][16]) -> out6 (device float [N][6]) */
+fit_status fit_unet_forward(fit_unet* net, int nx, int ny, int nz, const void* in16, float* out6, void* stream);
+/* loss L = ||U(in) - t||^2 / ||t||^2 (host *loss, synchronising) and its gradient w.r.t. every
+ * parameter (device float [param_count], may be NULL) */
+fit_status fit_unet_backward(fit_unet* net, int nx, int ny, int nz, const void* in16, const float* target6,
+                             float* grad, double* loss, void* stream);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss */
+fit_status fit_unet_train_step(fit_unet* net, int nx, int ny, int nz, const void* in16, const float* target6,
+                               float lr, double* loss, void* stream);
+/* pack a complex64 residual r (device, n_e) times scale, plus the grid's material channels, into
+ * the network input (device bf16 [ncell][16]) */
+fit_status fit_unet_pack(const fit_grid* g, const void* r, double scale, void* out16, void* stream);
+/* pack a complex128 correction e (device, n_e) times scale into a training target
+ * (device float [ncell][6]); masked edges are zero */
+fit_status fit_unet_pack_target(const fit_grid* g, const void* e, double scale, float* out6, void* stream);
+/* z = scale * (network output as complex64, n_e), zero on masked edges */
+fit_status fit_unet_unpack(const fit_grid* g, const float* y6, double scale, void* z, void* stream);
+/* attach a network to the grid; fit_solve with precond = FIT_PC_UNET (FGMRES, FIT_SOLVE_MIXED)
+ * then applies M(v) = D^-1 v + rms(v) U(v / rms(v)) as the right preconditioner: the network learns
+ * the part of the correction that the Jacobi term misses (its head starts at zero, so an untrained
+ * network gives plain Jacobi).  The grid does not own the network. */
+fit_status fit_set_preconditioner(fit_grid* g, int kind, fit_unet* net);
+
+/* fit_jacobi -- y_b = D(omega_b)^-1 x_b with D = diag(A(omega)): for an unmasked edge the sum of M_nu
+ * over the four facets containing it (the column sums of squares of the weighted curl, Eq. Precond)
+ * minus w^2 M_eps plus j w M_kappa; masked edges are left unchanged.  Same argument conventions as
+ * fit_apply.  Allocates a few bytes with cudaMallocAsync on the stream. */
+fit_status fit_jacobi(fit_grid* g, int nbatch, const double* omega, const void* x, void* y, fit_prec prec,
+                      void* stream);
+
+/* fit_coef_scale -- s such that the complex64 coefficients (and the inner complex64 operator) are
+ * s * (SI values): s = 1 / max M_nu.  Materials must be set. */
+fit_status fit_coef_scale(const fit_grid* g, double* s);
 
 /* fit_grid_destroy -- free the handle and all its device memory (NULL is a no-op). */
 void fit_grid_destroy(fit_grid* g);

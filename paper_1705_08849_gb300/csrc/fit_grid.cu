@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "fit_internal.cuh"
 
 static thread_local std::string g_last_error;
@@ -134,6 +136,21 @@ __global__ void assemble_kernel(const double* __restrict__ dx, const double* __r
   mask[cp] = m;
 }
 
+// Material channels of the learned preconditioner per cell (bf16): eps_r / 10, log10(1 + sigma) / 8,
+// 1 / mu_r, and the cell size (dx dy dz)^(1/3) in millimetres.
+__global__ void mat16_kernel(const float* __restrict__ eps_r, const float* __restrict__ sigma,
+                             const float* __restrict__ inv_mu_r, const double* __restrict__ dx,
+                             const double* __restrict__ dy, const double* __restrict__ dz, int nx, int ny, int nz,
+                             __nv_bfloat16* out) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= (long long)nx * ny * nz) return;
+  int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+  out[4 * c + 0] = __float2bfloat16(eps_r[c] / 10.f);
+  out[4 * c + 1] = __float2bfloat16((float)(log10(1.0 + (double)sigma[c]) / 8.0));
+  out[4 * c + 2] = __float2bfloat16(inv_mu_r[c]);
+  out[4 * c + 3] = __float2bfloat16((float)(cbrt(dx[i] * dy[j] * dz[k]) * 1e3));
+}
+
 // max over facets of M_nu (positive doubles order like their bit patterns)
 __global__ void max_nu_kernel(const double* __restrict__ nu, long long n, unsigned long long* out) {
   unsigned long long best = 0;
@@ -203,7 +220,7 @@ void fit_grid_destroy(fit_grid* g) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(g->device);
-  void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev, g->err_dev};
+  void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev, g->err_dev, g->mat16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);
@@ -240,7 +257,8 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
       (st = fit_dev_alloc(g, (void**)&g->nu32, np * 3 * sizeof(float))) ||
       (st = fit_dev_alloc(g, (void**)&g->ek32, np * 6 * sizeof(float))) ||
       (st = fit_dev_alloc(g, (void**)&g->mask, np)) ||
-      (st = fit_dev_alloc(g, (void**)&g->err_dev, sizeof(int)))) {
+      (st = fit_dev_alloc(g, (void**)&g->err_dev, sizeof(int))) ||
+      (st = fit_dev_alloc(g, (void**)&g->mat16, (size_t)g->ncell * 4 * 2))) {
     fit_grid_destroy(g);
     return st;
   }
@@ -253,6 +271,7 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
   cudaMemset(g->ek32, 0, np * 6 * sizeof(float));
   cudaMemset(g->mask, 0, np);
   cudaMemset(g->err_dev, 0, sizeof(int));
+  cudaMemset(g->mat16, 0, (size_t)g->ncell * 4 * 2);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     fit_set_error(std::string("fit_grid_create: ") + cudaGetErrorString(e));
@@ -282,6 +301,8 @@ fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma
   long long blocks = ((long long)n + threads - 1) / threads;
   assemble_kernel<<<(unsigned)blocks, threads>>>(g->dx, g->dy, g->dz, d_eps, d_sig, d_imu, d_pec, g->nx, g->ny,
                                                  g->nz, g->nxp, g->nu64, g->ek64, g->mask);
+  mat16_kernel<<<(unsigned)blocks, threads>>>(d_eps, d_sig, d_imu, g->dx, g->dy, g->dz, g->nx, g->ny, g->nz,
+                                              (__nv_bfloat16*)g->mat16);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_eps);
@@ -320,6 +341,12 @@ fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const dou
   FIT_CHECK_CUDA(cudaMemcpy(g->ek64, ek.data(), np * 6 * sizeof(double), cudaMemcpyHostToDevice));
   FIT_CHECK_CUDA(cudaMemcpy(g->mask, mk.data(), np, cudaMemcpyHostToDevice));
   return finish_coefficients(g);
+}
+
+fit_status fit_coef_scale(const fit_grid* g, double* s) {
+  FIT_REQUIRE(g && s && g->has_materials, "fit_coef_scale: null argument or materials not set");
+  *s = g->coef_scale;
+  return FIT_OK;
 }
 
 fit_status fit_set_hbm_budget(fit_grid* g, size_t bytes) {

@@ -43,7 +43,17 @@ struct fit_grid {
   // autotuned apply kernel per (batch, precision): -1 = generic kernel, k >= 0 = fused variant k
   std::map<long long, int> tuned;
   int* err_dev = nullptr;  // device error word: a bounded wait in a kernel ran out
+  void* mat16 = nullptr;   // [ncell][4] bf16 material channels of the learned preconditioner
+  struct fit_unet* unet = nullptr;  // attached learned preconditioner (not owned)
 };
+
+struct fit_unet;
+// z = scale_out * U(scale_in * v) for one complex64 vector of the grid (x16: [ncell][16] bf16 scratch)
+// (plus dinv (.) v when dinv is given: the Jacobi term of the preconditioner)
+fit_status fit_unet_apply_vec(fit_unet* u, const fit_grid* g, const void* v, void* z, float scale_in, float scale_out,
+                              void* x16, const void* dinv, cudaStream_t s);
+// size the network's activations for the grid and refresh its bf16 weights (call before capture)
+fit_status fit_unet_prepare(fit_unet* u, const fit_grid* g, cudaStream_t s);
 
 // Thread-local last-error message.
 void fit_set_error(const std::string& msg);

@@ -53,6 +53,8 @@ struct Sys {
   int max_inner;       // inner iteration cap of the current inner solve
   double rin_min2;     // smallest inner recurrence residual of the current inner solve
   double rin0;         // inner residual at the start of the current inner solve
+  int hist;            // history snapshots written
+  int hist_pad;
   int rin_min_it;      // iteration at which it was reached
   int pad_;
 };
@@ -426,6 +428,26 @@ __global__ void __launch_bounds__(256) k_dots_ts(const typename cplx<T>::t* __re
   fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
 }
 
+// history snapshot of x after an outer step: slot sys.hist when outer % every == 0 (copy), then
+// k_history_count advances the slot (a separate launch, so every copy block has read the old slot)
+__global__ void __launch_bounds__(256) k_history(const double2* __restrict__ x, double2* hist, const Sys* __restrict__ sys,
+                                                 int every, int len, P p) {
+  const int b = blockIdx.y;
+  const Sys& s = sys[b];
+  if (s.outer == 0 || s.outer % every != 0 || s.hist >= len || s.hist_pad == s.outer) return;
+  const long long off = (long long)b * p.ne;
+  double2* dst = hist + ((long long)s.hist * p.B + b) * p.ne;
+  VEC_LOOP(p) { dst[e] = x[off + e]; }
+}
+__global__ void k_history_count(Sys* sys, int every, int len, P p) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= p.B) return;
+  Sys& s = sys[b];
+  if (s.outer == 0 || s.outer % every != 0 || s.hist >= len || s.hist_pad == s.outer) return;
+  s.hist += 1;
+  s.hist_pad = s.outer;  // one snapshot per outer step
+}
+
 // x128 += corr * d (only systems still in the outer loop)
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_x(double2* x, const typename cplx<T>::t* __restrict__ d,
@@ -742,6 +764,7 @@ struct Work {
   void* nusum = nullptr;
   void* dinv = nullptr;   // Jacobi D^-1 per system (inner precision)
   void *phat = nullptr, *shat = nullptr;  // BiCGStab: preconditioned p and s
+  void* x16 = nullptr;   // U-Net input scratch ([ncell][16] bf16)
   double *part_apply = nullptr, *part_vec = nullptr;
   long long napply = 0;
   double *h1 = nullptr, *h2 = nullptr, *H = nullptr, *G = nullptr, *CS = nullptr, *SN = nullptr, *Y = nullptr;
@@ -765,7 +788,7 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   size_t bytes = ne * B * 16;  // r128
   if (method == FIT_BICGSTAB) bytes += 6 * vec + (pc != FIT_PC_NONE ? 2 * vec : 0);
   else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
-  if (pc == FIT_PC_JACOBI) bytes += ne * esz / 2 + vec;
+  if (pc == FIT_PC_JACOBI || pc == FIT_PC_UNET) bytes += ne * esz / 2 + vec;
   size_t napply = (size_t)std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
   bytes += (size_t)B * napply * 4 * 8;
   bytes += (size_t)B * 1216 * 2 * FG_MAXV * 8;
@@ -806,9 +829,13 @@ fit_status setup(Work& w, int B) {
     ALLOC(w.d, vec);
     w.rin = w.Vb;  // V0 holds r~
   }
-  if (w.pc == FIT_PC_JACOBI) {
+  if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {  // the learned preconditioner adds to Jacobi
     ALLOC(w.nusum, ne * w.esz / 2);
     ALLOC(w.dinv, vec);
+  }
+  if (w.pc == FIT_PC_UNET) {
+    ALLOC(w.x16, (size_t)g->ncell * 16 * 2);
+    if ((st = fit_unet_prepare(g->unet, g, 0)) != FIT_OK) return st;
   }
   w.napply = std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
   ALLOC(w.part_apply, (size_t)B * w.napply * 4 * sizeof(double));
@@ -841,7 +868,7 @@ fit_status setup(Work& w, int B) {
   w.p.tiny = w.mixed ? 1e-30 : 1e-300;
   w.p.stall = 1000;
   w.p.precond = w.pc;
-  if (w.pc == FIT_PC_JACOBI) {
+  if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {
     long long nc = g->ncell;
     if (w.mixed)
       k_nusum<float><<<(unsigned)((nc + 255) / 256), 256>>>(g->nu32, g->nx, g->ny, g->nz, g->nxp, (float*)w.nusum);
@@ -969,6 +996,17 @@ struct Seq {
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
+    } else if (w.pc == FIT_PC_UNET) {
+      // z = U(v) with v of unit norm: the network sees v / rms(v) = sqrt(n_e) v
+      const float sin = (float)sqrt((double)w.p.ne), sout = 1.0f / sin;
+      for (int b = 0; b < w.p.B; ++b) {
+        const size_t off = (size_t)b * w.p.ne * w.esz;
+        fit_status r = fit_unet_apply_vec(w.g->unet, w.g, (const char*)w.Vb + (size_t)j * vecb + off,
+                                          (char*)w.Zb + (size_t)j * vecb + off, sin, sout, w.x16,
+                                          (const char*)w.dinv + off, s);
+        if (r != FIT_OK && st == FIT_OK) st = r;
+      }
+      zin = (const char*)w.Zb + (size_t)j * vecb;
     }
     apply(zin, wj1, FIT_EPI_NONE, nullptr, w.inner, st_inner);
     ortho<T, 0>(j, nullptr);
@@ -995,6 +1033,9 @@ struct Seq {
     check();
   }
 
+  double2* hist = nullptr;
+  int hist_len = 0, hist_every = 1;
+
   template <typename T>
   void outer_tail(const int* st_outer) {
     using V = typename cplx<T>::t;
@@ -1002,6 +1043,11 @@ struct Seq {
     check();
     long long n3 = apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
     fin<3>(w.part_apply, n3, 4, OpOuter{});
+    if (hist) {
+      k_history<<<vgrid(), 256, 0, s>>>(x, hist, w.sys, hist_every, hist_len, w.p);
+      k_history_count<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.sys, hist_every, hist_len, w.p);
+      check();
+    }
   }
 
   void cond(int which, int guard_max, cudaGraphConditionalHandle h, int use_handle) {
@@ -1022,14 +1068,17 @@ __global__ void k_mirror_status(const Sys* __restrict__ sys, int* inner, int* ou
 
 template <typename T>
 fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, int use_graph, int max_outer_guard,
-                     int max_inner_guard) {
+                     int max_inner_guard, double2* hist, int hist_len, int hist_every) {
   int* st_inner = nullptr;
   int* st_outer = nullptr;
   fit_status st;
   if ((st = w.alloc((void**)&st_inner, w.p.B * sizeof(int))) != FIT_OK) return st;
   if ((st = w.alloc((void**)&st_outer, w.p.B * sizeof(int))) != FIT_OK) return st;
   Seq q{w, rhs, x, s};
-  if (w.pc == FIT_PC_JACOBI) {  // D^-1 per system, once per solve
+  q.hist = hist;
+  q.hist_len = hist_len;
+  q.hist_every = hist_every;
+  if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {  // D^-1 per system, once per solve
     const fit_grid* g = w.g;
     k_dinv<T><<<dim3(w.p.nblk, w.p.B), 256, 0, s>>>((const T*)w.nusum, w.mixed ? (const T*)g->ek32 : (const T*)g->ek64,
                                                      g->mask, w.omega, g->nx, g->ny, g->nxp,
@@ -1214,7 +1263,67 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
 
 }  // namespace
 
+namespace {
+// y = D(w)^-1 x with D = diag(A(w)) = sum of M_nu over the facets containing the edge - w^2 M_eps
+// + j w M_kappa (Eq. Precond construction); masked edges: y = x
+template <typename T>
+__global__ void k_jacobi_apply(const typename cplx<T>::t* __restrict__ x, typename cplx<T>::t* y, const T* __restrict__ nu,
+                               const T* __restrict__ ek, const uint8_t* __restrict__ mask, const double* __restrict__ omega,
+                               int nx, int ny, int nz, int nxp, long long ne, int nbatch, double out_scale) {
+  const long long n = ne * nbatch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ne);
+    const long long e = t - (long long)b * ne;
+    const long long c = e / 3;
+    const int q = (int)(e - 3 * c);
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    auto NU = [&](int a, int bb, int cc, int w) -> double {
+      if (a < 0 || bb < 0 || cc < 0) return 0.0;
+      return (double)nu[3 * (a + (long long)nxp * (bb + (long long)ny * cc)) + w];
+    };
+    const long long cp = i + (long long)nxp * (j + (long long)ny * k);
+    const auto xv = x[t];
+    typename cplx<T>::t o;
+    if ((mask[cp] >> q) & 1) {
+      o = xv;
+    } else {
+      double ns;
+      if (q == 0) ns = NU(i, j, k, 1) + NU(i, j, k - 1, 1) + NU(i, j, k, 2) + NU(i, j - 1, k, 2);
+      else if (q == 1) ns = NU(i, j, k, 0) + NU(i, j, k - 1, 0) + NU(i, j, k, 2) + NU(i - 1, j, k, 2);
+      else ns = NU(i, j, k, 0) + NU(i, j - 1, k, 0) + NU(i, j, k, 1) + NU(i - 1, j, k, 1);
+      const double w = omega[b];
+      const double dr = ns - w * w * (double)ek[6 * cp + q], di = w * (double)ek[6 * cp + 3 + q];
+      const double den = (dr * dr + di * di) / out_scale;
+      o.x = (T)((xv.x * dr + xv.y * di) / den);
+      o.y = (T)((xv.y * dr - xv.x * di) / den);
+    }
+    y[t] = o;
+  }
+}
+}  // namespace
+
 extern "C" {
+
+fit_status fit_jacobi(fit_grid* g, int nbatch, const double* omega, const void* x, void* y, fit_prec prec,
+                      void* stream) {
+  FIT_REQUIRE(g && omega && x && y && nbatch >= 1, "fit_jacobi: bad argument");
+  FIT_REQUIRE(g->has_materials, "fit_jacobi: materials not set");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* om = nullptr;
+  FIT_CHECK_CUDA(cudaMallocAsync((void**)&om, nbatch * sizeof(double), s));
+  FIT_CHECK_CUDA(cudaMemcpyAsync(om, omega, nbatch * sizeof(double), cudaMemcpyHostToDevice, s));
+  const long long n = g->ne * nbatch;
+  const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+  if (prec == FIT_C64)  // scaled coefficients: D_s = s D, so D^-1 = s D_s^-1
+    k_jacobi_apply<float><<<blocks, 256, 0, s>>>((const float2*)x, (float2*)y, g->nu32, g->ek32, g->mask, om, g->nx,
+                                                 g->ny, g->nz, g->nxp, g->ne, nbatch, g->coef_scale);
+  else
+    k_jacobi_apply<double><<<blocks, 256, 0, s>>>((const double2*)x, (double2*)y, g->nu64, g->ek64, g->mask, om, g->nx,
+                                                  g->ny, g->nz, g->nxp, g->ne, nbatch, 1.0);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  FIT_CHECK_CUDA(cudaFreeAsync(om, s));
+  return FIT_OK;
+}
 
 void fit_solve_opts_default(fit_solve_opts* o) {
   if (!o) return;
@@ -1228,6 +1337,9 @@ void fit_solve_opts_default(fit_solve_opts* o) {
   o->use_graph = 1;
   o->precond = FIT_PC_NONE;
   o->stream = nullptr;
+  o->history = nullptr;
+  o->history_len = 0;
+  o->history_every = 1;
 }
 
 fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rhs, void* x, double tol,
@@ -1245,9 +1357,14 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
               "fit_solve: FGMRES restart must be in 1..64");
   FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET,
               "fit_solve: unknown preconditioner");
-  FIT_REQUIRE(o.precond != FIT_PC_UNET, "fit_solve: no learned preconditioner is loaded");
+  FIT_REQUIRE(o.precond != FIT_PC_UNET || g->unet != nullptr,
+              "fit_solve: FIT_PC_UNET needs a network attached with fit_set_preconditioner");
+  FIT_REQUIRE(o.precond != FIT_PC_UNET || (o.method == FIT_FGMRES && o.precision == FIT_SOLVE_MIXED),
+              "fit_solve: the learned preconditioner runs inside complex64 FGMRES (FIT_SOLVE_MIXED)");
   FIT_REQUIRE(o.max_iter >= 1 && o.max_outer >= 1, "fit_solve: iteration caps must be >= 1");
   FIT_REQUIRE(o.inner_tol > 0 && o.inner_tol < 1, "fit_solve: inner_tol must be in (0, 1)");
+  FIT_REQUIRE(!o.history || (o.history_len >= 1 && o.history_every >= 1), "fit_solve: bad history options");
+  FIT_REQUIRE(!o.history || o.batch == 0 || o.batch >= nfreq, "fit_solve: history needs all systems in one batch");
   for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(isfinite(omega[f]), "fit_solve: omega must be finite");
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)o.stream;
@@ -1286,8 +1403,15 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
     auto t0 = std::chrono::steady_clock::now();
     int outer_guard = o.max_outer + 1;
     int inner_guard = o.max_iter + 1;
-    st = mixed ? run_batch<float>(w, rb, xb, s, o.use_graph, outer_guard, inner_guard)
-               : run_batch<double>(w, rb, xb, s, o.use_graph, outer_guard, inner_guard);
+    double2* hist = (double2*)o.history;
+    if (hist && nb != nfreq) {
+      fit_set_error("fit_solve: history needs all systems in one batch (raise the HBM budget)");
+      return FIT_EBUDGET;
+    }
+    st = mixed ? run_batch<float>(w, rb, xb, s, o.use_graph, outer_guard, inner_guard, hist, o.history_len,
+                                  o.history_every)
+               : run_batch<double>(w, rb, xb, s, o.use_graph, outer_guard, inner_guard, hist, o.history_len,
+                                   o.history_every);
     if (st != FIT_OK) return st;
     FIT_CHECK_CUDA(cudaStreamSynchronize(s));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1310,6 +1434,7 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
         r.outer = y.outer;
         r.relres = y.bnorm2 > 0 ? sqrt(y.rnorm2 / y.bnorm2) : 0.0;
         r.seconds = secs;
+        r.snapshots = y.hist;
       }
     }
   }

@@ -1,0 +1,528 @@
+// Learned right preconditioner: the U-Net runtime (parameters, activations, forward, backward,
+// Adam) and its C ABI.  The network maps a normalised complex64 residual plus four material
+// channels to a correction: z = rms(v) * U(v / rms(v)) approximates A_in^{-1} v, A_in being the
+// scaled complex64 operator of the inner FGMRES.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fit_internal.cuh"
+#include "fit_unet_kernels.cuh"
+
+namespace {
+
+enum LayerKind { L_CONV3 = 0, L_TCONV = 1, L_HEAD = 2 };
+struct LayerSpec {
+  int kind, cin, cout;
+};
+// c1a c1b | c2a c2b | c3a c3b | t2 c2c c2d | t1 c1c c1d | head
+const LayerSpec kLayers[] = {{L_CONV3, 16, 16}, {L_CONV3, 16, 16}, {L_CONV3, 16, 32}, {L_CONV3, 32, 32},
+                             {L_CONV3, 32, 64}, {L_CONV3, 64, 64}, {L_TCONV, 64, 32}, {L_CONV3, 64, 32},
+                             {L_CONV3, 32, 32}, {L_TCONV, 32, 16}, {L_CONV3, 32, 16}, {L_CONV3, 16, 16},
+                             {L_HEAD, 16, 6}};
+constexpr int kNL = sizeof(kLayers) / sizeof(kLayers[0]);
+enum { C1A, C1B, C2A, C2B, C3A, C3B, T2, C2C, C2D, T1, C1C, C1D, HEAD };
+
+long long wcount(const LayerSpec& l) {
+  const long long taps = l.kind == L_CONV3 ? 27 : (l.kind == L_TCONV ? 8 : 1);
+  return taps * l.cin * l.cout;
+}
+
+unsigned nblocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32); }
+
+}  // namespace
+
+struct fit_unet {
+  int device = 0;
+  long long nparams = 0;
+  long long woff[kNL], boff[kNL];
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // master params, grads, Adam moments
+  bf16 *wf[kNL] = {}, *wt[kNL] = {};                                // bf16 forward / dgrad conv weights
+  double* sums = nullptr;
+  int step = 0;
+  bool weights_dirty = true;
+  // activations for one grid size
+  int nx = 0, ny = 0, nz = 0;
+  std::vector<std::pair<void*, size_t>> bufs;
+  bf16 *A1a, *S1, *P1, *A2a, *S2, *P2, *A3a, *B3, *U2, *A2c, *B2, *U1, *A1c, *B1;
+  float *Y, *dY;
+  bf16 *g16a, *g16b, *g16c, *g8a, *g8b, *g8c, *g64a, *g64b, *g64c;
+  ~fit_unet() {
+    for (auto& b : bufs) cudaFree(b.first);
+    for (int l = 0; l < kNL; ++l) {
+      if (wf[l]) cudaFree(wf[l]);
+      if (wt[l]) cudaFree(wt[l]);
+    }
+    cudaFree(p);
+    cudaFree(g);
+    cudaFree(m);
+    cudaFree(v);
+    cudaFree(sums);
+  }
+};
+
+namespace {
+
+fit_status alloc_acts(fit_unet* u, int nx, int ny, int nz) {
+  if (u->nx == nx && u->ny == ny && u->nz == nz) return FIT_OK;
+  for (auto& b : u->bufs) cudaFree(b.first);
+  u->bufs.clear();
+  const long long N = (long long)nx * ny * nz, N2 = N / 8, N4 = N / 64;
+  auto take = [&](size_t bytes) -> void* {
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, std::max<size_t>(bytes, 256)) != cudaSuccess) return nullptr;
+    u->bufs.push_back({ptr, bytes});
+    return ptr;
+  };
+  const size_t b = sizeof(bf16);
+  u->A1a = (bf16*)take(N * 16 * b);
+  u->S1 = (bf16*)take(N * 16 * b);
+  u->P1 = (bf16*)take(N2 * 16 * b);
+  u->A2a = (bf16*)take(N2 * 32 * b);
+  u->S2 = (bf16*)take(N2 * 32 * b);
+  u->P2 = (bf16*)take(N4 * 32 * b);
+  u->A3a = (bf16*)take(N4 * 64 * b);
+  u->B3 = (bf16*)take(N4 * 64 * b);
+  u->U2 = (bf16*)take(N2 * 32 * b);
+  u->A2c = (bf16*)take(N2 * 32 * b);
+  u->B2 = (bf16*)take(N2 * 32 * b);
+  u->U1 = (bf16*)take(N * 16 * b);
+  u->A1c = (bf16*)take(N * 16 * b);
+  u->B1 = (bf16*)take(N * 16 * b);
+  u->Y = (float*)take(N * 6 * sizeof(float));
+  u->dY = (float*)take(N * 6 * sizeof(float));
+  u->g16a = (bf16*)take(N * 16 * b);
+  u->g16b = (bf16*)take(N * 16 * b);
+  u->g16c = (bf16*)take(N * 16 * b);
+  u->g8a = (bf16*)take(N2 * 32 * b);
+  u->g8b = (bf16*)take(N2 * 32 * b);
+  u->g8c = (bf16*)take(N2 * 32 * b);
+  u->g64a = (bf16*)take(N4 * 64 * b);
+  u->g64b = (bf16*)take(N4 * 64 * b);
+  u->g64c = (bf16*)take(N4 * 64 * b);
+  for (auto& bb : u->bufs)
+    if (!bb.first) {
+      fit_set_error("U-Net: activation allocation failed");
+      return FIT_ENOMEM;
+    }
+  if (u->bufs.size() != 25) {
+    fit_set_error("U-Net: activation allocation failed");
+    return FIT_ENOMEM;
+  }
+  u->nx = nx;
+  u->ny = ny;
+  u->nz = nz;
+  return FIT_OK;
+}
+
+void refresh_weights(fit_unet* u, cudaStream_t s) {
+  if (!u->weights_dirty) return;
+  for (int l = 0; l < kNL; ++l)
+    if (kLayers[l].kind == L_CONV3)
+      unet::conv_weights_bf16_kernel<<<nblocks(wcount(kLayers[l])), 256, 0, s>>>(
+          u->p + u->woff[l], u->wf[l], u->wt[l], kLayers[l].cout, kLayers[l].cin);
+  u->weights_dirty = false;
+}
+
+// conv3 launch: picks the (CIN, NC) instantiation; in2/out2 implement concat / split
+fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w, const float* bias, bf16* out1, int o1,
+                 bf16* out2, int o2, int nx, int ny, int nz, int relu, cudaStream_t s) {
+  unet::ConvArgs a;
+  a.in1 = in1;
+  a.in2 = in2;
+  a.c1 = c1;
+  a.c2 = c2;
+  a.w = w;
+  a.bias = bias;
+  a.out1 = out1;
+  a.out2 = out2;
+  a.o1 = o1;
+  a.o2 = o2;
+  a.cout = o1 + o2;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.relu = relu;
+  const int cin = c1 + c2;
+  const int nc = a.cout >= 32 ? 32 : 16;
+  dim3 grid((nx + unet::CX - 1) / unet::CX, (ny + unet::CY - 1) / unet::CY, (unsigned)(nz * ((a.cout + nc - 1) / nc)));
+  auto go = [&](auto kern, int smem) -> fit_status {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    kern<<<grid, 256, smem, s>>>(a);
+    FIT_CHECK_CUDA(cudaGetLastError());
+    return FIT_OK;
+  };
+  if (cin == 16 && nc == 16) return go(unet::conv3_kernel<16, 16>, unet::conv3_smem<16, 16>());
+  if (cin == 16 && nc == 32) return go(unet::conv3_kernel<16, 32>, unet::conv3_smem<16, 32>());
+  if (cin == 32 && nc == 16) return go(unet::conv3_kernel<32, 16>, unet::conv3_smem<32, 16>());
+  if (cin == 32 && nc == 32) return go(unet::conv3_kernel<32, 32>, unet::conv3_smem<32, 32>());
+  if (cin == 64 && nc == 16) return go(unet::conv3_kernel<64, 16>, unet::conv3_smem<64, 16>());
+  if (cin == 64 && nc == 32) return go(unet::conv3_kernel<64, 32>, unet::conv3_smem<64, 32>());
+  fit_set_error("U-Net: unsupported conv shape");
+  return FIT_EINVAL;
+}
+
+#define UCK(x)                              \
+  do {                                      \
+    fit_status st__ = (x);                  \
+    if (st__ != FIT_OK) return st__;        \
+  } while (0)
+
+fit_status forward(fit_unet* u, const bf16* X0, cudaStream_t s) {
+  const int nx = u->nx, ny = u->ny, nz = u->nz;
+  const int mx = nx / 2, my = ny / 2, mz = nz / 2, qx = nx / 4, qy = ny / 4, qz = nz / 4;
+  const long long N = (long long)nx * ny * nz;
+  refresh_weights(u, s);
+  auto B = [&](int l) { return u->p + u->boff[l]; };
+  UCK(conv3(X0, 16, nullptr, 0, u->wf[C1A], B(C1A), u->A1a, 16, nullptr, 0, nx, ny, nz, 1, s));
+  UCK(conv3(u->A1a, 16, nullptr, 0, u->wf[C1B], B(C1B), u->S1, 16, nullptr, 0, nx, ny, nz, 1, s));
+  unet::pool_fwd_kernel<<<nblocks(N / 8 * 16), 256, 0, s>>>(u->S1, u->P1, 16, nx, ny, nz);
+  UCK(conv3(u->P1, 16, nullptr, 0, u->wf[C2A], B(C2A), u->A2a, 32, nullptr, 0, mx, my, mz, 1, s));
+  UCK(conv3(u->A2a, 32, nullptr, 0, u->wf[C2B], B(C2B), u->S2, 32, nullptr, 0, mx, my, mz, 1, s));
+  unet::pool_fwd_kernel<<<nblocks(N / 64 * 32), 256, 0, s>>>(u->S2, u->P2, 32, mx, my, mz);
+  UCK(conv3(u->P2, 32, nullptr, 0, u->wf[C3A], B(C3A), u->A3a, 64, nullptr, 0, qx, qy, qz, 1, s));
+  UCK(conv3(u->A3a, 64, nullptr, 0, u->wf[C3B], B(C3B), u->B3, 64, nullptr, 0, qx, qy, qz, 1, s));
+  unet::tconv_fwd_kernel<<<nblocks(N / 8 * 32), 256, 0, s>>>(u->B3, u->p + u->woff[T2], B(T2), u->U2, 64, 32, mx, my, mz);
+  UCK(conv3(u->S2, 32, u->U2, 32, u->wf[C2C], B(C2C), u->A2c, 32, nullptr, 0, mx, my, mz, 1, s));
+  UCK(conv3(u->A2c, 32, nullptr, 0, u->wf[C2D], B(C2D), u->B2, 32, nullptr, 0, mx, my, mz, 1, s));
+  unet::tconv_fwd_kernel<<<nblocks(N * 16), 256, 0, s>>>(u->B2, u->p + u->woff[T1], B(T1), u->U1, 32, 16, nx, ny, nz);
+  UCK(conv3(u->S1, 16, u->U1, 16, u->wf[C1C], B(C1C), u->A1c, 16, nullptr, 0, nx, ny, nz, 1, s));
+  UCK(conv3(u->A1c, 16, nullptr, 0, u->wf[C1D], B(C1D), u->B1, 16, nullptr, 0, nx, ny, nz, 1, s));
+  unet::head_fwd_kernel<<<nblocks(N * 6), 256, 0, s>>>(u->B1, u->p + u->woff[HEAD], B(HEAD), u->Y, 16, 6, N);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+// gradient of the loss w.r.t. all parameters into u->g (zeroed here); dY must hold dL/dY
+fit_status backward(fit_unet* u, const bf16* X0, cudaStream_t s) {
+  const int nx = u->nx, ny = u->ny, nz = u->nz;
+  const int mx = nx / 2, my = ny / 2, mz = nz / 2, qx = nx / 4, qy = ny / 4, qz = nz / 4;
+  const long long N = (long long)nx * ny * nz, N2 = N / 8, N4 = N / 64;
+  FIT_CHECK_CUDA(cudaMemsetAsync(u->g, 0, u->nparams * sizeof(float), s));
+  auto GW = [&](int l) { return u->g + u->woff[l]; };
+  auto GB = [&](int l) { return u->g + u->boff[l]; };
+  auto wgrad = [&](const bf16* dy, int cout, const bf16* x1, int c1, const bf16* x2, int c2, int l, int ax, int ay,
+                   int az) {
+    unet::WgradArgs w;
+    w.dy = dy;
+    w.x1 = x1;
+    w.x2 = x2;
+    w.c1 = c1;
+    w.c2 = c2;
+    w.cout = cout;
+    w.dw = GW(l);
+    w.db = GB(l);
+    w.nx = ax;
+    w.ny = ay;
+    w.nz = az;
+    w.chunk = 4096;
+    const long long nv = (long long)ax * ay * az;
+    unet::conv3_wgrad_kernel<<<dim3((unsigned)((nv + 4095) / 4096), 27), 256, 0, s>>>(w);
+  };
+  auto relu_bwd = [&](bf16* gg, const bf16* y, long long n) { unet::relu_bwd_kernel<<<nblocks(n), 256, 0, s>>>(gg, y, n); };
+  // head
+  unet::head_bwd_weight_kernel<<<(unsigned)((N + 4095) / 4096), 256, 0, s>>>(u->B1, u->dY, GW(HEAD), GB(HEAD), 16, 6, N);
+  unet::head_bwd_data_kernel<<<nblocks(N * 16), 256, 0, s>>>(u->dY, u->p + u->woff[HEAD], u->g16a, 16, 6, N);
+  // c1d
+  relu_bwd(u->g16a, u->B1, N * 16);
+  wgrad(u->g16a, 16, u->A1c, 16, nullptr, 0, C1D, nx, ny, nz);
+  UCK(conv3(u->g16a, 16, nullptr, 0, u->wt[C1D], nullptr, u->g16b, 16, nullptr, 0, nx, ny, nz, 0, s));
+  // c1c (input S1 ++ U1): d(S1) part -> g16c, d(U1) -> g16a
+  relu_bwd(u->g16b, u->A1c, N * 16);
+  wgrad(u->g16b, 16, u->S1, 16, u->U1, 16, C1C, nx, ny, nz);
+  UCK(conv3(u->g16b, 16, nullptr, 0, u->wt[C1C], nullptr, u->g16c, 16, u->g16a, 16, nx, ny, nz, 0, s));
+  // t1: d(B2) -> g8a
+  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((N2 + 1023) / 1024), 8), 256, 0, s>>>(u->B2, u->g16a, GW(T1), GB(T1), 32,
+                                                                                      16, nx, ny, nz, 1024);
+  unet::tconv_bwd_data_kernel<<<nblocks(N2 * 32), 256, 0, s>>>(u->g16a, u->p + u->woff[T1], u->g8a, 32, 16, nx, ny, nz);
+  // c2d
+  relu_bwd(u->g8a, u->B2, N2 * 32);
+  wgrad(u->g8a, 32, u->A2c, 32, nullptr, 0, C2D, mx, my, mz);
+  UCK(conv3(u->g8a, 32, nullptr, 0, u->wt[C2D], nullptr, u->g8b, 32, nullptr, 0, mx, my, mz, 0, s));
+  // c2c (input S2 ++ U2): d(S2) part -> g8c, d(U2) -> g8a
+  relu_bwd(u->g8b, u->A2c, N2 * 32);
+  wgrad(u->g8b, 32, u->S2, 32, u->U2, 32, C2C, mx, my, mz);
+  UCK(conv3(u->g8b, 32, nullptr, 0, u->wt[C2C], nullptr, u->g8c, 32, u->g8a, 32, mx, my, mz, 0, s));
+  // t2: d(B3) -> g64a
+  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((N4 + 1023) / 1024), 8), 256, 0, s>>>(u->B3, u->g8a, GW(T2), GB(T2), 64,
+                                                                                      32, mx, my, mz, 1024);
+  unet::tconv_bwd_data_kernel<<<nblocks(N4 * 64), 256, 0, s>>>(u->g8a, u->p + u->woff[T2], u->g64a, 64, 32, mx, my, mz);
+  // c3b
+  relu_bwd(u->g64a, u->B3, N4 * 64);
+  wgrad(u->g64a, 64, u->A3a, 64, nullptr, 0, C3B, qx, qy, qz);
+  UCK(conv3(u->g64a, 64, nullptr, 0, u->wt[C3B], nullptr, u->g64b, 64, nullptr, 0, qx, qy, qz, 0, s));
+  // c3a (input P2): d(P2) -> g64c (32 channels)
+  relu_bwd(u->g64b, u->A3a, N4 * 64);
+  wgrad(u->g64b, 64, u->P2, 32, nullptr, 0, C3A, qx, qy, qz);
+  UCK(conv3(u->g64b, 64, nullptr, 0, u->wt[C3A], nullptr, u->g64c, 32, nullptr, 0, qx, qy, qz, 0, s));
+  // pool2 backward, plus the skip part: d(S2) = g8c + pool_bwd(g64c)
+  unet::pool_bwd_kernel<<<nblocks(N2 * 32), 256, 0, s>>>(u->g64c, u->g8a, 32, mx, my, mz);
+  unet::bf16_add_kernel<<<nblocks(N2 * 32), 256, 0, s>>>(u->g8c, u->g8a, N2 * 32);
+  // c2b
+  relu_bwd(u->g8c, u->S2, N2 * 32);
+  wgrad(u->g8c, 32, u->A2a, 32, nullptr, 0, C2B, mx, my, mz);
+  UCK(conv3(u->g8c, 32, nullptr, 0, u->wt[C2B], nullptr, u->g8b, 32, nullptr, 0, mx, my, mz, 0, s));
+  // c2a (input P1): d(P1) -> g8a (16 channels)
+  relu_bwd(u->g8b, u->A2a, N2 * 32);
+  wgrad(u->g8b, 32, u->P1, 16, nullptr, 0, C2A, mx, my, mz);
+  UCK(conv3(u->g8b, 32, nullptr, 0, u->wt[C2A], nullptr, u->g8a, 16, nullptr, 0, mx, my, mz, 0, s));
+  // pool1 backward: d(S1) = g16c + pool_bwd(g8a)
+  unet::pool_bwd_kernel<<<nblocks(N * 16), 256, 0, s>>>(u->g8a, u->g16a, 16, nx, ny, nz);
+  unet::bf16_add_kernel<<<nblocks(N * 16), 256, 0, s>>>(u->g16c, u->g16a, N * 16);
+  // c1b
+  relu_bwd(u->g16c, u->S1, N * 16);
+  wgrad(u->g16c, 16, u->A1a, 16, nullptr, 0, C1B, nx, ny, nz);
+  UCK(conv3(u->g16c, 16, nullptr, 0, u->wt[C1B], nullptr, u->g16b, 16, nullptr, 0, nx, ny, nz, 0, s));
+  // c1a (input X0; no data gradient needed)
+  relu_bwd(u->g16b, u->A1a, N * 16);
+  wgrad(u->g16b, 16, X0, 16, nullptr, 0, C1A, nx, ny, nz);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status check_dims(int nx, int ny, int nz) {
+  if (nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4) {
+    fit_set_error("U-Net: grid dimensions must be multiples of 4 (two 2x poolings)");
+    return FIT_EINVAL;
+  }
+  return FIT_OK;
+}
+
+fit_status loss_and_grad(fit_unet* u, const float* target, double* loss, cudaStream_t s) {
+  const long long n = (long long)u->nx * u->ny * u->nz * 6;
+  FIT_CHECK_CUDA(cudaMemsetAsync(u->sums, 0, 2 * sizeof(double), s));
+  unet::loss_sums_kernel<<<nblocks(n), 256, 0, s>>>(u->Y, target, n, u->sums);
+  unet::loss_grad_kernel<<<nblocks(n), 256, 0, s>>>(u->Y, target, n, u->sums, u->dY);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  if (loss) {
+    double h[2];
+    FIT_CHECK_CUDA(cudaMemcpyAsync(h, u->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+    *loss = h[1] > 0 ? h[0] / h[1] : 0.0;
+  }
+  return FIT_OK;
+}
+
+}  // namespace
+
+// ---- grid-side helpers: input packing and output unpacking --------------------------------------
+namespace {
+
+// in16[c][0..5] = scale * (Re, Im) of r_x, r_y, r_z; [6..9] = material channels; [10..15] = 0
+__global__ void pack_kernel(const float2* __restrict__ r, float scale, const bf16* __restrict__ mat, bf16* out,
+                            long long ncell) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      const float2 z = r[3 * c + w];
+      v[2 * w] = __float2bfloat16(scale * z.x);
+      v[2 * w + 1] = __float2bfloat16(scale * z.y);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[6 + q] = mat ? mat[4 * c + q] : __float2bfloat16(0.f);
+#pragma unroll
+    for (int q = 10; q < 16; ++q) v[q] = __float2bfloat16(0.f);
+    reinterpret_cast<uint4*>(out + 16 * c)[0] = reinterpret_cast<uint4*>(v)[0];
+    reinterpret_cast<uint4*>(out + 16 * c)[1] = reinterpret_cast<uint4*>(v)[1];
+  }
+}
+
+// z[3c + w] = scale * (y[c][2w] + j y[c][2w+1]) (zero on masked edges) + dinv[3c + w] * v[3c + w]
+// when a Jacobi term is given (dinv, v non-null)
+__global__ void unpack_kernel(const float* __restrict__ y, float scale, const uint8_t* __restrict__ mask, int nx, int ny,
+                              int nxp, float2* z, long long ncell, const float2* __restrict__ dinv,
+                              const float2* __restrict__ v) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
+    const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      float2 o = ((m >> w) & 1) ? make_float2(0.f, 0.f) : make_float2(scale * y[6 * c + 2 * w], scale * y[6 * c + 2 * w + 1]);
+      if (dinv) {
+        const float2 d = dinv[3 * c + w], vv = v[3 * c + w];
+        o.x += d.x * vv.x - d.y * vv.y;
+        o.y += d.x * vv.y + d.y * vv.x;
+      }
+      z[3 * c + w] = o;
+    }
+  }
+}
+
+// t[c][2w..] = scale * (Re, Im) of e[3c + w] (complex128 input), zero on masked edges
+__global__ void pack_target_kernel(const double2* __restrict__ e, double scale, const uint8_t* __restrict__ mask, int nx,
+                                   int ny, int nxp, float* t, long long ncell) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
+    const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      const double2 z = ((m >> w) & 1) ? make_double2(0.0, 0.0) : e[3 * c + w];
+      t[6 * c + 2 * w] = (float)(scale * z.x);
+      t[6 * c + 2 * w + 1] = (float)(scale * z.y);
+    }
+  }
+}
+
+}  // namespace
+
+// Used by the solver: z = scale_out * U(scale_in * v) for one complex64 vector (pack, forward,
+// unpack); all launches are stream-ordered and capturable.
+fit_status fit_unet_apply_vec(fit_unet* u, const fit_grid* g, const void* v, void* z, float scale_in, float scale_out,
+                              void* x16, const void* dinv, cudaStream_t s) {
+  UCK(check_dims(g->nx, g->ny, g->nz));
+  UCK(alloc_acts(u, g->nx, g->ny, g->nz));
+  pack_kernel<<<nblocks(g->ncell), 256, 0, s>>>((const float2*)v, scale_in, (const bf16*)g->mat16, (bf16*)x16, g->ncell);
+  UCK(forward(u, (const bf16*)x16, s));
+  unpack_kernel<<<nblocks(g->ncell), 256, 0, s>>>(u->Y, scale_out, g->mask, g->nx, g->ny, g->nxp, (float2*)z, g->ncell,
+                                                  (const float2*)dinv, (const float2*)v);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_prepare(fit_unet* u, const fit_grid* g, cudaStream_t s) {
+  UCK(check_dims(g->nx, g->ny, g->nz));
+  UCK(alloc_acts(u, g->nx, g->ny, g->nz));
+  refresh_weights(u, s);  // bf16 weight copies are current before any capture
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+extern "C" {
+
+long long fit_unet_param_count(void) {
+  long long n = 0;
+  for (int l = 0; l < kNL; ++l) n += wcount(kLayers[l]) + kLayers[l].cout;
+  return n;
+}
+
+fit_status fit_unet_create(unsigned long long seed, fit_unet** out) {
+  FIT_REQUIRE(out, "fit_unet_create: out is NULL");
+  *out = nullptr;
+  fit_unet* u = new fit_unet();
+  FIT_CHECK_CUDA(cudaGetDevice(&u->device));
+  long long off = 0;
+  for (int l = 0; l < kNL; ++l) {
+    u->woff[l] = off;
+    off += wcount(kLayers[l]);
+    u->boff[l] = off;
+    off += kLayers[l].cout;
+  }
+  u->nparams = off;
+  const size_t pb = (size_t)off * sizeof(float);
+  if (cudaMalloc(&u->p, pb) || cudaMalloc(&u->g, pb) || cudaMalloc(&u->m, pb) || cudaMalloc(&u->v, pb) ||
+      cudaMalloc(&u->sums, 4 * sizeof(double))) {
+    delete u;
+    fit_set_error("fit_unet_create: allocation failed");
+    return FIT_ENOMEM;
+  }
+  cudaMemset(u->p, 0, pb);
+  cudaMemset(u->m, 0, pb);
+  cudaMemset(u->v, 0, pb);
+  for (int l = 0; l < kNL; ++l) {
+    const LayerSpec& L = kLayers[l];
+    const double fan_in = (double)(L.kind == L_CONV3 ? 27 : 1) * L.cin;
+    // He-normal for the ReLU layers; the head starts at zero, so an untrained network adds nothing
+    // to the Jacobi term of the preconditioner
+    const double stdv = L.kind == L_CONV3 ? sqrt(2.0 / fan_in) : (L.kind == L_HEAD ? 0.0 : sqrt(1.0 / fan_in));
+    unet::init_normal_kernel<<<nblocks(wcount(L)), 256>>>(u->p + u->woff[l], wcount(L), (float)stdv, seed + 7919ULL * l);
+    if (L.kind == L_CONV3) {
+      const size_t wb = (size_t)wcount(L) * sizeof(bf16);
+      if (cudaMalloc(&u->wf[l], wb) || cudaMalloc(&u->wt[l], wb)) {
+        delete u;
+        fit_set_error("fit_unet_create: allocation failed");
+        return FIT_ENOMEM;
+      }
+    }
+  }
+  FIT_CHECK_CUDA(cudaDeviceSynchronize());
+  *out = u;
+  return FIT_OK;
+}
+
+void fit_unet_destroy(fit_unet* u) { delete u; }
+
+fit_status fit_unet_get_params(const fit_unet* u, float* host, long long n) {
+  FIT_REQUIRE(u && host && n == u->nparams, "fit_unet_get_params: bad argument");
+  FIT_CHECK_CUDA(cudaMemcpy(host, u->p, n * sizeof(float), cudaMemcpyDeviceToHost));
+  return FIT_OK;
+}
+
+fit_status fit_unet_set_params(fit_unet* u, const float* host, long long n) {
+  FIT_REQUIRE(u && host && n == u->nparams, "fit_unet_set_params: bad argument");
+  FIT_CHECK_CUDA(cudaMemcpy(u->p, host, n * sizeof(float), cudaMemcpyHostToDevice));
+  u->weights_dirty = true;
+  return FIT_OK;
+}
+
+fit_status fit_unet_forward(fit_unet* u, int nx, int ny, int nz, const void* in16, float* out6, void* stream) {
+  FIT_REQUIRE(u && in16 && out6, "fit_unet_forward: null argument");
+  UCK(check_dims(nx, ny, nz));
+  cudaStream_t s = (cudaStream_t)stream;
+  UCK(alloc_acts(u, nx, ny, nz));
+  UCK(forward(u, (const bf16*)in16, s));
+  FIT_CHECK_CUDA(cudaMemcpyAsync(out6, u->Y, (size_t)nx * ny * nz * 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return FIT_OK;
+}
+
+fit_status fit_unet_backward(fit_unet* u, int nx, int ny, int nz, const void* in16, const float* target6, float* grad,
+                             double* loss, void* stream) {
+  FIT_REQUIRE(u && in16 && target6, "fit_unet_backward: null argument");
+  UCK(check_dims(nx, ny, nz));
+  cudaStream_t s = (cudaStream_t)stream;
+  UCK(alloc_acts(u, nx, ny, nz));
+  UCK(forward(u, (const bf16*)in16, s));
+  UCK(loss_and_grad(u, target6, loss, s));
+  UCK(backward(u, (const bf16*)in16, s));
+  if (grad) FIT_CHECK_CUDA(cudaMemcpyAsync(grad, u->g, u->nparams * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return FIT_OK;
+}
+
+fit_status fit_unet_train_step(fit_unet* u, int nx, int ny, int nz, const void* in16, const float* target6, float lr,
+                               double* loss, void* stream) {
+  FIT_REQUIRE(u && in16 && target6 && lr > 0, "fit_unet_train_step: bad argument");
+  UCK(fit_unet_backward(u, nx, ny, nz, in16, target6, nullptr, loss, stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  u->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)u->step), c2 = 1.f - powf(b2, (float)u->step);
+  unet::adam_kernel<<<nblocks(u->nparams), 256, 0, s>>>(u->p, u->g, u->m, u->v, u->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  u->weights_dirty = true;
+  return FIT_OK;
+}
+
+fit_status fit_unet_pack(const fit_grid* g, const void* r, double scale, void* out16, void* stream) {
+  FIT_REQUIRE(g && r && out16, "fit_unet_pack: null argument");
+  pack_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>((const float2*)r, (float)scale,
+                                                                    (const bf16*)g->mat16, (bf16*)out16, g->ncell);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_pack_target(const fit_grid* g, const void* e, double scale, float* out6, void* stream) {
+  FIT_REQUIRE(g && e && out6, "fit_unet_pack_target: null argument");
+  pack_target_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>((const double2*)e, scale, g->mask, g->nx,
+                                                                           g->ny, g->nxp, out6, g->ncell);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_unpack(const fit_grid* g, const float* y6, double scale, void* z, void* stream) {
+  FIT_REQUIRE(g && y6 && z, "fit_unet_unpack: null argument");
+  unpack_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>(y6, (float)scale, g->mask, g->nx, g->ny, g->nxp,
+                                                                      (float2*)z, g->ncell, nullptr, nullptr);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_set_preconditioner(fit_grid* g, int kind, fit_unet* net) {
+  FIT_REQUIRE(g, "fit_set_preconditioner: null grid");
+  FIT_REQUIRE(kind == FIT_PC_UNET, "fit_set_preconditioner: only FIT_PC_UNET takes a network");
+  g->unet = net;
+  return FIT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,454 @@
+// Kernels of the learned right preconditioner: a 3-level 3D U-Net (16/32/64 channels, 3x3x3
+// convolutions, 2x average pooling, 2x2x2 transposed convolutions, skip concatenation, 1x1x1
+// head), BF16 activations and weights with FP32 accumulation, NDHWC layout (channels innermost,
+// voxel index x + nx*(y + ny*z)).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+typedef __nv_bfloat16 bf16;
+
+namespace unet {
+
+// ------------------------------------------------------------------------------------------------
+// 3x3x3 convolution, stride 1, zero padding 1, as an implicit GEMM on the tensor cores:
+//   out[v][co] = act( bias[co] + sum_{tap, ci} in[v + off(tap)][ci] * W[tap][co][ci] )
+// M = output voxels (a CTA owns 32 x 4 x 1 of them, a warp 16 along x), N = output channels (NC per
+// CTA), K = 27 * CIN.  The input halo tile (34 x 6 x 3 voxels) and the CTA's weight slice are
+// staged in shared memory (rows padded by 8 channels so ldmatrix is conflict-free) and fed to
+// mma.sync m16n8k16 (bf16 x bf16 -> f32) through ldmatrix.
+// Two input sources implement the skip concatenation (channels [0, c1) from in1, [c1, CIN) from
+// in2); two outputs split the output channels ([0, o1) to out1, the rest to out2).  The backward
+// data pass (dgrad) is this same kernel on flipped, transposed weights.
+// ------------------------------------------------------------------------------------------------
+struct ConvArgs {
+  const bf16* in1;
+  const bf16* in2;
+  int c1, c2;        // channels of the two inputs (c1 + c2 = CIN)
+  const bf16* w;     // [27][cout][CIN]
+  const float* bias; // [cout] or null
+  bf16* out1;
+  bf16* out2;
+  int o1, o2;        // channels of the two outputs (o1 + o2 = cout)
+  int cout;
+  int nx, ny, nz;
+  int relu;
+};
+
+constexpr int CX = 32, CY = 4;                 // output voxels per CTA (x, y)
+constexpr int HX = CX + 2, HY = CY + 2, HZ = 3;  // input halo tile
+
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ inline void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int CIN, int NC>
+__global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a) {
+  constexpr int RS = CIN + 8;  // padded channel stride (bf16) of a staged row
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* in_s = (bf16*)smem;                 // [HZ][HY][HX][RS]
+  bf16* w_s = in_s + HZ * HY * HX * RS;     // [27][NC][RS]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * CY;
+  const int nblk_n = (a.cout + NC - 1) / NC;
+  const int z = blockIdx.z / nblk_n, n0 = (blockIdx.z % nblk_n) * NC;
+
+  // stage the input halo tile, 8 channels (16 bytes) per copy, zero outside the grid
+  constexpr int CH8 = CIN / 8;
+  for (int q = tid; q < HZ * HY * HX * CH8; q += 256) {
+    const int c8 = q % CH8, vox = q / CH8;
+    const int hx = vox % HX, hy = (vox / HX) % HY, hz = vox / (HX * HY);
+    const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z - 1 + hz;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gx >= 0 && gy >= 0 && gz >= 0 && gx < a.nx && gy < a.ny && gz < a.nz) {
+      const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * gz);
+      const int c = c8 * 8;
+      if (c < a.c1) v = *reinterpret_cast<const uint4*>(a.in1 + gv * a.c1 + c);
+      else v = *reinterpret_cast<const uint4*>(a.in2 + gv * a.c2 + (c - a.c1));
+    }
+    *reinterpret_cast<uint4*>(in_s + vox * RS + c8 * 8) = v;
+  }
+  // stage this CTA's slice of the weights (output channels n0 .. n0+NC-1)
+  for (int q = tid; q < 27 * NC * CH8; q += 256) {
+    const int c8 = q % CH8, row = q / CH8;
+    const int tap = row / NC, n = row % NC;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (n0 + n < a.cout) v = *reinterpret_cast<const uint4*>(a.w + ((long long)tap * a.cout + n0 + n) * CIN + c8 * 8);
+    *reinterpret_cast<uint4*>(w_s + row * RS + c8 * 8) = v;
+  }
+  __syncthreads();
+
+  // warp tile: 16 voxels along x (one y row) x NC channels
+  const int wy = warp >> 1, wx = (warp & 1) * 16;
+  float acc[NC / 8][4];
+#pragma unroll
+  for (int t = 0; t < NC / 8; ++t)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+  const int arow = lane & 15, ahalf = lane >> 4;       // A: row / k-half this lane addresses
+  const int bm = lane >> 3, brow = lane & 7;           // B: matrix / row this lane addresses
+  for (int tap = 0; tap < 27; ++tap) {
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const bf16* arow_p = in_s + ((dz * HY + wy + dy) * HX + wx + arow + dx) * RS + ahalf * 8;
+#pragma unroll
+    for (int kc = 0; kc < CIN / 16; ++kc) {
+      uint32_t a0, a1, a2, a3;
+      ldsm_x4(smem_addr(arow_p + kc * 16), a0, a1, a2, a3);
+#pragma unroll
+      for (int np = 0; np < NC / 16; ++np) {
+        const int n = np * 16 + (bm >> 1) * 8 + brow;
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4(smem_addr(w_s + (tap * NC + n) * RS + kc * 16 + (bm & 1) * 8), b0, b1, b2, b3);
+        mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
+        mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+      }
+    }
+  }
+  // epilogue: bias, ReLU, bf16, split over the two outputs
+  const int gy = y0 + wy;
+  if (gy >= a.ny) return;
+#pragma unroll
+  for (int t = 0; t < NC / 8; ++t) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gx = x0 + wx + (lane >> 2) + 8 * h;
+      const int co = n0 + t * 8 + 2 * (lane & 3);
+      if (gx >= a.nx || co >= a.cout) continue;
+      float v0 = acc[t][2 * h], v1 = acc[t][2 * h + 1];
+      if (a.bias) {
+        v0 += a.bias[co];
+        v1 += a.bias[co + 1];
+      }
+      if (a.relu) {
+        v0 = fmaxf(v0, 0.f);
+        v1 = fmaxf(v1, 0.f);
+      }
+      const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * z);
+      __nv_bfloat162 pv = __floats2bfloat162_rn(v0, v1);
+      if (co < a.o1) *reinterpret_cast<__nv_bfloat162*>(a.out1 + gv * a.o1 + co) = pv;
+      else *reinterpret_cast<__nv_bfloat162*>(a.out2 + gv * a.o2 + (co - a.o1)) = pv;
+    }
+  }
+}
+
+template <int CIN, int NC>
+inline int conv3_smem() {
+  return (HZ * HY * HX * (CIN + 8) + 27 * NC * (CIN + 8)) * (int)sizeof(bf16);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Weight gradient of a 3x3x3 convolution (FP32 on the CUDA cores):
+//   dW[tap][co][ci] += sum_v dy[v][co] * x[v + off(tap)][ci],   db[co] += sum_v dy[v][co]
+// Grid (voxel chunks, 27 taps); each thread owns a 4 x 4 block of (co, ci) and accumulates over
+// 32-voxel tiles staged in shared memory; one atomicAdd per owned entry at the end.
+// ------------------------------------------------------------------------------------------------
+struct WgradArgs {
+  const bf16* dy;  // [N][cout]
+  const bf16* x1;
+  const bf16* x2;
+  int c1, c2;      // input channels of the forward conv (split over two sources)
+  int cout;
+  float* dw;       // [27][cout][c1 + c2]
+  float* db;       // [cout] or null (accumulated by tap 13)
+  int nx, ny, nz;
+  int chunk;       // voxels per CTA
+};
+
+__global__ void __launch_bounds__(256) conv3_wgrad_kernel(WgradArgs a) {
+  const int cin = a.c1 + a.c2;
+  const int tap = blockIdx.y;
+  const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  const long long nvox = (long long)a.nx * a.ny * a.nz;
+  const long long v0 = (long long)blockIdx.x * a.chunk;
+  const long long v1 = min(nvox, v0 + a.chunk);
+  __shared__ float sdy[32][65];
+  __shared__ float sx[32][65];
+  const int nbco = a.cout / 4, nbci = cin / 4;
+  float acc[4][16];  // up to 4 owned blocks of 4 x 4 (cout/4 * cin/4 <= 1024)
+  float accb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    accb[q] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[q][r] = 0.f;
+  }
+  for (long long vb = v0; vb < v1; vb += 32) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < 32 * 64; q += 256) {
+      const int vi = q / 64, c = q % 64;
+      const long long v = vb + vi;
+      float d = 0.f, xv = 0.f;
+      if (v < v1) {
+        if (c < a.cout) d = __bfloat162float(a.dy[v * a.cout + c]);
+        if (c < cin) {
+          const int x = (int)(v % a.nx), y = (int)((v / a.nx) % a.ny), z = (int)(v / ((long long)a.nx * a.ny));
+          const int xs = x + dx, ys = y + dy, zs = z + dz;
+          if (xs >= 0 && ys >= 0 && zs >= 0 && xs < a.nx && ys < a.ny && zs < a.nz) {
+            const long long vs = xs + (long long)a.nx * (ys + (long long)a.ny * zs);
+            xv = c < a.c1 ? __bfloat162float(a.x1[vs * a.c1 + c]) : __bfloat162float(a.x2[vs * a.c2 + (c - a.c1)]);
+          }
+        }
+      }
+      sdy[vi][c] = d;
+      sx[vi][c] = xv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int blk = threadIdx.x + 256 * q;
+      if (blk >= nbco * nbci) break;
+      const int co0 = (blk / nbci) * 4, ci0 = (blk % nbci) * 4;
+      for (int vi = 0; vi < 32; ++vi) {
+        float d[4], xv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          d[r] = sdy[vi][co0 + r];
+          xv[r] = sx[vi][ci0 + r];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[q][4 * r + c] += d[r] * xv[c];
+      }
+    }
+    if (a.db && tap == 13 && threadIdx.x < a.cout) {
+      float s = 0.f;
+      for (int vi = 0; vi < 32; ++vi) s += sdy[vi][threadIdx.x];
+      accb[0] += s;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int blk = threadIdx.x + 256 * q;
+    if (blk >= nbco * nbci) break;
+    const int co0 = (blk / nbci) * 4, ci0 = (blk % nbci) * 4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) atomicAdd(&a.dw[((long long)tap * a.cout + co0 + r) * cin + ci0 + c], acc[q][4 * r + c]);
+  }
+  if (a.db && tap == 13 && threadIdx.x < a.cout) atomicAdd(&a.db[threadIdx.x], accb[0]);
+}
+
+// ---- pooling ------------------------------------------------------------------------------------
+// out (coarse, n/2 per axis) = mean of the 8 children; backward: each child gets dout / 8
+__global__ void pool_fwd_kernel(const bf16* in, bf16* out, int c, int nx, int ny, int nz) {
+  const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+  const long long n = (long long)mx * my * mz * c;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(t % c);
+    const long long v = t / c;
+    const int X = (int)(v % mx), Y = (int)((v / mx) % my), Z = (int)(v / ((long long)mx * my));
+    float s = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int x = 2 * X + (q & 1), y = 2 * Y + ((q >> 1) & 1), z = 2 * Z + (q >> 2);
+      s += __bfloat162float(in[(x + (long long)nx * (y + (long long)ny * z)) * c + ch]);
+    }
+    out[t] = __float2bfloat16(0.125f * s);
+  }
+}
+
+__global__ void pool_bwd_kernel(const bf16* dout, bf16* din, int c, int nx, int ny, int nz) {
+  const long long n = (long long)nx * ny * nz * c;
+  const int mx = nx / 2, my = ny / 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(t % c);
+    const long long v = t / c;
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+    const long long V = (x / 2) + (long long)mx * ((y / 2) + (long long)my * (z / 2));
+    din[t] = __float2bfloat16(0.125f * __bfloat162float(dout[V * c + ch]));
+  }
+}
+
+// ---- 2x2x2 transposed convolution, stride 2 (coarse -> fine) -------------------------------------
+// out[x][y][z][co] = b[co] + sum_ci in[x/2][y/2][z/2][ci] * W[(z%2, y%2, x%2)][co][ci]
+__global__ void tconv_fwd_kernel(const bf16* in, const float* w, const float* b, bf16* out, int cin, int cout, int nx,
+                                 int ny, int nz) {
+  const long long n = (long long)nx * ny * nz * cout;
+  const int mx = nx / 2, my = ny / 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int co = (int)(t % cout);
+    const long long v = t / cout;
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+    const int k = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+    const long long V = (x / 2) + (long long)mx * ((y / 2) + (long long)my * (z / 2));
+    const bf16* ip = in + V * cin;
+    const float* wp = w + ((long long)k * cout + co) * cin;
+    float s = b[co];
+    for (int ci = 0; ci < cin; ++ci) s += __bfloat162float(ip[ci]) * wp[ci];
+    out[t] = __float2bfloat16(s);
+  }
+}
+
+// din[V][ci] = sum_{k, co} dout[child(V, k)][co] * W[k][co][ci]
+__global__ void tconv_bwd_data_kernel(const bf16* dout, const float* w, bf16* din, int cin, int cout, int nx, int ny,
+                                      int nz) {
+  const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+  const long long n = (long long)mx * my * mz * cin;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int ci = (int)(t % cin);
+    const long long V = t / cin;
+    const int X = (int)(V % mx), Y = (int)((V / mx) % my), Z = (int)(V / ((long long)mx * my));
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+      const bf16* dp = dout + (x + (long long)nx * (y + (long long)ny * z)) * cout;
+      const float* wp = w + (long long)k * cout * cin + ci;
+      for (int co = 0; co < cout; ++co) s += __bfloat162float(dp[co]) * wp[(long long)co * cin];
+    }
+    din[t] = __float2bfloat16(s);
+  }
+}
+
+// dW[k][co][ci] += sum_V in[V][ci] * dout[child(V, k)][co];  db[co] += sum dout[.][co]
+// grid (coarse-voxel chunks, 8 children); one thread per (co, ci) pair (cout * cin <= 2048)
+__global__ void tconv_bwd_weight_kernel(const bf16* in, const bf16* dout, float* dw, float* db, int cin, int cout,
+                                        int nx, int ny, int nz, int chunk) {
+  const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+  const long long nv = (long long)mx * my * mz;
+  const int k = blockIdx.y;
+  const long long V0 = (long long)blockIdx.x * chunk, V1 = min(nv, V0 + chunk);
+  for (int pair = threadIdx.x; pair < cin * cout; pair += blockDim.x) {
+    const int co = pair / cin, ci = pair % cin;
+    float s = 0.f, sb = 0.f;
+    for (long long V = V0; V < V1; ++V) {
+      const int X = (int)(V % mx), Y = (int)((V / mx) % my), Z = (int)(V / ((long long)mx * my));
+      const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
+      const float d = __bfloat162float(dout[(x + (long long)nx * (y + (long long)ny * z)) * cout + co]);
+      s += __bfloat162float(in[V * cin + ci]) * d;
+      sb += d;
+    }
+    atomicAdd(&dw[((long long)k * cout + co) * cin + ci], s);
+    if (ci == 0) atomicAdd(&db[co], sb);
+  }
+}
+
+// ---- 1x1x1 head (16 -> 6 channels, FP32 output) ----------------------------------------------------
+__global__ void head_fwd_kernel(const bf16* in, const float* w, const float* b, float* out, int cin, int cout,
+                                long long nv) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nv * cout; t += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(t % cout);
+    const long long v = t / cout;
+    float s = b[o];
+    for (int c = 0; c < cin; ++c) s += __bfloat162float(in[v * cin + c]) * w[o * cin + c];
+    out[t] = s;
+  }
+}
+
+// din[v][c] = sum_o dout[v][o] W[o][c];  dW[o][c] += sum_v dout[v][o] in[v][c];  db[o] += sum_v dout[v][o]
+__global__ void head_bwd_data_kernel(const float* dout, const float* w, bf16* din, int cin, int cout, long long nv) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nv * cin; t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % cin);
+    const long long v = t / cin;
+    float s = 0.f;
+    for (int o = 0; o < cout; ++o) s += dout[v * cout + o] * w[o * cin + c];
+    din[t] = __float2bfloat16(s);
+  }
+}
+
+__global__ void __launch_bounds__(256) head_bwd_weight_kernel(const bf16* in, const float* dout, float* dw, float* db,
+                                                              int cin, int cout, long long nv) {
+  // one thread per (o, c) pair plus the bias; grid-strided over voxel chunks of 4096
+  const long long v0 = (long long)blockIdx.x * 4096, v1 = min(nv, v0 + 4096);
+  for (int pair = threadIdx.x; pair < cout * (cin + 1); pair += blockDim.x) {
+    const int o = pair / (cin + 1), c = pair % (cin + 1);
+    float s = 0.f;
+    for (long long v = v0; v < v1; ++v) {
+      const float d = dout[v * cout + o];
+      s += c < cin ? d * __bfloat162float(in[v * cin + c]) : d;
+    }
+    if (c < cin) atomicAdd(&dw[o * cin + c], s);
+    else atomicAdd(&db[o], s);
+  }
+}
+
+// a += b (bf16), for gradients that meet at a skip connection
+__global__ void bf16_add_kernel(bf16* a, const bf16* b, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    a[t] = __float2bfloat16(__bfloat162float(a[t]) + __bfloat162float(b[t]));
+}
+
+// g = g * (y > 0)   (ReLU backward on the stored post-activation y)
+__global__ void relu_bwd_kernel(bf16* g, const bf16* y, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    if (!(__bfloat162float(y[t]) > 0.f)) g[t] = __float2bfloat16(0.f);
+}
+
+// ---- loss: L = ||y - t||^2 / ||t||^2 over a sample, dy = 2 (y - t) / ||t||^2 -----------------------
+__global__ void loss_sums_kernel(const float* y, const float* t, long long n, double* sums) {
+  double a = 0.0, b = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)y[i] - (double)t[i];
+    a += d * d;
+    b += (double)t[i] * (double)t[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+  }
+}
+
+__global__ void loss_grad_kernel(const float* y, const float* t, long long n, const double* sums, float* dy) {
+  const float sc = (float)(2.0 / fmax(sums[1], 1e-300));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dy[i] = sc * (y[i] - t[i]);
+}
+
+// ---- Adam on the flat FP32 master parameters ---------------------------------------------------
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// forward copy W[tap][co][ci] -> bf16, and the dgrad copy Wt[26 - tap][ci][co]
+__global__ void conv_weights_bf16_kernel(const float* w, bf16* wf, bf16* wt, int cout, int cin) {
+  const long long n = 27LL * cout * cin;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int ci = (int)(t % cin), co = (int)((t / cin) % cout), tap = (int)(t / ((long long)cin * cout));
+    const bf16 b = __float2bfloat16(w[t]);
+    wf[t] = b;
+    wt[((long long)(26 - tap) * cin + ci) * cout + co] = b;
+  }
+}
+
+// deterministic counter-based normal draws for weight initialisation (splitmix64 + Box-Muller)
+__device__ inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+__global__ void init_normal_kernel(float* p, long long n, float stdv, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed ^ (2 * (uint64_t)i)), b = splitmix64(seed ^ (2 * (uint64_t)i + 1));
+    const double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0), u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    p[i] = (float)(stdv * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+  }
+}
+
+}  // namespace unet

@@ -35,12 +35,13 @@ class FitError(RuntimeError):
 class fit_solve_opts(ct.Structure):
     _fields_ = [("method", ct.c_int), ("restart", ct.c_int), ("precision", ct.c_int), ("max_iter", ct.c_int),
                 ("max_outer", ct.c_int), ("inner_tol", ct.c_double), ("batch", ct.c_int),
-                ("use_graph", ct.c_int), ("precond", ct.c_int), ("stream", ct.c_void_p)]
+                ("use_graph", ct.c_int), ("precond", ct.c_int), ("stream", ct.c_void_p),
+                ("history", ct.c_void_p), ("history_len", ct.c_int), ("history_every", ct.c_int)]
 
 
 class fit_solve_report(ct.Structure):
     _fields_ = [("status", ct.c_int), ("iterations", ct.c_int), ("outer", ct.c_int), ("relres", ct.c_double),
-                ("seconds", ct.c_double)]
+                ("seconds", ct.c_double), ("snapshots", ct.c_int)]
 
 
 def lib():
@@ -71,6 +72,29 @@ def lib():
         L.fit_apply_variant_count.restype = ct.c_int
         L.fit_apply_tuned.argtypes = [vp, i, i, ct.POINTER(ct.c_int)]
         L.fit_apply_tuned.restype = ct.c_int
+        L.fit_jacobi.argtypes = [vp, i, pd, vp, vp, i, vp]
+        L.fit_jacobi.restype = ct.c_int
+        L.fit_coef_scale.argtypes = [vp, ct.POINTER(ct.c_double)]
+        L.fit_coef_scale.restype = ct.c_int
+        pfl = ct.POINTER(ct.c_float)
+        L.fit_unet_create.argtypes = [ct.c_ulonglong, ct.POINTER(vp)]
+        L.fit_unet_destroy.argtypes = [vp]
+        L.fit_unet_destroy.restype = None
+        L.fit_unet_param_count.argtypes = []
+        L.fit_unet_param_count.restype = ct.c_longlong
+        L.fit_unet_get_params.argtypes = [vp, pfl, ct.c_longlong]
+        L.fit_unet_set_params.argtypes = [vp, pfl, ct.c_longlong]
+        L.fit_unet_forward.argtypes = [vp, i, i, i, vp, vp, vp]
+        L.fit_unet_backward.argtypes = [vp, i, i, i, vp, vp, vp, ct.POINTER(ct.c_double), vp]
+        L.fit_unet_train_step.argtypes = [vp, i, i, i, vp, vp, ct.c_float, ct.POINTER(ct.c_double), vp]
+        L.fit_unet_pack.argtypes = [vp, vp, d, vp, vp]
+        L.fit_unet_pack_target.argtypes = [vp, vp, d, vp, vp]
+        L.fit_unet_unpack.argtypes = [vp, vp, d, vp, vp]
+        L.fit_set_preconditioner.argtypes = [vp, i, vp]
+        for name in ("fit_unet_create", "fit_unet_get_params", "fit_unet_set_params", "fit_unet_forward",
+                     "fit_unet_backward", "fit_unet_train_step", "fit_unet_pack", "fit_unet_pack_target",
+                     "fit_unet_unpack", "fit_set_preconditioner"):
+            getattr(L, name).restype = ct.c_int
         L.fit_last_error.argtypes = []
         L.fit_last_error.restype = ct.c_char_p
         for name in ("fit_grid_create", "fit_set_materials", "fit_set_material_matrices", "fit_apply", "fit_solve",
@@ -188,8 +212,8 @@ def fit_solve(g, omega, rhs, x, tol, opts=None, **kw):
                          ct.byref(o), reps)
     if st not in (FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN, FIT_ENAN):  # per-system outcomes are returned
         _check(st, "fit_solve")
-    return st, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres, seconds=r.seconds)
-                for r in reps]
+    return st, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres, seconds=r.seconds,
+                     snapshots=r.snapshots) for r in reps]
 
 
 def fit_apply_variant_count(prec):
@@ -202,6 +226,91 @@ def fit_apply_tuned(g, prec, nbatch):
     out = (ct.c_int * 4)()
     _check(lib().fit_apply_tuned(g, prec, nbatch, out), "fit_apply_tuned")
     return dict(choice=out[0], tx=out[1], ty=out[2], tz=out[3])
+
+
+def fit_jacobi(g, omega, x, y, prec=FIT_C128, stream=None):
+    """y_b = diag(A(omega_b))^-1 x_b (the Jacobi preconditioner of Eq. Precond)."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    ne = grid_info(g)["ne"]
+    _check_vec(x, ne, len(om), prec, "x")
+    _check_vec(y, ne, len(om), prec, "y")
+    _check(lib().fit_jacobi(g, len(om), pom, _ptr(x), _ptr(y), prec, _stream_ptr(stream)), "fit_jacobi")
+
+
+def fit_coef_scale(g):
+    out = ct.c_double()
+    _check(lib().fit_coef_scale(g, ct.byref(out)), "fit_coef_scale")
+    return out.value
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+class UNet:
+    """Owning wrapper of a fit_unet handle (the learned right preconditioner)."""
+
+    def __init__(self, seed=0):
+        self.h = ct.c_void_p()
+        _check(lib().fit_unet_create(int(seed), ct.byref(self.h)), "fit_unet_create")
+        self.nparams = int(lib().fit_unet_param_count())
+
+    def get_params(self):
+        out = np.empty(self.nparams, np.float32)
+        _check(lib().fit_unet_get_params(self.h, out.ctypes.data_as(ct.POINTER(ct.c_float)), self.nparams),
+               "fit_unet_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().fit_unet_set_params(self.h, p.ctypes.data_as(ct.POINTER(ct.c_float)), self.nparams),
+               "fit_unet_set_params")
+
+    def forward(self, nx, ny, nz, in16, out6, stream=None):
+        _check(lib().fit_unet_forward(self.h, nx, ny, nz, _ptr(in16), _ptr(out6), _stream_ptr(stream)),
+               "fit_unet_forward")
+
+    def backward(self, nx, ny, nz, in16, target6, grad=None, stream=None):
+        loss = ct.c_double()
+        _check(lib().fit_unet_backward(self.h, nx, ny, nz, _ptr(in16), _ptr(target6),
+                                       _ptr(grad) if grad is not None else None, ct.byref(loss), _stream_ptr(stream)),
+               "fit_unet_backward")
+        return loss.value
+
+    def train_step(self, nx, ny, nz, in16, target6, lr, stream=None):
+        loss = ct.c_double()
+        _check(lib().fit_unet_train_step(self.h, nx, ny, nz, _ptr(in16), _ptr(target6), float(lr), ct.byref(loss),
+                                         _stream_ptr(stream)), "fit_unet_train_step")
+        return loss.value
+
+    def close(self):
+        if self.h is not None:
+            lib().fit_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fit_unet_pack(g, r, scale, out16, stream=None):
+    _check(lib().fit_unet_pack(g, _ptr(r), float(scale), _ptr(out16), _stream_ptr(stream)), "fit_unet_pack")
+
+
+def fit_unet_pack_target(g, e, scale, out6, stream=None):
+    _check(lib().fit_unet_pack_target(g, _ptr(e), float(scale), _ptr(out6), _stream_ptr(stream)),
+           "fit_unet_pack_target")
+
+
+def fit_unet_unpack(g, y6, scale, z, stream=None):
+    _check(lib().fit_unet_unpack(g, _ptr(y6), float(scale), _ptr(z), _stream_ptr(stream)), "fit_unet_unpack")
+
+
+def fit_set_preconditioner(g, net):
+    _check(lib().fit_set_preconditioner(g, FIT_PC_UNET, net.h if net is not None else None),
+           "fit_set_preconditioner")
 
 
 def fit_set_hbm_budget(g, nbytes):
