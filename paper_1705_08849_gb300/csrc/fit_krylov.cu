@@ -996,8 +996,15 @@ struct Seq {
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
+    } else if (w.pc == FIT_PC_UNET && (j & 1)) {
+      // odd Arnoldi steps use the Jacobi term alone: the flexible method may vary the preconditioner
+      // per step, and with plain-Jacobi directions in the basis the residual minimisation never
+      // depends only on the network's directions
+      k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
+      check();
+      zin = (const char*)w.Zb + (size_t)j * vecb;
     } else if (w.pc == FIT_PC_UNET) {
-      // z = U(v) with v of unit norm: the network sees v / rms(v) = sqrt(n_e) v
+      // z = D^-1 v + U(v) with v of unit norm: the network sees v / rms(v) = sqrt(n_e) v
       const float sin = (float)sqrt((double)w.p.ne), sout = 1.0f / sin;
       for (int b = 0; b < w.p.B; ++b) {
         const size_t off = (size_t)b * w.p.ne * w.esz;

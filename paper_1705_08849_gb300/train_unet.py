@@ -94,8 +94,11 @@ def harvest(seeds, n=64, every=6, slots=24, tol=1e-7, fmin=1e9, fmax=10e9, log=p
 
 
 def train(net, samples, n, steps, lr=1e-3, lr_min=1e-4, seed=0, val=None, log=print):
+    """Adam with a cosine learning rate; with validation pairs the parameters with the lowest
+    validation loss seen at the checkpoints (every steps/10) are kept (early stopping)."""
     rng = np.random.default_rng(seed)
     hist = []
+    best = (validate(net, val, n), net.get_params()) if val else None
     t0 = time.time()
     for it in range(steps):
         lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / max(1, steps)))
@@ -105,8 +108,13 @@ def train(net, samples, n, steps, lr=1e-3, lr_min=1e-4, seed=0, val=None, log=pr
         if (it + 1) % max(1, steps // 10) == 0:
             msg = f"step {it + 1}: train loss (mean of last {steps // 10}) {np.mean(hist[-(steps // 10):]):.4f}"
             if val:
-                msg += f", validation {validate(net, val, n):.4f}"
+                v = validate(net, val, n)
+                msg += f", validation {v:.4f}"
+                if v < best[0]:
+                    best = (v, net.get_params())
             log(msg + f", {time.time() - t0:.1f} s")
+    if best is not None:
+        net.set_params(best[1])
     return hist
 
 
