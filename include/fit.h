@@ -94,6 +94,24 @@ fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const dou
 fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
                      fit_prec prec, void* stream);
 
+/* fit_apply_noalloc -- the same operator apply as fit_apply, for callers that must not allocate
+ * device memory (the paper has no counterpart).  fit_apply keeps the batch's frequencies in a buffer
+ * owned by the handle and may cudaMalloc a larger one on a call with a larger batch; a host thread
+ * driving a latency-critical loop (where cudaMalloc / cudaFree can synchronise the device) or a
+ * framework whose device memory is entirely managed by its own pool cannot allow that.  This call
+ * keeps the frequencies in a static device array of 4096 doubles (32 KiB, held by every device that
+ * loads the library until the process exits) and never allocates, never frees and never runs the
+ * autotuner: it uses the kernel the autotuner already picked for (prec, nbatch) on this handle, or
+ * the first fused variant.
+ *   nbatch   1 .. 4096; larger batches return FIT_EINVAL
+ *   other arguments as for fit_apply (host omega, device x and y, stream)
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before anything that must not see CUDA runtime set-up work.
+ * All calls share the one array and each overwrites the entries it uses, so calls whose work may
+ * overlap on the GPU (different streams, or different host threads) race on it: serialise them. */
+fit_status fit_apply_noalloc(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
+                             fit_prec prec, void* stream);
+
 typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1 } fit_method;
 typedef enum { FIT_SOLVE_C128 = 0, FIT_SOLVE_MIXED = 1 } fit_solve_precision;
 typedef enum { FIT_PC_NONE = 0, FIT_PC_JACOBI = 1, FIT_PC_UNET = 2 } fit_pc_kind;

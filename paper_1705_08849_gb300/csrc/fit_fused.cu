@@ -663,6 +663,21 @@ fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, co
   return launch_choice(g, choice, nbatch, omega_dev, x, y, prec, out_scale, s, e);
 }
 
+// The apply without the autotuner: the cached choice for (prec, nbatch) if one exists, else the
+// first fused variant (or the generic kernel where the fused one does not apply).  Runs no timing,
+// creates no events and allocates nothing.
+fit_status fit_launch_apply_fixed(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                                  fit_prec prec, double out_scale, cudaStream_t s) {
+  fit_epi e;
+  const bool aligned = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+  if (!aligned || !fused_supported(g, prec))
+    return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, &e);
+  const long long key = (long long)nbatch * 2 + (prec == FIT_C64 ? 0 : 1);
+  auto it = g->tuned.find(key);
+  const int choice = it != g->tuned.end() ? it->second : 0;
+  return launch_choice(g, choice, nbatch, omega_dev, x, y, prec, out_scale, s, e);
+}
+
 int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out4) {
   const long long key = (long long)nbatch * 2 + (prec == FIT_C64 ? 0 : 1);
   auto it = g->tuned.find(key);

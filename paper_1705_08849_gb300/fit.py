@@ -72,6 +72,8 @@ def lib():
         L.fit_apply_variant_count.restype = ct.c_int
         L.fit_apply_tuned.argtypes = [vp, i, i, ct.POINTER(ct.c_int)]
         L.fit_apply_tuned.restype = ct.c_int
+        L.fit_apply_noalloc.argtypes = [vp, i, pd, vp, vp, i, vp]
+        L.fit_apply_noalloc.restype = ct.c_int
         L.fit_jacobi.argtypes = [vp, i, pd, vp, vp, i, vp]
         L.fit_jacobi.restype = ct.c_int
         L.fit_coef_scale.argtypes = [vp, ct.POINTER(ct.c_double)]
@@ -186,6 +188,16 @@ def fit_apply(g, omega, x, y, prec=FIT_C64, stream=None):
     _check_vec(y, ne, len(om), prec, "y")
     _check(lib().fit_apply(g, len(om), pom, ct.c_void_p(x.data_ptr()), ct.c_void_p(y.data_ptr()), prec,
                            _stream_ptr(stream)), "fit_apply")
+
+
+def fit_apply_noalloc(g, omega, x, y, prec=FIT_C64, stream=None):
+    """fit_apply without device allocations (static frequency scratch of 4096 systems)."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    ne = grid_info(g)["ne"]
+    _check_vec(x, ne, len(om), prec, "x")
+    _check_vec(y, ne, len(om), prec, "y")
+    _check(lib().fit_apply_noalloc(g, len(om), pom, ct.c_void_p(x.data_ptr()), ct.c_void_p(y.data_ptr()), prec,
+                                   _stream_ptr(stream)), "fit_apply_noalloc")
 
 
 def fit_solve_opts_default():
