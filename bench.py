@@ -296,7 +296,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind, "traffic": None,
             "bytes_per_dof": BYTES_PER_DOF_C64,
-            "kernel": ("fused_apply_kernel (TMA)" if tuned["choice"] >= 0 else "apply_generic_kernel")}
+            "kernel": (("ws_apply_kernel" if tuned["ws"] else "fused_apply_kernel") if tuned["choice"] >= 0
+                       else "apply_generic_kernel")}
 
     line = {"metric": "GDoF/s operator apply", "value": value, "unit": "GDoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -304,7 +305,8 @@ def main():
             "config": {"workload": args.workload, "grid": [case["nx"], case["ny"], case["nz"]], "unknowns": ne,
                        "omega_hz": float(case["freqs"][0]), "l2": "flushed between timed applies (512 MiB write "
                        "then 512 MiB read)", "parallelism": f"replicas{world}",
-                       "autotuned_tile": [tuned["tx"], tuned["ty"], tuned["tz"]], "kernel_choice": tuned["choice"]},
+                       "autotuned_tile": [tuned["tx"], tuned["ty"], tuned["tz"]], "ring_stages": tuned["stages"],
+                       "kernel_choice": tuned["choice"]},
             "roofline": roof, "clocks": clk.summary(), "step_stats": step_stats,
             "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ne, "d2h_bytes_per_step": 8 * ne},
             "gpu_launches": args.steps}

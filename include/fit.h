@@ -174,13 +174,17 @@ fit_status fit_grid_info(const fit_grid* g, long long* out6);
 int fit_apply_variant_count(fit_prec prec);
 
 /* fit_apply_tuned -- the apply kernel the autotuner picked for (prec, nbatch) on this grid:
- *   out4[0] = -2 not tuned yet, -1 generic kernel, k >= 0 fused variant k
- *   out4[1..3] = tile TX, TY and planes per CTA (TZ) of that kernel.
+ *   out6[0] = -2 not tuned yet, -1 generic kernel, k >= 0 fused variant k
+ *   out6[1..3] = tile TX, TY and planes per CTA (TZ; 0 = chosen at launch so that the tiles fill
+ *               the resident CTAs in one balanced wave) of that kernel
+ *   out6[4] = shared-memory ring stages (0 for the generic kernel)
+ *   out6[5] = 0 generic or CTA-synchronous fused kernel, 1 warp-specialised fused kernel
+ *             (one producer warp feeding the ring, one consumer warp per tile row).
  * The autotuner runs on the first fit_apply / fit_solve with a new (prec, nbatch); it times every
  * candidate on the caller's stream (synchronising it) and caches the fastest in the handle.
  * Tests and experiments can force a kernel with the environment variable
  * FIT_APPLY_KERNEL=generic or FIT_APPLY_KERNEL=fused:<k>. */
-fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out4);
+fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out6);
 
 /* ---- learned right preconditioner (3-level 3D U-Net) ---------------------------------------------
  * Not in the paper: its matrix-free operator "cannot use black-box preconditioners" (Sec. I), and

@@ -79,6 +79,49 @@ struct FusedArgs {
   T out_scale;
 };
 
+// ---- masking of a staged e plane -------------------------------------------------------------------
+// Edges on PEC walls and inside PEC cells are identity rows and zero columns of A, so their x values
+// must not enter the curl: the staged e plane (cells i0-2 .. i0+TX+1, rows j0-1 .. j0+TY) is zeroed
+// where the mask says so.  The staged mask row covers cells i0-16 .. i0+TX+15, so the e columns
+// are mask bytes 14 .. TX+17, i.e. 32-bit words 3 .. 12 of each row (the outer halves of words 3
+// and 12 belong to cells outside the e row).  NT threads share the plane; every thread loads its
+// words first (independent loads, no per-row vote), and only a nonzero word costs any stores.
+template <typename L, int NT>
+__device__ inline void zero_masked_plane(typename L::V* e, const uint8_t* m, int t) {
+  using V = typename L::V;
+  constexpr int NWR = 10, NWORDS = L::ER * NWR, ROUNDS = (NWORDS + NT - 1) / NT;
+  static_assert(TX == 32 && L::MW % 4 == 0 && 4 * (3 + NWR) <= L::MW, "mask row layout: 36 staged columns");
+  uint32_t wv[ROUNDS];
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int idx = t + NT * r;
+    uint32_t v = 0u;
+    if (idx < NWORDS) {
+      const int cy = idx / NWR, wi = 3 + idx % NWR;
+      v = reinterpret_cast<const uint32_t*>(m + cy * L::MW)[wi];
+      if (wi == 3) v &= 0xFFFF0000u;
+      if (wi == 3 + NWR - 1) v &= 0x0000FFFFu;
+    }
+    wv[r] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    if (wv[r] == 0u) continue;
+    const int idx = t + NT * r;
+    const int cy = idx / NWR, wi = 3 + idx % NWR;
+#pragma unroll
+    for (int bi = 0; bi < 4; ++bi) {
+      const uint32_t mb = (wv[r] >> (8 * bi)) & 0xFFu;
+      if (mb) {
+        V* ec = e + cy * L::EW + 3 * (4 * wi + bi - 14);
+        if (mb & 1u) ec[0] = czero<V>();
+        if (mb & 2u) ec[1] = czero<V>();
+        if (mb & 4u) ec[2] = czero<V>();
+      }
+    }
+  }
+}
+
 // ---- PTX helpers: mbarrier and bulk tensor copies -----------------------------------------------
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -195,25 +238,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
       }
     };
     auto zero_pass = [&](int q) {  // P: zero masked components of the staged e plane
-      V* e = (V*)(stage(G0 + q) + L::E_OFF);
-      const uint8_t* m = stage(G0 + q) + L::M_OFF;
-      // warp w takes rows w, w + TY, ...; a row whose 36 staged mask bytes (cells i0-2 .. i0+33,
-      // byte offsets 14 .. 49 of the 64-byte mask row) are all zero is skipped after one vote
-      for (int cy = ty; cy < TY + 2; cy += TY) {
-        const uint8_t* mrow = m + cy * L::MW;
-        const uint32_t word = tx < 16 ? reinterpret_cast<const uint32_t*>(mrow)[tx] : 0u;
-        const uint32_t sel = tx == 3 ? 0xFFFF0000u : (tx >= 4 && tx <= 11 ? 0xFFFFFFFFu : (tx == 12 ? 0x0000FFFFu : 0u));
-        if (!__any_sync(0xffffffffu, (word & sel) != 0u)) continue;
-        for (int cx = tx; cx < TX + 4; cx += 32) {
-          const uint8_t mb = mrow[cx + 14];
-          if (mb) {
-            V* ec = e + cy * L::EW + 3 * cx;
-            if (mb & 1) ec[0] = czero<V>();
-            if (mb & 2) ec[1] = czero<V>();
-            if (mb & 4) ec[2] = czero<V>();
-          }
-        }
-      }
+      zero_masked_plane<L, TX * TY>((V*)(stage(G0 + q) + L::E_OFF), stage(G0 + q) + L::M_OFF, tid);
       fence_proxy_async();  // order these generic writes before later bulk copies into the stage
     };
 
@@ -363,6 +388,313 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
   if (tid == 0) bulk_wait_all();  // every output store has landed before the CTA retires
 }
 
+
+// ---- warp-specialised variant -------------------------------------------------------------------
+// Warps 0..TY-1 are consumers (one tile row each), warp TY issues the bulk copies (lane 0) and warp
+// TY+1 masks the staged planes.  Per ring stage s:
+//   full[s]  (1 arrival + bytes): the bulk copies of a plane have landed
+//   ready[s] (1 arrival): the masking warp has zeroed the plane's masked edges; consumers may read it
+//   empty[s] (TY arrivals): every consumer warp is done with the plane; the stage may be refilled
+// The issuing warp waits on nothing but empty[], so a stage is refilled as soon as it is released;
+// the masking warp waits on nothing but full[].  Plane p needs the release of plane p - S, which
+// the consumers give after their step p - S (planes p - S and p - S + 1), so no role waits on work
+// that depends on its own later progress.  No CTA-wide barrier is needed in the steady state, and
+// the issuing warp runs into the next tile while the consumers finish the current one.
+__device__ inline bool mbar_test_wait(uint64_t* bar, uint32_t parity) {  // non-blocking probe
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for a handoff between warps of the CTA: spin on try_wait (which itself suspends the thread
+// until the phase completes or a short hardware limit passes) with no sleep in between, so the
+// waiting warp resumes as soon as the other side arrives; gives up after 0.5 s of wall time.
+__device__ inline bool mbar_wait_handoff(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && global_ns() - t0 > 500000000ull) return false;
+  }
+  return false;
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ inline void named_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// resident CTAs per SM the register budget is sized for: about 20 warps per SM for complex64
+template <typename T, int TY>
+constexpr int ws_min_blocks() {
+  return sizeof(T) == 4 ? (20 / (TY + 2) > 1 ? 20 / (TY + 2) : 1) : 1;
+}
+
+template <typename T, int TY, int EPI, int S>
+__global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_kernel(const __grid_constant__ CUtensorMap tm_x,
+                                                                  const __grid_constant__ CUtensorMap tm_u,
+                                                                  const __grid_constant__ CUtensorMap tm_nu,
+                                                                  const __grid_constant__ CUtensorMap tm_ek,
+                                                                  const __grid_constant__ CUtensorMap tm_mask,
+                                                                  FusedArgs<T> a, typename cplx<T>::t* yout, fit_epi epi) {
+  using V = typename cplx<T>::t;
+  constexpr bool kU = (EPI == FIT_EPI_DOT_U || EPI == FIT_EPI_RESID);
+  using L = Layout<T, TY, kU>;
+  constexpr uint32_t kTx = L::TX_BYTES + (kU ? L::U_BYTES : 0);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  V* stg_all = (V*)(smem + S * L::STAGE);                           // per consumer warp: 96 values
+  uint64_t* full = (uint64_t*)(smem + S * L::STAGE + L::O_BYTES);   // O_BYTES >= TY*96*sizeof(V)
+  uint64_t* ready = full + S;
+  uint64_t* empty = ready + S;
+  double* red = (double*)(empty + S);                                // [TY][3] tile partial sums
+  volatile int* abort_flag = (volatile int*)(red + 3 * TY);
+
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&ready[s], 1);
+      mbar_init(&empty[s], TY);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto stage = [&](unsigned gq) -> unsigned char* { return smem + (gq % S) * L::STAGE; };
+  auto fail = [&]() { atomicExch(a.err, 1); };
+
+  auto tile_of = [&](int t, int& bx, int& by, int& zc, int& b) {
+    bx = t % a.ntx;
+    by = (t / a.ntx) % a.nty;
+    zc = (t / (a.ntx * a.nty)) % a.nzc;
+    b = t / (a.ntx * a.nty * a.nzc);
+  };
+
+  if (warp == TY) {
+    // ---------------- issuing warp: lane 0 refills released stages ----------------
+    if (lane != 0) return;
+    unsigned G = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      int bx, by, zc, b;
+      tile_of(t, bx, by, zc, b);
+      if (epi.status && epi.status[b] != 0) continue;  // the same skip in every role
+      const int i0 = bx * TX, j0 = by * TY;
+      const int k0 = zc * a.tz, k1 = min(a.nz, k0 + a.tz);
+      for (int p = k0 - 1; p <= k1; ++p, ++G) {
+        const unsigned s = G % S, use = G / S;
+        if (use > 0 && !mbar_wait_handoff(&empty[s], (use - 1) & 1)) {
+          // record; the copies still in flight are the last (at most S - 1) issued: let them land
+          fail();
+          for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1);
+          return;
+        }
+        unsigned char* st = stage(G);
+        mbar_expect_tx(&full[s], kTx);
+        tma_load_4d(st + L::E_OFF, &tm_x, L::CE * 3 * (i0 - 2), j0 - 1, p, b, &full[s]);
+        tma_load_3d(st + L::N_OFF, &tm_nu, 3 * (i0 - 4), j0 - 1, p, &full[s]);
+        tma_load_3d(st + L::K_OFF, &tm_ek, 6 * i0, j0, p, &full[s]);
+        tma_load_3d(st + L::M_OFF, &tm_mask, i0 - 16, j0 - 1, p, &full[s]);
+        if (kU) tma_load_4d(st + L::U_OFF, &tm_u, L::CE * 3 * i0, j0, p, b, &full[s]);
+      }
+    }
+    // every copy lands before the CTA retires
+    for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1);
+    return;
+  }
+
+  if (warp == TY + 1) {
+    // ---------------- masking warp: zero the masked edges of each landed plane ----------------
+    unsigned G = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      int bx, by, zc, b;
+      tile_of(t, bx, by, zc, b);
+      if (epi.status && epi.status[b] != 0) continue;
+      const int nplanes = min(a.nz, zc * a.tz + a.tz) - zc * a.tz + 2;
+      for (int q = 0; q < nplanes; ++q, ++G) {
+        if (!__all_sync(0xffffffffu, mbar_wait_handoff(&full[G % S], (G / S) & 1))) {  // warp-uniform
+          if (lane == 0) fail();
+          return;
+        }
+        zero_masked_plane<L, 32>((V*)(stage(G) + L::E_OFF), stage(G) + L::M_OFF, lane);
+        fence_proxy_async();  // these generic writes precede the stage's next bulk copy
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[G % S]);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumer warps: row ty = warp ----------------
+  unsigned G = 0;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    int bx, by, zc, b;
+    tile_of(t, bx, by, zc, b);
+    if (epi.status && epi.status[b] != 0) continue;
+    const int i0 = bx * TX, j0 = by * TY;
+    const int k0 = zc * a.tz, k1 = min(a.nz, k0 + a.tz);
+    const int nplanes = k1 - k0 + 2;  // planes k0-1 .. k1
+    const unsigned G0 = G;
+    {
+      const int tx = lane, ty = warp;
+      const int er = (ty + 1) * L::EW + 3 * (tx + 2);
+      const int nr = (ty + 1) * L::NW + 3 * (tx + 4);
+      V* stg = stg_all + ty * 96;
+      // A warp whose wait timed out stops computing but still passes the tile's named barriers, so
+      // the other consumer warps never wait on it; all consumers leave together after the tile.
+      bool dead = !mbar_wait_handoff(&ready[G0 % S], (G0 / S) & 1) || !mbar_wait_handoff(&ready[(G0 + 1) % S], ((G0 + 1) / S) & 1);
+      dead = __any_sync(0xffffffffu, dead);  // warp-uniform
+      T acc[3] = {T(0), T(0), T(0)};
+      if (!dead) {
+        V e0[3], em[3], ejm[3];
+        V hxp, hyp;
+        {
+          const V* p0 = (const V*)(stage(G0) + L::E_OFF) + er;
+          const V* p1 = (const V*)(stage(G0 + 1) + L::E_OFF) + er;
+          const T* n0 = (const T*)(stage(G0) + L::N_OFF) + nr;
+#pragma unroll
+          for (int w = 0; w < 3; ++w) {
+            e0[w] = p1[w];
+            em[w] = p1[w - 3];
+            ejm[w] = p1[w - L::EW];
+          }
+          hxp = n0[0] * (p0[1] - e0[1] + p0[L::EW + 2] - p0[2]);
+          hyp = n0[1] * (p0[2] - p0[3 + 2] + e0[0] - p0[0]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[G0 % S]);  // plane k0-1 is no longer needed
+        const double wd = a.omega[b];
+        const T w1 = (T)wd, w2 = (T)(wd * wd);
+        const long long boff = (long long)b * a.ne;
+        const V* xg = a.x + boff;
+        V* yg = yout + boff;
+        const int i = i0 + tx, j = j0 + ty;
+        const bool valid = i < a.nx && j < a.ny;
+        const int nvalid = 3 * max(0, min(TX, a.nx - i0));
+        for (int k = k0; k < k1; ++k) {
+          const int qk = k - k0 + 1, qn = qk + 1;
+          if (__any_sync(0xffffffffu, !mbar_wait_handoff(&ready[(G0 + qn) % S], ((G0 + qn) / S) & 1))) {
+            dead = true;
+            break;
+          }
+          const unsigned char* s0 = stage(G0 + qk);
+          const V* p0 = (const V*)(s0 + L::E_OFF) + er;
+          const V* p1 = (const V*)(stage(G0 + qn) + L::E_OFF) + er;
+          const T* nn = (const T*)(s0 + L::N_OFF) + nr;
+          V e1[3], em1[3], ejm1[3];
+#pragma unroll
+          for (int w = 0; w < 3; ++w) {
+            e1[w] = p1[w];
+            em1[w] = p1[w - 3];
+            ejm1[w] = p1[w - L::EW];
+          }
+          const V ez_jp = p0[L::EW + 2], ex_jp = p0[L::EW];
+          const V ez_ip = p0[3 + 2], ey_ip = p0[3 + 1];
+          const V ex_imjp = p0[L::EW - 3], ey_ipjm = p0[3 + 1 - L::EW];
+          const V hx = nn[0] * (e0[1] - e1[1] + ez_jp - e0[2]);
+          const V hy = nn[1] * (e0[2] - ez_ip + e1[0] - e0[0]);
+          const V hz = nn[2] * (e0[0] - ex_jp + ey_ip - e0[1]);
+          const V hy_im = nn[1 - 3] * (em[2] - e0[2] + em1[0] - em[0]);
+          const V hz_im = nn[2 - 3] * (em[0] - ex_imjp + e0[1] - em[1]);
+          const V hx_jm = nn[0 - L::NW] * (ejm[1] - ejm1[1] + e0[2] - ejm[2]);
+          const V hz_jm = nn[2 - L::NW] * (ejm[0] - e0[0] + ey_ipjm - ejm[1]);
+          V curl[3];
+          curl[0] = hyp - hy + hz - hz_jm;
+          curl[1] = hz_im - hz + hx - hxp;
+          curl[2] = hx_jm - hx + hy - hy_im;
+          const T* ek = (const T*)(s0 + L::K_OFF) + ty * L::KW + 6 * tx;
+          const uint8_t m = (s0 + L::M_OFF)[(ty + 1) * L::MW + tx + 16];
+          const V* uv = (const V*)(s0 + L::U_OFF) + ty * L::OW + 3 * tx;
+          const long long rowbase = 3 * (i0 + (long long)a.nx * (j + (long long)a.ny * k));
+#pragma unroll
+          for (int w = 0; w < 3; ++w) {
+            V out;
+            V xv = e0[w];
+            if ((m >> w) & 1) {
+              xv = valid ? xg[rowbase + 3 * tx + w] : czero<V>();  // raw x on a masked edge
+              out = xv;
+            } else {
+              const T ar = -w2 * ek[w], ai = w1 * ek[3 + w];
+              out.x = a.out_scale * (curl[w].x + ar * xv.x - ai * xv.y);
+              out.y = a.out_scale * (curl[w].y + ar * xv.y + ai * xv.x);
+            }
+            if (EPI == FIT_EPI_RESID) out = uv[w] - out;
+            if (valid) {
+              if (EPI == FIT_EPI_DOT_U) {
+                acc[0] += uv[w].x * out.x + uv[w].y * out.y;
+                acc[1] += uv[w].x * out.y - uv[w].y * out.x;
+              } else if (EPI == FIT_EPI_DOT_TS) {
+                acc[0] += out.x * xv.x + out.y * xv.y;
+                acc[1] += out.x * xv.y - out.y * xv.x;
+                acc[2] += out.x * out.x + out.y * out.y;
+              } else if (EPI == FIT_EPI_RESID) {
+                acc[2] += out.x * out.x + out.y * out.y;
+              }
+            }
+            stg[3 * tx + w] = out;
+          }
+          __syncwarp();  // every lane has read plane qk; the staged output row is complete
+          if (lane == 0) mbar_arrive(&empty[(G0 + qk) % S]);
+          if (j < a.ny) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              const int q = tx + 32 * r;
+              if (q < nvalid) yg[rowbase + q] = stg[q];
+            }
+          }
+          __syncwarp();
+          hxp = hx;
+          hyp = hy;
+#pragma unroll
+          for (int w = 0; w < 3; ++w) {
+            e0[w] = e1[w];
+            em[w] = em1[w];
+            ejm[w] = ejm1[w];
+          }
+        }
+        if (!dead && lane == 0) mbar_arrive(&empty[(G0 + nplanes - 1) % S]);  // plane k1 (read as k+1 only)
+      }
+      if (dead) {
+        fail();
+        *abort_flag = 1;
+      }
+      if (EPI != FIT_EPI_NONE) {  // tile partial sums: warp shuffles, then FP64 over the rows in order
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) {
+          T v = acc[qq];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) red[ty * 3 + qq] = (double)v;
+        }
+        named_barrier(1, TX * TY);
+        if (ty == 0 && lane < 3) {
+          double sum = 0.0;
+          for (int r = 0; r < TY; ++r) sum += red[r * 3 + lane];
+          const long long nblk = (long long)a.ntx * a.nty * a.nzc;
+          const long long blk = ((long long)zc * a.nty + by) * a.ntx + bx;
+          epi.part[((long long)b * nblk + blk) * 4 + lane] = sum;
+        }
+        named_barrier(1, TX * TY);
+        if (*abort_flag) return;  // read after the barrier: the same answer in every consumer warp
+      } else if (dead) {
+        return;  // no named barrier follows without an epilogue
+      }
+    }
+    G += nplanes;
+  }
+}
+
 // ---- host side -----------------------------------------------------------------------------------
 typedef CUresult (*encode_fn_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -394,16 +726,18 @@ bool encode(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, 
 }
 
 struct Variant {
-  int ty, tz, stages;
+  int ty, tz, stages, ws;  // ws: warp-specialised producer/consumer kernel
 };
 // candidate launch shapes; the autotuner picks one per (grid, precision, batch)
 // tz = 0: chunk length chosen at launch so that the tiles fill the resident CTAs in one balanced wave
-const Variant kVariants64[] = {{8, 16, 4}, {8, 32, 4}, {8, 8, 4}, {4, 32, 4}, {4, 16, 4}, {16, 16, 3}, {16, 32, 3},
-                               {8, 16, 3}, {8, 32, 3}, {4, 32, 3}, {4, 32, 6}, {4, 32, 8}, {4, 64, 8},
-                               {8, 32, 6}, {8, 64, 6}, {4, 0, 3}, {4, 0, 4}, {8, 0, 3}, {8, 0, 4}, {16, 0, 3}};
-const Variant kVariants128[] = {{4, 16, 3}, {4, 32, 3}, {8, 16, 3}, {8, 32, 3}, {4, 0, 3}, {8, 0, 3}};
+const Variant kVariants64[] = {{8, 16, 4, 0}, {4, 32, 4, 0}, {4, 16, 4, 0}, {16, 16, 3, 0}, {8, 32, 3, 0},
+                               {4, 0, 3, 0},  {4, 0, 4, 0},  {8, 0, 3, 0},  {8, 0, 4, 0},  {16, 0, 3, 0},
+                               {4, 0, 4, 1},  {4, 0, 6, 1},  {8, 0, 4, 1},  {8, 0, 6, 1},  {16, 0, 4, 1},
+                               {8, 32, 4, 1}, {4, 32, 6, 1}, {8, 64, 6, 1}};
+const Variant kVariants128[] = {{4, 16, 3, 0}, {4, 32, 3, 0}, {8, 16, 3, 0}, {8, 32, 3, 0}, {4, 0, 3, 0},
+                                {8, 0, 3, 0},  {4, 0, 4, 1},  {8, 0, 4, 1}};
 
-template <typename T, int TY, int S>
+template <typename T, int TY, int S, int WS>
 fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
                           const T* ek, double out_scale, cudaStream_t s, fit_epi& e, int tz) {
   const bool c64 = sizeof(T) == 4;
@@ -477,16 +811,21 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
   a.nty = (g->ny + TY - 1) / TY;
   a.ne = g->ne;
   a.out_scale = (T)out_scale;
-  dim3 block(TX, TY, 1);
+  dim3 block(TX, WS ? TY + 2 : TY, 1);
   const bool ku = e.mode == FIT_EPI_DOT_U || e.mode == FIT_EPI_RESID;
-  const int smem = ku ? Layout<T, TY, true>::smem(S) : Layout<T, TY, false>::smem(S);
+  int smem = ku ? Layout<T, TY, true>::smem(S) : Layout<T, TY, false>::smem(S);
+  if (WS) smem += 3 * 8 * S + 8 * 3 * TY + 16;  // three barriers per stage, row partial sums, abort flag
   auto run = [&](auto kern) -> fit_status {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    FIT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
-    const long long slots = (long long)std::max(1, per_sm) * nsm;
+    FIT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block.x * block.y, smem));
+    if (per_sm < 1) {  // shared memory or registers do not allow one resident CTA of this shape
+      fit_set_error("fused apply: launch shape does not fit on an SM");
+      return FIT_EINVAL;
+    }
+    const long long slots = (long long)per_sm * nsm;
     int tzz = tz;
     if (tzz <= 0) {  // balanced: as many equal z-chunks per column tile as the resident CTAs allow
       const long long cols = (long long)a.ntx * a.nty * nbatch;
@@ -498,15 +837,25 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
     a.ntiles = a.ntx * a.nty * a.nzc * nbatch;
     e.nslots = (long long)a.ntx * a.nty * a.nzc;
     const int grid = (int)std::max(1LL, std::min((long long)a.ntiles, slots));  // one persistent wave
-    kern<<<grid, block, smem, s>>>(mx, my, mu, mnu, mek, mmask, a, e);
+    if constexpr (WS) kern<<<grid, block, smem, s>>>(mx, mu, mnu, mek, mmask, a, (typename cplx<T>::t*)y, e);
+    else kern<<<grid, block, smem, s>>>(mx, my, mu, mnu, mek, mmask, a, e);
     FIT_CHECK_CUDA(cudaGetLastError());
     return FIT_OK;
   };
-  switch (e.mode) {
-    case FIT_EPI_NONE: return run(fused_apply_kernel<T, TY, FIT_EPI_NONE, S>);
-    case FIT_EPI_DOT_U: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_U, S>);
-    case FIT_EPI_DOT_TS: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_TS, S>);
-    case FIT_EPI_RESID: return run(fused_apply_kernel<T, TY, FIT_EPI_RESID, S>);
+  if constexpr (WS) {
+    switch (e.mode) {
+      case FIT_EPI_NONE: return run(ws_apply_kernel<T, TY, FIT_EPI_NONE, S>);
+      case FIT_EPI_DOT_U: return run(ws_apply_kernel<T, TY, FIT_EPI_DOT_U, S>);
+      case FIT_EPI_DOT_TS: return run(ws_apply_kernel<T, TY, FIT_EPI_DOT_TS, S>);
+      case FIT_EPI_RESID: return run(ws_apply_kernel<T, TY, FIT_EPI_RESID, S>);
+    }
+  } else {
+    switch (e.mode) {
+      case FIT_EPI_NONE: return run(fused_apply_kernel<T, TY, FIT_EPI_NONE, S>);
+      case FIT_EPI_DOT_U: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_U, S>);
+      case FIT_EPI_DOT_TS: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_TS, S>);
+      case FIT_EPI_RESID: return run(fused_apply_kernel<T, TY, FIT_EPI_RESID, S>);
+    }
   }
   fit_set_error("fused apply: unknown epilogue");
   return FIT_EINVAL;
@@ -515,16 +864,22 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
 template <typename T>
 fit_status launch_fused(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
                         const T* ek, double out_scale, cudaStream_t s, fit_epi& e, const Variant& v) {
-  if (v.ty == 4 && v.stages == 4) return launch_variant<T, 4, 4>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-  if (v.ty == 8 && v.stages == 4) return launch_variant<T, 8, 4>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-  if (v.ty == 16 && v.stages == 3) return launch_variant<T, 16, 3>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-  if (v.ty == 4 && v.stages == 3) return launch_variant<T, 4, 3>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-  if (v.ty == 8 && v.stages == 3) return launch_variant<T, 8, 3>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-  if constexpr (sizeof(T) == 4) {  // deeper rings: more planes in flight per CTA (complex64 only)
-    if (v.ty == 4 && v.stages == 6) return launch_variant<T, 4, 6>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-    if (v.ty == 4 && v.stages == 8) return launch_variant<T, 4, 8>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
-    if (v.ty == 8 && v.stages == 6) return launch_variant<T, 8, 6>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz);
+#define FIT_LV(TY_, S_, WS_) \
+  if (v.ty == TY_ && v.stages == S_ && v.ws == WS_) \
+    return launch_variant<T, TY_, S_, WS_>(g, nbatch, omega_dev, x, y, nu, ek, out_scale, s, e, v.tz)
+  FIT_LV(4, 4, 0);
+  FIT_LV(8, 4, 0);
+  FIT_LV(16, 3, 0);
+  FIT_LV(4, 3, 0);
+  FIT_LV(8, 3, 0);
+  FIT_LV(4, 4, 1);
+  FIT_LV(8, 4, 1);
+  if constexpr (sizeof(T) == 4) {  // complex64 only
+    FIT_LV(4, 6, 1);
+    FIT_LV(8, 6, 1);
+    FIT_LV(16, 4, 1);
   }
+#undef FIT_LV
   fit_set_error("fused apply: no such variant");
   return FIT_EINVAL;
 }
@@ -678,21 +1033,25 @@ fit_status fit_launch_apply_fixed(fit_grid* g, int nbatch, const double* omega_d
   return launch_choice(g, choice, nbatch, omega_dev, x, y, prec, out_scale, s, e);
 }
 
-int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out4) {
+int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out6) {
   const long long key = (long long)nbatch * 2 + (prec == FIT_C64 ? 0 : 1);
   auto it = g->tuned.find(key);
   int c = it == g->tuned.end() ? -2 : it->second;
-  out4[0] = c;
+  out6[0] = c;
   if (c >= 0) {
     int n = 0;
     const Variant* v = variants(prec, &n);
-    out4[1] = TX;
-    out4[2] = v[c].ty;
-    out4[3] = v[c].tz;
-  } else {
-    out4[1] = 32;
-    out4[2] = 8;
-    out4[3] = 1;
+    out6[1] = TX;
+    out6[2] = v[c].ty;
+    out6[3] = v[c].tz;
+    out6[4] = v[c].stages;
+    out6[5] = v[c].ws;
+  } else {  // the generic kernel: 32 x 8 threads, one plane each
+    out6[1] = 32;
+    out6[2] = 8;
+    out6[3] = 1;
+    out6[4] = 0;
+    out6[5] = 0;
   }
   return c;
 }
@@ -705,9 +1064,9 @@ int fit_apply_variant_count(fit_prec prec) {
   return n;
 }
 
-fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out4) {
-  FIT_REQUIRE(g && out4 && nbatch >= 1, "fit_apply_tuned: bad argument");
-  fit_tuned_choice(g, prec, nbatch, out4);
+fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out6) {
+  FIT_REQUIRE(g && out6 && nbatch >= 1, "fit_apply_tuned: bad argument");
+  fit_tuned_choice(g, prec, nbatch, out6);
   return FIT_OK;
 }
 

@@ -153,4 +153,5 @@ def test_autotuner_records_a_choice():
         assert fit.fit_apply_tuned(g.h, 0, 1)["choice"] == -2
         g.apply([1e10], x, y, 0)
         t = fit.fit_apply_tuned(g.h, 0, 1)
-        assert t["choice"] >= -1 and t["tx"] == 32
+        assert t["choice"] >= -1 and t["tx"] == 32 and t["ws"] in (0, 1)
+        assert (t["stages"] > 0) == (t["choice"] >= 0)

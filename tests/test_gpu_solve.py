@@ -67,6 +67,29 @@ def test_small_lossy_batch(method, precond, use_graph):
         assert rr <= 1e-9, (i, rr, rep[i])
 
 
+def test_every_fused_variant_in_a_solve(monkeypatch):
+    """Every fused launch shape, forced in turn, inside a mixed-precision BiCGStab solve of a batch:
+    the inner complex64 applies carry the fused dot-product epilogues (<r^, A p>, then <t, s> and
+    <t, t>) and the outer complex128 apply the residual epilogue, so a wrong partial sum in any
+    variant shows as a solve that stalls or a solution the oracle's residual rejects."""
+    fit = fitlib()
+    from oracle import fit as F
+    nx, ny, nz = 66, 20, 14  # ragged tiles along x, y and z; nx even so complex64 rows stay 16-byte aligned
+    case = G.small_random(nx, ny, nz, seed=32, pec_frac=0.05)
+    mask = F.edge_mask(nx, ny, nz, case["pec"])
+    rhs = np.stack([G.random_vector(3 * nx * ny * nz, s) * (1 - mask) for s in (4, 5)])
+    freqs = [4e9, 9e9]
+    nvar = max(fit.fit_apply_variant_count(0), fit.fit_apply_variant_count(1))
+    for k in range(nvar):
+        monkeypatch.setenv("FIT_APPLY_KERNEL", f"fused:{k}")
+        st, rep, xs, bs, ws = _solve(case, freqs, 1e-9, rhs=rhs, method=0, precond=0, max_outer=400,
+                                     max_iter=20000)
+        assert st == 0, (k, rep)
+        for i in range(len(freqs)):
+            rr, _ = _oracle_relres(case, ws[i], xs[i], bs[i])
+            assert rr <= 1e-9, (k, i, rr, rep[i])
+
+
 def test_graph_and_host_loop_agree_exactly(monkeypatch):
     """The device-side loop (graph) and the host-driven loop run the same kernels in the same order.
     Each solve uses its own grid handle, whose autotuner could pick a different apply variant (a
