@@ -306,6 +306,7 @@ def main():
                        "omega_hz": float(case["freqs"][0]), "l2": "flushed between timed applies (512 MiB write "
                        "then 512 MiB read)", "parallelism": f"replicas{world}",
                        "autotuned_tile": [tuned["tx"], tuned["ty"], tuned["tz"]], "ring_stages": tuned["stages"],
+                       "l2_prefetch_planes": tuned["pf"],
                        "kernel_choice": tuned["choice"]},
             "roofline": roof, "clocks": clk.summary(), "step_stats": step_stats,
             "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ne, "d2h_bytes_per_step": 8 * ne},

@@ -174,17 +174,23 @@ fit_status fit_grid_info(const fit_grid* g, long long* out6);
 int fit_apply_variant_count(fit_prec prec);
 
 /* fit_apply_tuned -- the apply kernel the autotuner picked for (prec, nbatch) on this grid:
- *   out6[0] = -2 not tuned yet, -1 generic kernel, k >= 0 fused variant k
- *   out6[1..3] = tile TX, TY and planes per CTA (TZ; 0 = chosen at launch so that the tiles fill
- *               the resident CTAs in one balanced wave) of that kernel
- *   out6[4] = shared-memory ring stages (0 for the generic kernel)
- *   out6[5] = 0 generic or CTA-synchronous fused kernel, 1 warp-specialised fused kernel
- *             (one producer warp feeding the ring, one consumer warp per tile row).
+ *   out7[0] = -2 not tuned yet, -1 generic kernel, k >= 0 fused variant k
+ *   out7[1..3] = tile TX, TY and planes per CTA (TZ; 0 = chosen at launch so that the tiles fill
+ *               the resident CTAs in one balanced wave; -1 = one system's (column, plane) pairs
+ *               split evenly over the resident CTAs) of that kernel
+ *   out7[4] = shared-memory ring stages (0 for the generic kernel)
+ *   out7[5] = 0 generic or CTA-synchronous fused kernel, 1 warp-specialised fused kernel
+ *             (a copy-issuing warp and a masking warp feed the ring, one consumer warp per row)
+ *   out7[6] = L2 prefetch distance: planes of the tile requested into L2 this far ahead of
+ *             their copy into shared memory (0: none).
  * The autotuner runs on the first fit_apply / fit_solve with a new (prec, nbatch); it times every
  * candidate on the caller's stream (synchronising it) and caches the fastest in the handle.
+ * Candidates are timed from a cold L2: for the duration of the tuning the handle holds a scratch
+ * buffer of twice the L2 size (counted against fit_set_hbm_budget; if it does not fit, candidates
+ * are timed back to back instead).
  * Tests and experiments can force a kernel with the environment variable
  * FIT_APPLY_KERNEL=generic or FIT_APPLY_KERNEL=fused:<k>. */
-fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out6);
+fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out7);
 
 /* ---- learned right preconditioner (3-level 3D U-Net) ---------------------------------------------
  * Not in the paper: its matrix-free operator "cannot use black-box preconditioners" (Sec. I), and

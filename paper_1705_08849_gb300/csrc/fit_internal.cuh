@@ -104,9 +104,9 @@ fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, co
 // already tuned.  Must not be called while the stream is being captured.
 fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, fit_prec prec,
                           cudaStream_t s);
-// The cached choice: out6 = {choice (-1 generic, -2 untuned, >= 0 fused variant), TX, TY, TZ,
-// ring stages, warp-specialised (0/1)}.
-int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out6);
+// The cached choice: out7 = {choice (-1 generic, -2 untuned, >= 0 fused variant), TX, TY, TZ,
+// ring stages, warp-specialised (0/1), L2 prefetch distance in planes}.
+int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out7);
 // Number of partial-sum slots per system that the apply writes for an epilogue.
 long long fit_apply_partials(const fit_grid* g, fit_prec prec);
 

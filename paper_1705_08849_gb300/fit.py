@@ -233,12 +233,12 @@ def fit_apply_variant_count(prec):
 
 
 def fit_apply_tuned(g, prec, nbatch):
-    """The autotuner's pick for (prec, nbatch): dict(choice, tx, ty, tz, stages, ws); choice -1 = generic
-    kernel, -2 = not tuned yet, k >= 0 = fused variant k; tz 0 = balanced at launch; ws 1 = the
-    warp-specialised fused kernel."""
-    out = (ct.c_int * 6)()
+    """The autotuner's pick for (prec, nbatch): dict(choice, tx, ty, tz, stages, ws, pf); choice -1 =
+    generic kernel, -2 = not tuned yet, k >= 0 = fused variant k; tz 0 = balanced at launch; ws 1 =
+    the warp-specialised fused kernel; pf = L2 prefetch distance in planes."""
+    out = (ct.c_int * 7)()
     _check(lib().fit_apply_tuned(g, prec, nbatch, out), "fit_apply_tuned")
-    return dict(choice=out[0], tx=out[1], ty=out[2], tz=out[3], stages=out[4], ws=out[5])
+    return dict(choice=out[0], tx=out[1], ty=out[2], tz=out[3], stages=out[4], ws=out[5], pf=out[6])
 
 
 def fit_jacobi(g, omega, x, y, prec=FIT_C128, stream=None):

@@ -135,11 +135,14 @@ def test_apply_sampled_package256_c64(kernel):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_every_fused_variant(prec, monkeypatch):
-    """Each launch shape the autotuner may pick, forced in turn, on a ragged batched grid."""
+    """Each launch shape the autotuner may pick, forced in turn, on a ragged grid: one system (where
+    the warp-specialised kernel splits the (column, plane) pairs evenly over the CTAs, so ranges
+    start and end inside columns) and a batch of two (tiles of whole z-chunks)."""
     fit = fitlib()
     case = G.small_random(70, 27, 37, seed=8, pec_frac=0.07)
     for k in range(fit.fit_apply_variant_count(prec)):
         monkeypatch.setenv("FIT_APPLY_KERNEL", f"fused:{k}")
+        _check_case(case, [2 * np.pi * 5e9], prec, seed=100 + k)
         _check_case(case, [2 * np.pi * 2e9, 2 * np.pi * 11e9], prec, seed=k)
 
 
@@ -154,4 +157,4 @@ def test_autotuner_records_a_choice():
         g.apply([1e10], x, y, 0)
         t = fit.fit_apply_tuned(g.h, 0, 1)
         assert t["choice"] >= -1 and t["tx"] == 32 and t["ws"] in (0, 1)
-        assert (t["stages"] > 0) == (t["choice"] >= 0)
+        assert (t["stages"] > 0) == (t["choice"] >= 0) and t["pf"] >= 0

@@ -82,12 +82,15 @@ def test_every_fused_variant_in_a_solve(monkeypatch):
     nvar = max(fit.fit_apply_variant_count(0), fit.fit_apply_variant_count(1))
     for k in range(nvar):
         monkeypatch.setenv("FIT_APPLY_KERNEL", f"fused:{k}")
-        st, rep, xs, bs, ws = _solve(case, freqs, 1e-9, rhs=rhs, method=0, precond=0, max_outer=400,
-                                     max_iter=20000)
-        assert st == 0, (k, rep)
-        for i in range(len(freqs)):
-            rr, _ = _oracle_relres(case, ws[i], xs[i], bs[i])
-            assert rr <= 1e-9, (k, i, rr, rep[i])
+        # a batch of two, then one system alone (the warp-specialised kernel then splits the
+        # (column, plane) pairs evenly over its CTAs and writes one partial sum per CTA)
+        for fs, bs_in in ((freqs, rhs), (freqs[:1], rhs[:1])):
+            st, rep, xs, bs, ws = _solve(case, fs, 1e-9, rhs=bs_in, method=0, precond=0, max_outer=400,
+                                         max_iter=20000)
+            assert st == 0, (k, len(fs), rep)
+            for i in range(len(fs)):
+                rr, _ = _oracle_relres(case, ws[i], xs[i], bs[i])
+                assert rr <= 1e-9, (k, len(fs), i, rr, rep[i])
 
 
 def test_graph_and_host_loop_agree_exactly(monkeypatch):
