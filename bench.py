@@ -32,6 +32,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_DOF_C64 = 28.0   # read x 8 + write y 8 + M_nu, M_eps, M_kappa 3 x 4 (compulsory, per unknown)
+# learned preconditioner network: (voxel level, Cin, Cout) of the 3x3x3 convs (level l has (n/2^l)^3
+# voxels), the 2x2x2 transposed convs (one tap per output voxel) and the 1x1x1 head
+UNET_CONV3 = [(0, 16, 16), (0, 16, 16), (1, 16, 32), (1, 32, 32), (2, 32, 64), (2, 64, 64), (1, 64, 32), (1, 32, 32),
+              (0, 32, 16), (0, 16, 16)]
+UNET_TCONV = [(1, 64, 32), (0, 32, 16)]
+UNET_HEAD = (0, 16, 6)
+
+
+def unet_flops(nx, ny, nz):
+    """Multiply-add flops (2 per MAC) of one network application on an nx x ny x nz grid."""
+    v = lambda lvl: (nx >> lvl) * (ny >> lvl) * (nz >> lvl)
+    f = sum(2 * 27 * ci * co * v(l) for l, ci, co in UNET_CONV3)
+    f += sum(2 * ci * co * v(l) for l, ci, co in UNET_TCONV)
+    l, ci, co = UNET_HEAD
+    return f + 2 * ci * co * v(l)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -184,6 +199,38 @@ def time_solves(fit, torch, case, kinds, max_iter):
     return out
 
 
+def time_unet(fit, torch, case, steps, warmup):
+    """One application of the learned preconditioner's network (bf16 NDHWC input of 16 channels ->
+    6 FP32 channels) on the workload's grid, CUDA-event timed after warm-up; flops from the layer
+    table, against the BF16 tensor peak."""
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    net = fit.UNet(seed=1)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    xin = torch.randn(nz, ny, nx, 16, device="cuda", generator=gen).to(torch.bfloat16)
+    yout = torch.empty(nz, ny, nx, 6, device="cuda", dtype=torch.float32)
+    for _ in range(max(3, warmup)):
+        net.forward(nx, ny, nz, xin, yout)
+    torch.cuda.synchronize()
+    n = max(5, min(steps, 200))
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in evs:
+        a.record(stream)
+        net.forward(nx, ny, nz, xin, yout)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median([a.elapsed_time(b) for a, b in evs])
+    flops = unet_flops(nx, ny, nz)
+    peaks, kind = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    net.close()
+    return {"metric": "learned preconditioner application", "unit": "ms", "value": ms, "higher_is_better": False,
+            "workload": case["name"], "grid": [nx, ny, nz], "steps": n, "gflop": flops / 1e9,
+            "roofline": {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_kind": f"{kind} bf16 burst"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,7 +239,8 @@ def main():
     ap.add_argument("--impl", default="fit", choices=["fit", "reference"])
     ap.add_argument("--workload", default="layered128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve"],
+    ap.add_argument("--batch", type=int, default=1, help="systems (frequencies) per apply in the apply mode")
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet"],
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
     ap.add_argument("--solve", default="mixed", help="comma list of solves to time: mixed, c128, none")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
@@ -221,6 +269,10 @@ def main():
 
     case = _workload(args.workload)
     kinds = [k for k in args.solve.split(",") if k in ("mixed", "c128")]
+    if args.mode == "unet":
+        if rank == 0:
+            print(json.dumps(time_unet(fit, torch, case, args.steps, args.warmup)), flush=True)
+        return
     if args.mode == "solve":
         res = time_solves(fit, torch, case, kinds, args.max_iter)
         if rank == 0:
@@ -228,12 +280,14 @@ def main():
                               "solves": res}), flush=True)
         return
     ne = 3 * case["nx"] * case["ny"] * case["nz"]
-    w = 2 * np.pi * float(case["freqs"][0])
+    B = max(1, args.batch)
+    w0 = 2 * np.pi * float(case["freqs"][0])
+    w = [w0 * (1.0 + 0.5 * b / B) for b in range(B)]  # B frequencies from f0 to 1.5 f0
     g = fit.Grid.from_case(case)
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1234 + rank)
-    x = torch.randn(ne, dtype=torch.complex64, device="cuda", generator=gen)
+    x = torch.randn(B * ne, dtype=torch.complex64, device="cuda", generator=gen)
     y = torch.empty_like(x)
     flush_w = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     flush_r = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
@@ -243,7 +297,7 @@ def main():
         flush_r.sum()
 
     for _ in range(args.warmup):
-        g.apply([w], x, y, fit.FIT_C64)
+        g.apply(w, x, y, fit.FIT_C64)
     torch.cuda.synchronize()
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -254,7 +308,7 @@ def main():
         for k in range(args.steps):
             flush()
             evs[k][0].record(stream)
-            g.apply([w], x, y, fit.FIT_C64)
+            g.apply(w, x, y, fit.FIT_C64)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -267,7 +321,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
-    value = world * ne * args.steps / (total_ms * 1e-3) / 1e9
+    value = world * B * ne * args.steps / (total_ms * 1e-3) / 1e9
 
     # end to end through the C ABI with pinned host buffers
     xh = x.cpu().pin_memory()
@@ -276,26 +330,28 @@ def main():
     k_e2e = max(10, min(args.steps, 200))
     for _ in range(3):
         xd.copy_(xh, non_blocking=True)
-        g.apply([w], xd, y, fit.FIT_C64)
+        g.apply(w, xd, y, fit.FIT_C64)
         yh.copy_(y, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(k_e2e):
         xd.copy_(xh, non_blocking=True)
-        g.apply([w], xd, y, fit.FIT_C64)
+        g.apply(w, xd, y, fit.FIT_C64)
         yh.copy_(y, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / k_e2e
-    e2e_val = world * ne / (e2e_ms * 1e-3) / 1e9
+    e2e_val = world * B * ne / (e2e_ms * 1e-3) / 1e9
 
-    tuned = fit.fit_apply_tuned(g.h, fit.FIT_C64, 1)
+    tuned = fit.fit_apply_tuned(g.h, fit.FIT_C64, B)
     peaks, kind = _peaks()
-    achieved = BYTES_PER_DOF_C64 * ne / (ms_step * 1e-3) / 1e9
+    # per unknown: x and y move once per system, the coefficients once per launch (shared by B systems)
+    bytes_per_dof = 16.0 + (BYTES_PER_DOF_C64 - 16.0) / B
+    achieved = bytes_per_dof * B * ne / (ms_step * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind, "traffic": None,
-            "bytes_per_dof": BYTES_PER_DOF_C64,
+            "bytes_per_dof": bytes_per_dof,
             "kernel": (("ws_apply_kernel" if tuned["ws"] else "fused_apply_kernel") if tuned["choice"] >= 0
                        else "apply_generic_kernel")}
 
@@ -303,13 +359,13 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": [case["nx"], case["ny"], case["nz"]], "unknowns": ne,
-                       "omega_hz": float(case["freqs"][0]), "l2": "flushed between timed applies (512 MiB write "
+                       "batch": B, "omega_hz": float(case["freqs"][0]), "l2": "flushed between timed applies (512 MiB write "
                        "then 512 MiB read)", "parallelism": f"replicas{world}",
                        "autotuned_tile": [tuned["tx"], tuned["ty"], tuned["tz"]], "ring_stages": tuned["stages"],
                        "l2_prefetch_planes": tuned["pf"],
                        "kernel_choice": tuned["choice"]},
             "roofline": roof, "clocks": clk.summary(), "step_stats": step_stats,
-            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ne, "d2h_bytes_per_step": 8 * ne},
+            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * B * ne, "d2h_bytes_per_step": 8 * B * ne},
             "gpu_launches": args.steps}
 
     g.close()

@@ -83,6 +83,8 @@ struct FusedArgs {
   const double* omega;
   int* err;
   int nx, ny, nz, tz, nzc, ntx, nty, ntiles;
+  int nb;    // systems in the batch; tile t = (chunk, row, column) * nb + b, so that CTAs running at the
+             // same time work on one column for several systems and share its coefficients in L2
   int pf;    // L2 prefetch distance in planes ahead of the plane being loaded (0: none)
   int flat;  // 1: one system, the (column, plane) pairs split evenly over the CTAs (see ws kernel)
   long long ne;
@@ -233,8 +235,8 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
   const int nr = (ty + 1) * L::NW + 3 * (tx + 4);
 
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const int bx = t % a.ntx, by = (t / a.ntx) % a.nty;
-    const int zc = (t / (a.ntx * a.nty)) % a.nzc, b = t / (a.ntx * a.nty * a.nzc);
+    const int b = t % a.nb, c = t / a.nb;
+    const int bx = c % a.ntx, by = (c / a.ntx) % a.nty, zc = c / (a.ntx * a.nty);
     if (epi.status && epi.status[b] != 0) continue;  // uniform over the CTA
     const int i0 = bx * TX, j0 = by * TY;
     const int k0 = zc * a.tz, k1 = min(a.nz, k0 + a.tz);
@@ -513,7 +515,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
 
   // This CTA's work, one segment (bx, by, b, planes k0 .. k1-1) at a time; every role walks the
   // same sequence.  Tiled: tiles blockIdx.x, blockIdx.x + gridDim.x, ... of ntx*nty*nzc*nbatch
-  // chunks of tz planes; the partial sums of a tile go to its own slot.  Flat (one system): the
+  // chunks of tz planes, the system index fastest; the partial sums of a tile go to its own slot.  Flat (one system): the
   // ntx*nty*nz (column, plane) pairs, column-major, are cut into gridDim.x equal contiguous ranges,
   // one per CTA, so every resident CTA gets the same work; a range may cover the end of one column
   // and the start of the next, and the CTA's partial sums go to slot blockIdx.x once at the end.
@@ -541,10 +543,11 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
     if (tnext >= a.ntiles) return false;
     const int t = tnext;
     tnext += gridDim.x;
-    bx = t % a.ntx;
-    by = (t / a.ntx) % a.nty;
-    const int zc = (t / (a.ntx * a.nty)) % a.nzc;
-    b = t / (a.ntx * a.nty * a.nzc);
+    b = t % a.nb;
+    const int c = t / a.nb;
+    bx = c % a.ntx;
+    by = (c / a.ntx) % a.nty;
+    const int zc = c / (a.ntx * a.nty);
     k0 = zc * a.tz;
     k1 = min(a.nz, k0 + a.tz);
     slot = (zc * a.nty + by) * a.ntx + bx;
@@ -913,6 +916,7 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
   a.out_scale = (T)out_scale;
   a.pf = pf;
   a.flat = 0;
+  a.nb = nbatch;
   dim3 block(TX, WS ? TY + 2 : TY, 1);
   const bool ku = e.mode == FIT_EPI_DOT_U || e.mode == FIT_EPI_RESID;
   int smem = ku ? Layout<T, TY, true>::smem(S) : Layout<T, TY, false>::smem(S);
