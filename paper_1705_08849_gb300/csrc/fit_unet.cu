@@ -126,7 +126,55 @@ void refresh_weights(fit_unet* u, cudaStream_t s) {
   u->weights_dirty = false;
 }
 
-// conv3 launch: picks the (CIN, NC) instantiation; in2/out2 implement concat / split
+// conv3 launch of one (CIN, NC, TY) instantiation: the z-chunk length is chosen so that the
+// (x, y, channel-block) columns times the chunks fill the resident CTAs about once
+template <int CIN, int NC, int TY>
+fit_status launch_conv3(const unet::ConvArgs& a, cudaStream_t s) {
+  auto kern = unet::conv3_kernel<CIN, NC, TY>;
+  const int smem = unet::Conv3Shape<CIN, NC, TY>::smem();
+  static int per_sm = 0, nsm = 0;  // per instantiation, looked up once
+  if (per_sm == 0) {
+    int dev = 0;
+    FIT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FIT_CHECK_CUDA(cudaGetDevice(&dev));
+    FIT_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int p = 0;
+    FIT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kern, 256, smem));
+    if (p < 1) {
+      fit_set_error("U-Net: conv tile does not fit on an SM");
+      return FIT_EINVAL;
+    }
+    per_sm = p;
+  }
+  const int gx = (a.nx + unet::CX - 1) / unet::CX, gy = (a.ny + TY - 1) / TY, nblk = (a.cout + NC - 1) / NC;
+  const long long cols = (long long)gx * gy * nblk;
+  const long long per_col = std::max(1LL, (long long)per_sm * nsm / cols);
+  const int tz = (int)std::max(2LL, ((long long)a.nz + per_col - 1) / per_col);
+  const int nzc = (a.nz + tz - 1) / tz;
+  dim3 grid(gx, gy, (unsigned)(nzc * nblk));
+  kern<<<grid, 256, smem, s>>>(a, tz);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+// 2x2x2 transposed conv from an mx x my x mz coarse grid to the 2x finer one
+template <int CIN, int COUT>
+fit_status tconv_fwd(const bf16* in, const float* w, const float* b, bf16* out, int mx, int my, int mz,
+                     cudaStream_t s) {
+  auto kern = unet::tconv_fwd_kernel<CIN, COUT>;
+  constexpr int smem = unet::tconv_smem<CIN, COUT>();
+  static bool attr = false;
+  if (!attr) {
+    FIT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  const long long n = 8LL * mx * my * mz;
+  kern<<<(unsigned)((n + 255) / 256), 256, smem, s>>>(in, w, b, out, mx, my, mz);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+// conv3 launch: picks the (CIN, NC, TY) instantiation; in2/out2 implement concat / split
 fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w, const float* bias, bf16* out1, int o1,
                  bf16* out2, int o2, int nx, int ny, int nz, int relu, cudaStream_t s) {
   unet::ConvArgs a;
@@ -146,20 +194,11 @@ fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w
   a.nz = nz;
   a.relu = relu;
   const int cin = c1 + c2;
-  const int nc = a.cout >= 32 ? 32 : 16;
-  dim3 grid((nx + unet::CX - 1) / unet::CX, (ny + unet::CY - 1) / unet::CY, (unsigned)(nz * ((a.cout + nc - 1) / nc)));
-  auto go = [&](auto kern, int smem) -> fit_status {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<grid, 256, smem, s>>>(a);
-    FIT_CHECK_CUDA(cudaGetLastError());
-    return FIT_OK;
-  };
-  if (cin == 16 && nc == 16) return go(unet::conv3_kernel<16, 16>, unet::conv3_smem<16, 16>());
-  if (cin == 16 && nc == 32) return go(unet::conv3_kernel<16, 32>, unet::conv3_smem<16, 32>());
-  if (cin == 32 && nc == 16) return go(unet::conv3_kernel<32, 16>, unet::conv3_smem<32, 16>());
-  if (cin == 32 && nc == 32) return go(unet::conv3_kernel<32, 32>, unet::conv3_smem<32, 32>());
-  if (cin == 64 && nc == 16) return go(unet::conv3_kernel<64, 16>, unet::conv3_smem<64, 16>());
-  if (cin == 64 && nc == 32) return go(unet::conv3_kernel<64, 32>, unet::conv3_smem<64, 32>());
+  // shared memory per CTA: (16,16,8) 86 KB, (16,32,8) 107 KB, (32,16,4) 100 KB, (64,16,4) 180 KB
+  if (cin == 16 && a.cout <= 16) return launch_conv3<16, 16, 8>(a, s);
+  if (cin == 16) return launch_conv3<16, 32, 8>(a, s);
+  if (cin == 32) return launch_conv3<32, 16, 4>(a, s);
+  if (cin == 64) return launch_conv3<64, 16, 4>(a, s);
   fit_set_error("U-Net: unsupported conv shape");
   return FIT_EINVAL;
 }
@@ -178,19 +217,19 @@ fit_status forward(fit_unet* u, const bf16* X0, cudaStream_t s) {
   auto B = [&](int l) { return u->p + u->boff[l]; };
   UCK(conv3(X0, 16, nullptr, 0, u->wf[C1A], B(C1A), u->A1a, 16, nullptr, 0, nx, ny, nz, 1, s));
   UCK(conv3(u->A1a, 16, nullptr, 0, u->wf[C1B], B(C1B), u->S1, 16, nullptr, 0, nx, ny, nz, 1, s));
-  unet::pool_fwd_kernel<<<nblocks(N / 8 * 16), 256, 0, s>>>(u->S1, u->P1, 16, nx, ny, nz);
+  unet::pool_fwd_kernel<<<(unsigned)((N / 8 * 2 + 255) / 256), 256, 0, s>>>(u->S1, u->P1, 16, nx, ny, nz);
   UCK(conv3(u->P1, 16, nullptr, 0, u->wf[C2A], B(C2A), u->A2a, 32, nullptr, 0, mx, my, mz, 1, s));
   UCK(conv3(u->A2a, 32, nullptr, 0, u->wf[C2B], B(C2B), u->S2, 32, nullptr, 0, mx, my, mz, 1, s));
-  unet::pool_fwd_kernel<<<nblocks(N / 64 * 32), 256, 0, s>>>(u->S2, u->P2, 32, mx, my, mz);
+  unet::pool_fwd_kernel<<<(unsigned)((N / 64 * 4 + 255) / 256), 256, 0, s>>>(u->S2, u->P2, 32, mx, my, mz);
   UCK(conv3(u->P2, 32, nullptr, 0, u->wf[C3A], B(C3A), u->A3a, 64, nullptr, 0, qx, qy, qz, 1, s));
   UCK(conv3(u->A3a, 64, nullptr, 0, u->wf[C3B], B(C3B), u->B3, 64, nullptr, 0, qx, qy, qz, 1, s));
-  unet::tconv_fwd_kernel<<<nblocks(N / 8 * 32), 256, 0, s>>>(u->B3, u->p + u->woff[T2], B(T2), u->U2, 64, 32, mx, my, mz);
+  UCK((tconv_fwd<64, 32>(u->B3, u->p + u->woff[T2], B(T2), u->U2, qx, qy, qz, s)));
   UCK(conv3(u->S2, 32, u->U2, 32, u->wf[C2C], B(C2C), u->A2c, 32, nullptr, 0, mx, my, mz, 1, s));
   UCK(conv3(u->A2c, 32, nullptr, 0, u->wf[C2D], B(C2D), u->B2, 32, nullptr, 0, mx, my, mz, 1, s));
-  unet::tconv_fwd_kernel<<<nblocks(N * 16), 256, 0, s>>>(u->B2, u->p + u->woff[T1], B(T1), u->U1, 32, 16, nx, ny, nz);
+  UCK((tconv_fwd<32, 16>(u->B2, u->p + u->woff[T1], B(T1), u->U1, mx, my, mz, s)));
   UCK(conv3(u->S1, 16, u->U1, 16, u->wf[C1C], B(C1C), u->A1c, 16, nullptr, 0, nx, ny, nz, 1, s));
   UCK(conv3(u->A1c, 16, nullptr, 0, u->wf[C1D], B(C1D), u->B1, 16, nullptr, 0, nx, ny, nz, 1, s));
-  unet::head_fwd_kernel<<<nblocks(N * 6), 256, 0, s>>>(u->B1, u->p + u->woff[HEAD], B(HEAD), u->Y, 16, 6, N);
+  unet::head_fwd_kernel<16, 6><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(u->B1, u->p + u->woff[HEAD], B(HEAD), u->Y, (int)N);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }

@@ -14,10 +14,10 @@ namespace unet {
 // ------------------------------------------------------------------------------------------------
 // 3x3x3 convolution, stride 1, zero padding 1, as an implicit GEMM on the tensor cores:
 //   out[v][co] = act( bias[co] + sum_{tap, ci} in[v + off(tap)][ci] * W[tap][co][ci] )
-// M = output voxels (a CTA owns 32 x 4 x 1 of them, a warp 16 along x), N = output channels (NC per
-// CTA), K = 27 * CIN.  The input halo tile (34 x 6 x 3 voxels) and the CTA's weight slice are
-// staged in shared memory (rows padded by 8 channels so ldmatrix is conflict-free) and fed to
-// mma.sync m16n8k16 (bf16 x bf16 -> f32) through ldmatrix.
+// M = output voxels (a CTA owns 32 x TY of them per plane and marches along z, a warp 16 or 32
+// along x), N = output channels (NC per CTA), K = 27 * CIN.  Input halo planes and the CTA's weight
+// slice are staged in shared memory and fed to mma.sync m16n8k16 (bf16 x bf16 -> f32) through
+// ldmatrix.
 // Two input sources implement the skip concatenation (channels [0, c1) from in1, [c1, CIN) from
 // in2); two outputs split the output channels ([0, o1) to out1, the rest to out2).  The backward
 // data pass (dgrad) is this same kernel on flipped, transposed weights.
@@ -36,8 +36,7 @@ struct ConvArgs {
   int relu;
 };
 
-constexpr int CX = 32, CY = 4;                 // output voxels per CTA (x, y)
-constexpr int HX = CX + 2, HY = CY + 2, HZ = 3;  // input halo tile
+constexpr int CX = 32;  // output voxels per CTA along x
 
 __device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -56,98 +55,148 @@ __device__ inline void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <int CIN, int NC>
-__global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a) {
-  constexpr int RS = CIN + 8;  // padded channel stride (bf16) of a staged row
-  extern __shared__ __align__(16) unsigned char smem[];
-  bf16* in_s = (bf16*)smem;                 // [HZ][HY][HX][RS]
-  bf16* w_s = in_s + HZ * HY * HX * RS;     // [27][NC][RS]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * CY;
-  const int nblk_n = (a.cout + NC - 1) / NC;
-  const int z = blockIdx.z / nblk_n, n0 = (blockIdx.z % nblk_n) * NC;
+__device__ inline void cp_async16(uint32_t dst, const void* src, int src_bytes) {  // src_bytes 0: zero fill
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-  // stage the input halo tile, 8 channels (16 bytes) per copy, zero outside the grid
-  constexpr int CH8 = CIN / 8;
-  for (int q = tid; q < HZ * HY * HX * CH8; q += 256) {
-    const int c8 = q % CH8, vox = q / CH8;
-    const int hx = vox % HX, hy = (vox / HX) % HY, hz = vox / (HX * HY);
-    const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z - 1 + hz;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gx >= 0 && gy >= 0 && gz >= 0 && gx < a.nx && gy < a.ny && gz < a.nz) {
-      const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * gz);
-      const int c = c8 * 8;
-      if (c < a.c1) v = *reinterpret_cast<const uint4*>(a.in1 + gv * a.c1 + c);
-      else v = *reinterpret_cast<const uint4*>(a.in2 + gv * a.c2 + (c - a.c1));
+// The CTA owns a 32 x TY tile of output voxels in (x, y) and a chunk of tz planes along z, for NC
+// output channels.  Its weight slice is staged once; input halo planes (34 x (TY+2) voxels x CIN
+// channels, rows padded by 8 channels so ldmatrix is conflict-free) live in a ring of 4: planes
+// z-1, z, z+1 are read while plane z+2 is copied in with cp.async (zero fill outside the grid).
+// Each of the 8 warps owns TY/4 m16 tiles (16 voxels along x) and all NC channels; the B fragments
+// of a (tap, k-chunk) are loaded once and used for all of the warp's tiles.
+template <int CIN, int NC, int TY>
+struct Conv3Shape {
+  static constexpr int RS = CIN + 8;          // padded channel stride (bf16) of a staged voxel
+  static constexpr int PX = CX + 2, PY = TY + 2;
+  static constexpr int PLANE = PX * PY * RS;  // bf16 per staged halo plane
+  static constexpr int MT = TY / 4;           // m16 tiles per warp (2 * TY tiles over 8 warps)
+  static constexpr int smem() { return (27 * NC * RS + 4 * PLANE) * (int)sizeof(bf16); }
+};
+
+template <int CIN, int NC, int TY>
+__global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a, int tz) {
+  using SH = Conv3Shape<CIN, NC, TY>;
+  constexpr int RS = SH::RS, PX = SH::PX, PY = SH::PY, MT = SH::MT, CH8 = CIN / 8;
+  static_assert(TY % 4 == 0 && CIN % 16 == 0 && NC % 16 == 0, "conv3 tile shape");
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* w_s = (bf16*)smem;             // [27][NC][RS]
+  bf16* ring = w_s + 27 * NC * RS;     // [4][PY][PX][RS]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * TY;
+  const int nblk_n = (a.cout + NC - 1) / NC;
+  const int zc = blockIdx.z / nblk_n, n0 = (blockIdx.z % nblk_n) * NC;
+  const int z0 = zc * tz, z1 = min(a.nz, z0 + tz);
+  if (z0 >= z1) return;
+
+  // plane p goes to ring slot (p - (z0 - 1)) % 4
+  auto load_plane = [&](int p) {
+    bf16* dst = ring + ((p - (z0 - 1)) & 3) * SH::PLANE;
+    for (int q = tid; q < PX * PY * CH8; q += 256) {
+      const int c8 = q % CH8, vox = q / CH8;
+      const int hx = vox % PX, hy = vox / PX;
+      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+      const bool in = gx >= 0 && gy >= 0 && p >= 0 && gx < a.nx && gy < a.ny && p < a.nz;
+      const void* src = a.in1;  // a valid address even when nothing is read
+      if (in) {
+        const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * p);
+        const int c = c8 * 8;
+        src = c < a.c1 ? (const void*)(a.in1 + gv * a.c1 + c) : (const void*)(a.in2 + gv * a.c2 + (c - a.c1));
+      }
+      cp_async16(smem_addr(dst + vox * RS + c8 * 8), src, in ? 16 : 0);
     }
-    *reinterpret_cast<uint4*>(in_s + vox * RS + c8 * 8) = v;
-  }
-  // stage this CTA's slice of the weights (output channels n0 .. n0+NC-1)
+  };
+  // weights (output channels n0 .. n0+NC-1) and the first three planes: one copy group
   for (int q = tid; q < 27 * NC * CH8; q += 256) {
     const int c8 = q % CH8, row = q / CH8;
     const int tap = row / NC, n = row % NC;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (n0 + n < a.cout) v = *reinterpret_cast<const uint4*>(a.w + ((long long)tap * a.cout + n0 + n) * CIN + c8 * 8);
-    *reinterpret_cast<uint4*>(w_s + row * RS + c8 * 8) = v;
+    const bool in = n0 + n < a.cout;
+    const void* src = in ? (const void*)(a.w + ((long long)tap * a.cout + n0 + n) * CIN + c8 * 8) : (const void*)a.w;
+    cp_async16(smem_addr(w_s + row * RS + c8 * 8), src, in ? 16 : 0);
   }
-  __syncthreads();
+  load_plane(z0 - 1);
+  load_plane(z0);
+  load_plane(z0 + 1);
+  cp_async_commit();
 
-  // warp tile: 16 voxels along x (one y row) x NC channels
-  const int wy = warp >> 1, wx = (warp & 1) * 16;
-  float acc[NC / 8][4];
+  const int arow = lane & 15, ahalf = lane >> 4;  // A: row / k-half this lane addresses
+  const int bm = lane >> 3, brow = lane & 7;      // B: matrix / row this lane addresses
+  for (int z = z0; z < z1; ++z) {
+    if (z + 2 <= z1) load_plane(z + 2);  // plane z1 is the last one the chunk reads
+    cp_async_commit();                   // (possibly empty) group of plane z + 2
+    cp_async_wait<1>();                  // everything but that group has landed: planes z-1 .. z+1
+    __syncthreads();
+
+    float acc[MT][NC / 8][4];
 #pragma unroll
-  for (int t = 0; t < NC / 8; ++t)
+    for (int m = 0; m < MT; ++m)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
-  const int arow = lane & 15, ahalf = lane >> 4;       // A: row / k-half this lane addresses
-  const int bm = lane >> 3, brow = lane & 7;           // B: matrix / row this lane addresses
-  for (int tap = 0; tap < 27; ++tap) {
-    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-    const bf16* arow_p = in_s + ((dz * HY + wy + dy) * HX + wx + arow + dx) * RS + ahalf * 8;
+      for (int t = 0; t < NC / 8; ++t)
 #pragma unroll
-    for (int kc = 0; kc < CIN / 16; ++kc) {
-      uint32_t a0, a1, a2, a3;
-      ldsm_x4(smem_addr(arow_p + kc * 16), a0, a1, a2, a3);
+        for (int q = 0; q < 4; ++q) acc[m][t][q] = 0.f;
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+      const bf16* plane = ring + ((z - 1 + dz - (z0 - 1)) & 3) * SH::PLANE;
 #pragma unroll
-      for (int np = 0; np < NC / 16; ++np) {
-        const int n = np * 16 + (bm >> 1) * 8 + brow;
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4(smem_addr(w_s + (tap * NC + n) * RS + kc * 16 + (bm & 1) * 8), b0, b1, b2, b3);
-        mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-        mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+      for (int kc = 0; kc < CIN / 16; ++kc) {
+        uint32_t af[MT][4];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+          const int tile = warp * MT + m;            // 2 tiles per output row
+          const int row = tile >> 1, xh = (tile & 1) * 16;
+          const bf16* ap = plane + ((row + dy) * PX + xh + arow + dx) * RS + ahalf * 8 + kc * 16;
+          ldsm_x4(smem_addr(ap), af[m][0], af[m][1], af[m][2], af[m][3]);
+        }
+#pragma unroll
+        for (int np = 0; np < NC / 16; ++np) {
+          const int n = np * 16 + (bm >> 1) * 8 + brow;
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4(smem_addr(w_s + (tap * NC + n) * RS + kc * 16 + (bm & 1) * 8), b0, b1, b2, b3);
+#pragma unroll
+          for (int m = 0; m < MT; ++m) {
+            mma_bf16(acc[m][2 * np], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
+            mma_bf16(acc[m][2 * np + 1], af[m][0], af[m][1], af[m][2], af[m][3], b2, b3);
+          }
+        }
       }
     }
-  }
-  // epilogue: bias, ReLU, bf16, split over the two outputs
-  const int gy = y0 + wy;
-  if (gy >= a.ny) return;
+    // epilogue: bias, ReLU, bf16, split over the two outputs
 #pragma unroll
-  for (int t = 0; t < NC / 8; ++t) {
+    for (int m = 0; m < MT; ++m) {
+      const int tile = warp * MT + m;
+      const int gy = y0 + (tile >> 1);
+      if (gy >= a.ny) continue;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int gx = x0 + wx + (lane >> 2) + 8 * h;
-      const int co = n0 + t * 8 + 2 * (lane & 3);
-      if (gx >= a.nx || co >= a.cout) continue;
-      float v0 = acc[t][2 * h], v1 = acc[t][2 * h + 1];
-      if (a.bias) {
-        v0 += a.bias[co];
-        v1 += a.bias[co + 1];
+      for (int t = 0; t < NC / 8; ++t) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int gx = x0 + (tile & 1) * 16 + (lane >> 2) + 8 * h;
+          const int co = n0 + t * 8 + 2 * (lane & 3);
+          if (gx >= a.nx || co >= a.cout) continue;
+          float v0 = acc[m][t][2 * h], v1 = acc[m][t][2 * h + 1];
+          if (a.bias) {
+            v0 += a.bias[co];
+            v1 += a.bias[co + 1];
+          }
+          if (a.relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+          }
+          const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * z);
+          __nv_bfloat162 pv = __floats2bfloat162_rn(v0, v1);
+          if (co < a.o1) *reinterpret_cast<__nv_bfloat162*>(a.out1 + gv * a.o1 + co) = pv;
+          else *reinterpret_cast<__nv_bfloat162*>(a.out2 + gv * a.o2 + (co - a.o1)) = pv;
+        }
       }
-      if (a.relu) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
-      }
-      const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * z);
-      __nv_bfloat162 pv = __floats2bfloat162_rn(v0, v1);
-      if (co < a.o1) *reinterpret_cast<__nv_bfloat162*>(a.out1 + gv * a.o1 + co) = pv;
-      else *reinterpret_cast<__nv_bfloat162*>(a.out2 + gv * a.o2 + (co - a.o1)) = pv;
     }
+    __syncthreads();  // plane z-1's slot is refilled (with plane z+3) in the next step
   }
-}
-
-template <int CIN, int NC>
-inline int conv3_smem() {
-  return (HZ * HY * HX * (CIN + 8) + 27 * NC * (CIN + 8)) * (int)sizeof(bf16);
+  cp_async_wait<0>();  // no copy is left in flight when the CTA retires
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -247,19 +296,31 @@ __global__ void __launch_bounds__(256) conv3_wgrad_kernel(WgradArgs a) {
 // ---- pooling ------------------------------------------------------------------------------------
 // out (coarse, n/2 per axis) = mean of the 8 children; backward: each child gets dout / 8
 __global__ void pool_fwd_kernel(const bf16* in, bf16* out, int c, int nx, int ny, int nz) {
-  const int mx = nx / 2, my = ny / 2, mz = nz / 2;
-  const long long n = (long long)mx * my * mz * c;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(t % c);
-    const long long v = t / c;
-    const int X = (int)(v % mx), Y = (int)((v / mx) % my), Z = (int)(v / ((long long)mx * my));
-    float s = 0.f;
-    for (int q = 0; q < 8; ++q) {
-      const int x = 2 * X + (q & 1), y = 2 * Y + ((q >> 1) & 1), z = 2 * Z + (q >> 2);
-      s += __bfloat162float(in[(x + (long long)nx * (y + (long long)ny * z)) * c + ch]);
+  // one thread per (coarse voxel, group of 8 channels): eight 16-byte loads, one 16-byte store
+  const int mx = nx / 2, my = ny / 2, mz = nz / 2, g8 = c / 8;
+  const int n = mx * my * mz * g8;  // below 2^31 for any grid that fits
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int cg = t % g8, V = t / g8;
+  const int X = V % mx, Y = (V / mx) % my, Z = V / (mx * my);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int x = 2 * X + (q & 1), y = 2 * Y + ((q >> 1) & 1), z = 2 * Z + (q >> 2);
+    const uint4 u = *reinterpret_cast<const uint4*>(in + (x + (long long)nx * (y + (long long)ny * z)) * c + cg * 8);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h[e]);
+      s[2 * e] += f.x;
+      s[2 * e + 1] += f.y;
     }
-    out[t] = __float2bfloat16(0.125f * s);
   }
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(0.125f * s[2 * e], 0.125f * s[2 * e + 1]);
+  *reinterpret_cast<uint4*>(out + (long long)V * c + cg * 8) = u;
 }
 
 __global__ void pool_bwd_kernel(const bf16* dout, bf16* din, int c, int nx, int ny, int nz) {
@@ -276,21 +337,59 @@ __global__ void pool_bwd_kernel(const bf16* dout, bf16* din, int c, int nx, int 
 
 // ---- 2x2x2 transposed convolution, stride 2 (coarse -> fine) -------------------------------------
 // out[x][y][z][co] = b[co] + sum_ci in[x/2][y/2][z/2][ci] * W[(z%2, y%2, x%2)][co][ci]
-__global__ void tconv_fwd_kernel(const bf16* in, const float* w, const float* b, bf16* out, int cin, int cout, int nx,
-                                 int ny, int nz) {
-  const long long n = (long long)nx * ny * nz * cout;
-  const int mx = nx / 2, my = ny / 2;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int co = (int)(t % cout);
-    const long long v = t / cout;
-    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-    const int k = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
-    const long long V = (x / 2) + (long long)mx * ((y / 2) + (long long)my * (z / 2));
-    const bf16* ip = in + V * cin;
-    const float* wp = w + ((long long)k * cout + co) * cin;
-    float s = b[co];
-    for (int ci = 0; ci < cin; ++ci) s += __bfloat162float(ip[ci]) * wp[ci];
-    out[t] = __float2bfloat16(s);
+template <int CIN, int COUT>
+constexpr int tconv_smem() {
+  return (COUT * CIN * 8 + COUT) * (int)sizeof(float);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) tconv_fwd_kernel(const bf16* in, const float* w, const float* b, bf16* out,
+                                                        int mx, int my, int mz) {
+  // one thread per (coarse voxel V, child k = kx + 2 ky + 4 kz), k fastest; the weights are staged
+  // as [co][ci][k] so that the 8 children in a warp read 8 banks and its 4 voxels share them
+  extern __shared__ float tc_smem[];  // COUT * CIN * 8 weights, then COUT biases (tconv_smem<CIN, COUT>)
+  float* w_s = tc_smem;
+  float* b_s = tc_smem + COUT * CIN * 8;
+  for (int q = threadIdx.x; q < COUT * CIN * 8; q += blockDim.x) {
+    const int k = q & 7, ci = (q >> 3) % CIN, co = (q >> 3) / CIN;
+    w_s[q] = w[(k * COUT + co) * CIN + ci];
+  }
+  for (int q = threadIdx.x; q < COUT; q += blockDim.x) b_s[q] = b[q];
+  __syncthreads();
+  const int nvc = mx * my * mz;  // coarse voxels (below 2^31 / 8 for any grid that fits)
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 8 * nvc) return;
+  const int k = t & 7, V = t >> 3;
+  const int x = V % mx, y = (V / mx) % my, z = V / (mx * my);
+  const int X = 2 * x + (k & 1), Y = 2 * y + ((k >> 1) & 1), Z = 2 * z + (k >> 2);
+  const long long child = X + 2LL * mx * (Y + 2LL * my * Z);
+  float acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = b_s[co];
+  const uint4* ip = reinterpret_cast<const uint4*>(in + (long long)V * CIN);
+#pragma unroll
+  for (int c8 = 0; c8 < CIN / 8; ++c8) {
+    const uint4 u = ip[c8];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h[e]);
+      const int ci = c8 * 8 + 2 * e;
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) {
+        acc[co] = fmaf(f.x, w_s[(co * CIN + ci) * 8 + k], acc[co]);
+        acc[co] = fmaf(f.y, w_s[(co * CIN + ci + 1) * 8 + k], acc[co]);
+      }
+    }
+  }
+  uint4* op = reinterpret_cast<uint4*>(out + child * COUT);
+#pragma unroll
+  for (int c8 = 0; c8 < COUT / 8; ++c8) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(acc[c8 * 8 + 2 * e], acc[c8 * 8 + 2 * e + 1]);
+    op[c8] = u;
   }
 }
 
@@ -338,15 +437,35 @@ __global__ void tconv_bwd_weight_kernel(const bf16* in, const bf16* dout, float*
 }
 
 // ---- 1x1x1 head (16 -> 6 channels, FP32 output) ----------------------------------------------------
-__global__ void head_fwd_kernel(const bf16* in, const float* w, const float* b, float* out, int cin, int cout,
-                                long long nv) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nv * cout; t += (long long)gridDim.x * blockDim.x) {
-    const int o = (int)(t % cout);
-    const long long v = t / cout;
-    float s = b[o];
-    for (int c = 0; c < cin; ++c) s += __bfloat162float(in[v * cin + c]) * w[o * cin + c];
-    out[t] = s;
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) head_fwd_kernel(const bf16* in, const float* w, const float* b, float* out,
+                                                       int nv) {
+  // one thread per voxel: its CIN channels in 16-byte loads, all COUT outputs
+  __shared__ float w_s[COUT * CIN], b_s[COUT];
+  for (int q = threadIdx.x; q < COUT * CIN; q += blockDim.x) w_s[q] = w[q];
+  for (int q = threadIdx.x; q < COUT; q += blockDim.x) b_s[q] = b[q];
+  __syncthreads();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  float acc[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc[o] = b_s[o];
+  const uint4* ip = reinterpret_cast<const uint4*>(in + (long long)v * CIN);
+#pragma unroll
+  for (int c8 = 0; c8 < CIN / 8; ++c8) {
+    const uint4 u = ip[c8];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h[e]);
+#pragma unroll
+      for (int o = 0; o < COUT; ++o)
+        acc[o] = fmaf(f.y, w_s[o * CIN + c8 * 8 + 2 * e + 1], fmaf(f.x, w_s[o * CIN + c8 * 8 + 2 * e], acc[o]));
+    }
   }
+  float* op = out + (long long)v * COUT;
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) op[o] = acc[o];
 }
 
 // din[v][c] = sum_o dout[v][o] W[o][c];  dW[o][c] += sum_v dout[v][o] in[v][c];  db[o] += sum_v dout[v][o]
