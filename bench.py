@@ -174,7 +174,7 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_solves(fit, torch, case, kinds, max_iter):
+def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
     """Seconds per frequency to a 1e-8 true residual: FGMRES(30) with the Jacobi (Eq. Precond diagonal)
     right preconditioner, complex64 inner + FP64 refinement ("mixed") or complex128 throughout ("c128").
     Inputs are resident on the device; the timed region is the fit_solve call."""
@@ -190,7 +190,7 @@ def time_solves(fit, torch, case, kinds, max_iter):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, rep = g.solve([w], b, x, 1e-8, precision=prec, method=fit.FIT_FGMRES, restart=30,
-                              precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter)
+                              precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter, use_graph=use_graph)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             out[kind] = {"s_per_freq": dt, "iterations": rep[0]["iterations"], "outer": rep[0]["outer"],
@@ -244,6 +244,8 @@ def main():
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
     ap.add_argument("--solve", default="mixed", help="comma list of solves to time: mixed, c128, none")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
+    ap.add_argument("--graph", type=int, default=1, help="1: the solve runs as one CUDA graph; 0: host-driven loop "
+                    "(for per-kernel profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -274,7 +276,7 @@ def main():
             print(json.dumps(time_unet(fit, torch, case, args.steps, args.warmup)), flush=True)
         return
     if args.mode == "solve":
-        res = time_solves(fit, torch, case, kinds, args.max_iter)
+        res = time_solves(fit, torch, case, kinds, args.max_iter, args.graph)
         if rank == 0:
             print(json.dumps({"metric": "solve s/freq to 1e-8", "unit": "s", "workload": args.workload,
                               "solves": res}), flush=True)

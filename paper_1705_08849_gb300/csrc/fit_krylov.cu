@@ -56,7 +56,7 @@ struct Sys {
   int hist;            // history snapshots written
   int hist_pad;
   int rin_min_it;      // iteration at which it was reached
-  int pad_;
+  int reject;          // 1: the last correction raised the true residual and is undone
 };
 
 struct Ctl {
@@ -141,6 +141,7 @@ struct OpOuterInit {  // q2 = ||b||^2
     s.outer = 0;
     s.iters = 0;
     s.stagn = 0;
+    s.reject = 0;
     s.inner_status = SYS_CONV;
     s.inner_it = 0;
     if (!isfinite(q[2])) s.outer_status = SYS_NAN;
@@ -153,11 +154,24 @@ struct OpOuter {  // after r = b - A x: q2 = ||r||^2
   __device__ bool active(const Sys& s) const { return s.outer_status == SYS_RUN; }
   __device__ void apply(Sys& s, const double* q, const P& p, int) const {
     double r2 = q[2];
-    s.rnorm2 = r2;
-    s.rscale = sqrt(r2);
     s.outer += 1;
     s.iters += s.inner_it;
-    if (!isfinite(r2)) { s.outer_status = SYS_NAN; return; }
+    // A correction that raised the true residual (or made it non-finite) is undone by k_revert,
+    // which restores x and r; the loop stops there, since the deterministic inner solve would
+    // return the same correction from the same residual.
+    if (!isfinite(r2)) {
+      s.reject = 1;
+      s.outer_status = SYS_NAN;
+      return;
+    }
+    if (r2 > s.rnorm2) {
+      s.reject = 1;
+      s.outer_status = SYS_MAXIT;
+      return;
+    }
+    s.reject = 0;
+    s.rnorm2 = r2;
+    s.rscale = sqrt(r2);
     if (r2 <= s.tol2) { s.outer_status = SYS_CONV; return; }
     if (r2 < 0.99 * s.best2) { s.best2 = r2; s.stagn = 0; }
     else s.stagn += 1;
@@ -465,6 +479,40 @@ __global__ void __launch_bounds__(256) k_update_x(double2* x, const typename cpl
   }
 }
 
+// r_prev = r before a correction is tried
+__global__ void __launch_bounds__(256) k_copy_r(const double2* __restrict__ r, double2* __restrict__ rprev,
+                                                const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.y;
+  if (sys[b].outer_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  VEC_LOOP(p) rprev[off + e] = r[off + e];
+}
+
+// undo a rejected correction: x -= corr d, r = r_prev
+template <typename T>
+__global__ void __launch_bounds__(256) k_revert(double2* x, const typename cplx<T>::t* __restrict__ d, double2* r,
+                                                const double2* __restrict__ rprev, const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.y;
+  if (!sys[b].reject) return;
+  const long long off = (long long)b * p.ne;
+  const double c = sys[b].corr;
+  VEC_LOOP(p) {
+    auto dd = d[off + e];
+    double2 xx = x[off + e];
+    xx.x -= c * (double)dd.x;
+    xx.y -= c * (double)dd.y;
+    x[off + e] = xx;
+    r[off + e] = rprev[off + e];
+  }
+}
+
+// the revert of this refinement step is done: no later step may repeat it (the loop keeps running
+// while any system of the batch is active)
+__global__ void k_clear_reject(Sys* sys, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) sys[b].reject = 0;
+}
+
 // ---- FGMRES(m) vector kernels ---------------------------------------------------------------
 // Arnoldi step j works on the basis V[0..j] (vector i of system b at V + (i*B + b)*ne) and the
 // new vector w = V[j+1].  Partial slot layout: 2*(j+1) doubles (re, im of <V_i, w>) per block.
@@ -483,107 +531,176 @@ __device__ inline void warp_accum(T re, T im, double* slot_re, double* slot_im) 
 
 #define FG_MAXV 65  // m + 1 <= 65
 
-// mode 0: h_i = <V_i, w>                      (partials of 2(j+1) values)
-// mode 1: w -= sum_i h_i V_i, then h2_i = <V_i, w>
-// mode 2: w -= sum_i h2_i V_i, then q0 = ||w||^2
-// MAXV >= j+1 basis vectors are handled with fully unrolled, predicated loops: every V_i load of
-// an element is issued before it is used (one trip's loads all in flight) and the per-vector dot
-// accumulators stay in registers until a single warp reduction at the end.
-template <typename T, int MODE, int MAXV>
-__global__ void __launch_bounds__(256) k_fg_ortho(const typename cplx<T>::t* __restrict__ Vb, int j,
-                                                  const double* __restrict__ hcoef, const Sys* __restrict__ sys,
-                                                  double* part, P p) {
-  using V = typename cplx<T>::t;
-  const int b = blockIdx.y;
-  if (sys[b].inner_status != SYS_RUN) return;
-  __shared__ double red[8][2 * MAXV];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nv = j + 1;
-  const long long vs = (long long)p.B * p.ne;  // stride between basis vectors
-  const long long off = (long long)b * p.ne;
-  V* w = (V*)(Vb + (long long)(j + 1) * vs + off);
-  __shared__ T hs[2 * MAXV];  // projection coefficients, read as broadcasts
-  if (MODE >= 1) {
-    const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
-    for (int q = threadIdx.x; q < 2 * MAXV; q += 256) hs[q] = q < 2 * nv ? (T)hc[q] : T(0);
-    __syncthreads();
-  }
-  T ar[MAXV], ai[MAXV];
+// The three CGS2 passes.  They work on chunks of CH elements (one per thread, CH = 256 for complex64
+// and 128 for complex128) and keep only a few values per thread in registers:
+//   k_fg_dots:         h_i = <V_i, w>                   (2(j+1) partials per block)
+//   k_fg_update_dots:  w -= sum_i h_i V_i, then h2_i = <V_i, w>
+//   k_fg_update_norm:  w -= sum_i h2_i V_i, then ||w||^2 (partial slot 0)
+// The dots are a tall-skinny product: the chunk of w sits in shared memory and each warp streams
+// whole basis vectors (i = warp, warp + nwarps, ...) over it, summing in the vector precision within
+// the chunk and in FP64 across chunks, in a fixed order.  k_fg_update_dots keeps the chunk of every
+// V_i it reads for the update in shared memory, so V is read from HBM once for both halves.
+template <typename T>
+struct FgChunk {
+  static constexpr int CH = sizeof(T) == 4 ? 256 : 128;
+};
+
+template <typename T>
+__device__ inline void fg_chunk_dots(const typename cplx<T>::t* vchunk, long long vstride, bool vglobal,
+                                     const typename cplx<T>::t* ws, int nv, int nvalid, double* acc) {
+  constexpr int CH = FgChunk<T>::CH;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = CH / 32;
+  for (int i = warp; i < nv; i += nw) {
+    const auto* vi = vchunk + (vglobal ? (long long)i * vstride : (long long)i * CH);
+    T sr = T(0), si = T(0);
 #pragma unroll
-  for (int i = 0; i < MAXV; ++i) {
-    ar[i] = T(0);
-    ai[i] = T(0);
-  }
-  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < p.ne; e += (long long)gridDim.x * 256) {
-    V vi[MAXV];
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i) vi[i] = i < nv ? Vb[(long long)i * vs + off + e] : czero<V>();
-    V wv = w[e];
-    if (MODE >= 1) {
-#pragma unroll
-      for (int i = 0; i < MAXV; ++i) {
-        const T hr = hs[2 * i], hi = hs[2 * i + 1];
-        wv.x -= hr * vi[i].x - hi * vi[i].y;
-        wv.y -= hr * vi[i].y + hi * vi[i].x;
-      }
-      w[e] = wv;
-    }
-    if (MODE <= 1) {
-#pragma unroll
-      for (int i = 0; i < MAXV; ++i) {
-        ar[i] += vi[i].x * wv.x + vi[i].y * wv.y;
-        ai[i] += vi[i].x * wv.y - vi[i].y * wv.x;
-      }
-    } else {
-      ar[0] += wv.x * wv.x + wv.y * wv.y;
-    }
-  }
-  const int nq = MODE <= 1 ? nv : 1;
-#pragma unroll
-  for (int i = 0; i < MAXV; ++i) {
-    if (i < nq) {
-      T x = ar[i], y = ai[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_xor_sync(0xffffffffu, x, o);
-        y += __shfl_xor_sync(0xffffffffu, y, o);
-      }
-      if (lane == 0) {
-        red[warp][2 * i] = (double)x;
-        red[warp][2 * i + 1] = (double)y;
+    for (int q0 = 0; q0 < CH; q0 += 32) {
+      const int q = q0 + lane;
+      if (q < nvalid) {
+        const auto a = vi[q], b = ws[q];
+        sr += a.x * b.x + a.y * b.y;
+        si += a.x * b.y - a.y * b.x;
       }
     }
-  }
-  __syncthreads();
-  double* out = part + PSLOT(p, b);
-  for (int q = threadIdx.x; q < 2 * nq; q += 256) {
-    double s = 0.0;
-    for (int w8 = 0; w8 < 8; ++w8) s += red[w8][q];
-    out[q] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      acc[2 * i] += (double)sr;
+      acc[2 * i + 1] += (double)si;
+    }
   }
 }
 
-// fixed-order sum of the 2(j+1) partials of each block into hout[b][0..2(j+1)-1]
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_dots(const typename cplx<T>::t* __restrict__ Vb, int j,
+                                                 const Sys* __restrict__ sys, double* part, P p) {
+  using V = typename cplx<T>::t;
+  constexpr int CH = FgChunk<T>::CH;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  __shared__ V ws[CH];
+  __shared__ double acc[2 * FG_MAXV];
+  const int nv = j + 1, tid = threadIdx.x;
+  const long long vs = (long long)p.B * p.ne, off = (long long)b * p.ne;
+  const V* w = Vb + (long long)(j + 1) * vs + off;
+  for (int q = tid; q < 2 * nv; q += CH) acc[q] = 0.0;
+  for (long long c0 = (long long)blockIdx.x * CH; c0 < p.ne; c0 += (long long)gridDim.x * CH) {
+    const int nvalid = (int)min((long long)CH, p.ne - c0);
+    __syncthreads();  // the previous chunk's dots are done with ws
+    ws[tid] = tid < nvalid ? w[c0 + tid] : czero<V>();
+    __syncthreads();
+    fg_chunk_dots<T>(Vb + off + c0, vs, true, ws, nv, nvalid, acc);
+  }
+  __syncthreads();
+  double* out = part + PSLOT(p, b);
+  for (int q = tid; q < 2 * nv; q += CH) out[q] = acc[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_update_dots(const typename cplx<T>::t* __restrict__ Vb, int j,
+                                                        const double* __restrict__ hcoef,
+                                                        const Sys* __restrict__ sys, double* part, P p) {
+  using V = typename cplx<T>::t;
+  constexpr int CH = FgChunk<T>::CH;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  extern __shared__ __align__(16) unsigned char fg_smem[];
+  V* vsm = (V*)fg_smem;                 // [nv][CH]
+  const int nv = j + 1, tid = threadIdx.x;
+  V* ws = vsm + (long long)nv * CH;     // [CH]
+  double* acc = (double*)(ws + CH);     // [2 nv]
+  T* hs = (T*)(acc + 2 * nv);           // [2 nv]
+  const long long vs = (long long)p.B * p.ne, off = (long long)b * p.ne;
+  V* w = (V*)(Vb + (long long)(j + 1) * vs + off);
+  const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
+  for (int q = tid; q < 2 * nv; q += CH) {
+    acc[q] = 0.0;
+    hs[q] = (T)hc[q];
+  }
+  for (long long c0 = (long long)blockIdx.x * CH; c0 < p.ne; c0 += (long long)gridDim.x * CH) {
+    const int nvalid = (int)min((long long)CH, p.ne - c0);
+    const bool valid = tid < nvalid;
+    __syncthreads();  // hs is set; the previous chunk's dots are done with vsm and ws
+    V wv = valid ? w[c0 + tid] : czero<V>();
+    const V* vcol = Vb + off + c0 + tid;
+#pragma unroll 8
+    for (int i = 0; i < nv; ++i) {
+      const V a = valid ? vcol[(long long)i * vs] : czero<V>();
+      vsm[i * CH + tid] = a;
+      const T hr = hs[2 * i], hi = hs[2 * i + 1];
+      wv.x -= hr * a.x - hi * a.y;
+      wv.y -= hr * a.y + hi * a.x;
+    }
+    if (valid) w[c0 + tid] = wv;
+    ws[tid] = wv;
+    __syncthreads();
+    fg_chunk_dots<T>(vsm, 0, false, ws, nv, nvalid, acc);
+  }
+  __syncthreads();
+  double* out = part + PSLOT(p, b);
+  for (int q = tid; q < 2 * nv; q += CH) out[q] = acc[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fg_update_norm(const typename cplx<T>::t* __restrict__ Vb, int j,
+                                                        const double* __restrict__ hcoef,
+                                                        const Sys* __restrict__ sys, double* part, P p) {
+  using V = typename cplx<T>::t;
+  constexpr int CH = FgChunk<T>::CH;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  __shared__ T hs[2 * FG_MAXV];
+  const int nv = j + 1, tid = threadIdx.x;
+  const long long vs = (long long)p.B * p.ne, off = (long long)b * p.ne;
+  V* w = (V*)(Vb + (long long)(j + 1) * vs + off);
+  const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
+  for (int q = tid; q < 2 * nv; q += CH) hs[q] = (T)hc[q];
+  __syncthreads();
+  T nrm[1] = {T(0)};
+  for (long long e = (long long)blockIdx.x * CH + tid; e < p.ne; e += (long long)gridDim.x * CH) {
+    V wv = w[e];
+    const V* vcol = Vb + off + e;
+#pragma unroll 8
+    for (int i = 0; i < nv; ++i) {
+      const V a = vcol[(long long)i * vs];
+      const T hr = hs[2 * i], hi = hs[2 * i + 1];
+      wv.x -= hr * a.x - hi * a.y;
+      wv.y -= hr * a.y + hi * a.x;
+    }
+    w[e] = wv;
+    nrm[0] += wv.x * wv.x + wv.y * wv.y;
+  }
+  fit_block_sum<T, 1>(nrm, part + PSLOT(p, b));
+}
+
+// hout[b][q] = sum over the blocks k of part[b][k][q], q < nq: one warp per q, its lanes summing
+// blocks k = lane, lane + 32, ... and then a fixed shuffle tree (the same order on every run)
 __global__ void __launch_bounds__(256) k_fg_fin_dots(const double* __restrict__ part, int nq, double* hout,
                                                      const Sys* __restrict__ sys, P p) {
   const int b = blockIdx.x;
   if (sys[b].inner_status != SYS_RUN) return;
-  for (int q = threadIdx.x; q < nq; q += 256) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* pb = part + (long long)b * p.nblk * p.pstride;
+  for (int q = warp; q < nq; q += 8) {
     double s = 0.0;
-    for (int k = 0; k < p.nblk; ++k) s += part[((long long)b * p.nblk + k) * p.pstride + q];
-    hout[(long long)b * 2 * FG_MAXV + q] = s;
+    for (int k = lane; k < p.nblk; k += 32) s += pb[(long long)k * p.pstride + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) hout[(long long)b * 2 * FG_MAXV + q] = s;
   }
 }
 
 // Hessenberg column j = h + h2, h_{j+1,j} = ||w||; Givens rotations; residual estimate |g_{j+1}|
-__global__ void k_fg_givens(const double* __restrict__ part, int j, const double* __restrict__ h1,
+__global__ void k_fg_givens(const double* __restrict__ hn2, int j, const double* __restrict__ h1,
                             const double* __restrict__ h2, double* H, double* G, double* CS, double* SN, Sys* sys, P p) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= p.B) return;
   Sys& s = sys[b];
   if (s.inner_status != SYS_RUN) return;
-  double nrm2 = 0.0;
-  for (int k = 0; k < p.nblk; ++k) nrm2 += part[((long long)b * p.nblk + k) * p.pstride];
+  const double nrm2 = hn2[(long long)b * 2 * FG_MAXV];  // ||w||^2, reduced by k_fg_fin_dots
   const int m = p.m;
   double2* Hc = (double2*)(H + (long long)b * 2 * (m + 1) * m) + (long long)j * (m + 1);  // column j
   double2* g = (double2*)(G + (long long)b * 2 * (m + 1));
@@ -757,6 +874,7 @@ struct Work {
   P p{};
   // device buffers
   double2* r128 = nullptr;
+  double2* rprev = nullptr;  // r before the current correction (true-residual acceptance test)
   double* omega = nullptr;
   void *rin = nullptr, *rhat = nullptr, *pv = nullptr, *v = nullptr, *t = nullptr, *d = nullptr;
   void* Vb = nullptr;     // FGMRES basis (m+1 vectors)
@@ -767,7 +885,7 @@ struct Work {
   void* x16 = nullptr;   // U-Net input scratch ([ncell][16] bf16)
   double *part_apply = nullptr, *part_vec = nullptr;
   long long napply = 0;
-  double *h1 = nullptr, *h2 = nullptr, *H = nullptr, *G = nullptr, *CS = nullptr, *SN = nullptr, *Y = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *hn2 = nullptr, *H = nullptr, *G = nullptr, *CS = nullptr, *SN = nullptr, *Y = nullptr;
   Sys* sys = nullptr;
   Ctl* ctl = nullptr;
   std::vector<std::pair<void*, size_t>> allocs;
@@ -785,14 +903,14 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   size_t ne = (size_t)g->ne;
   size_t esz = mixed ? 8 : 16;
   size_t vec = ne * B * esz;
-  size_t bytes = ne * B * 16;  // r128
+  size_t bytes = ne * B * 32;  // r128 and r_prev
   if (method == FIT_BICGSTAB) bytes += 6 * vec + (pc != FIT_PC_NONE ? 2 * vec : 0);
   else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
   if (pc == FIT_PC_JACOBI || pc == FIT_PC_UNET) bytes += ne * esz / 2 + vec;
   size_t napply = (size_t)std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
   bytes += (size_t)B * napply * 4 * 8;
   bytes += (size_t)B * 1216 * 2 * FG_MAXV * 8;
-  bytes += (size_t)B * (2 * 2 * FG_MAXV + 2 * (m + 1) * m * 2 + 2 * (m + 1) * 2 + 2 * 2 * m + 2 * FG_MAXV) * 8;
+  bytes += (size_t)B * (3 * 2 * FG_MAXV + 2 * (m + 1) * m * 2 + 2 * (m + 1) * 2 + 2 * 2 * m + 2 * FG_MAXV) * 8;
   return bytes + (size_t)B * sizeof(Sys) + 4096;
 }
 
@@ -807,6 +925,7 @@ fit_status setup(Work& w, int B) {
 #define ALLOC(ptr, bytes) \
   if ((st = w.alloc((void**)&(ptr), (bytes))) != FIT_OK) return st
   ALLOC(w.r128, ne * B * sizeof(double2));
+  ALLOC(w.rprev, ne * B * sizeof(double2));
   ALLOC(w.omega, B * sizeof(double));
   if (w.method == FIT_BICGSTAB) {
     ALLOC(w.rin, vec);
@@ -847,6 +966,7 @@ fit_status setup(Work& w, int B) {
   if (w.method == FIT_FGMRES) {
     ALLOC(w.h1, (size_t)B * 2 * FG_MAXV * sizeof(double));
     ALLOC(w.h2, (size_t)B * 2 * FG_MAXV * sizeof(double));
+    ALLOC(w.hn2, (size_t)B * 2 * FG_MAXV * sizeof(double));
     ALLOC(w.H, (size_t)B * 2 * (w.m + 1) * w.m * sizeof(double));
     ALLOC(w.G, (size_t)B * 2 * (w.m + 1) * sizeof(double));
     ALLOC(w.CS, (size_t)B * 2 * w.m * sizeof(double));
@@ -972,15 +1092,23 @@ struct Seq {
     fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpRho{});
   }
 
-  // CGS2 pass over V[0..j]; the unrolled width is the smallest of 8/16/32/64 that holds j+1
+  // the three CGS2 passes over V[0..j] (mode 0: dots; 1: update with h, dots; 2: update with h2, norm)
   template <typename T, int MODE>
   void ortho(int j, const double* h) {
     using V = typename cplx<T>::t;
+    constexpr int CH = FgChunk<T>::CH;
     const int nv = j + 1;
-    if (nv <= 8) k_fg_ortho<T, MODE, 8><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
-    else if (nv <= 16) k_fg_ortho<T, MODE, 16><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
-    else if (nv <= 32) k_fg_ortho<T, MODE, 32><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
-    else k_fg_ortho<T, MODE, 64><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    if (MODE == 0) {
+      k_fg_dots<T><<<vgrid(), CH, 0, s>>>((const V*)w.Vb, j, w.sys, w.part_vec, w.p);
+    } else if (MODE == 1) {
+      const size_t smem = (size_t)(nv + 1) * CH * sizeof(V) + (size_t)2 * nv * sizeof(double) +
+                          (size_t)2 * nv * sizeof(T);
+      auto kern = k_fg_update_dots<T>;
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<vgrid(), CH, smem, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    } else {
+      k_fg_update_norm<T><<<vgrid(), CH, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+    }
     check();
   }
 
@@ -1023,7 +1151,8 @@ struct Seq {
     k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h2, w.sys, w.p);
     check();
     ortho<T, 2>(j, w.h2);
-    k_fg_givens<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.part_vec, j, w.h1, w.h2, w.H, w.G, w.CS, w.SN, w.sys, w.p);
+    k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 1, w.hn2, w.sys, w.p);
+    k_fg_givens<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.hn2, j, w.h1, w.h2, w.H, w.G, w.CS, w.SN, w.sys, w.p);
     check();
     k_fg_scale<T><<<vgrid(), 256, 0, s>>>((V*)w.Vb, j, w.sys, w.p);
     check();
@@ -1046,10 +1175,14 @@ struct Seq {
   template <typename T>
   void outer_tail(const int* st_outer) {
     using V = typename cplx<T>::t;
+    k_copy_r<<<vgrid(), 256, 0, s>>>(w.r128, w.rprev, w.sys, w.p);
     k_update_x<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.sys, w.p);
     check();
     long long n3 = apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
     fin<3>(w.part_apply, n3, 4, OpOuter{});
+    k_revert<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.r128, w.rprev, w.sys, w.p);
+    k_clear_reject<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.sys, w.p.B);
+    check();
     if (hist) {
       k_history<<<vgrid(), 256, 0, s>>>(x, hist, w.sys, hist_every, hist_len, w.p);
       k_history_count<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.sys, hist_every, hist_len, w.p);
