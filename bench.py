@@ -175,8 +175,9 @@ def run_reference(args, rank):
 
 
 def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
-    """Seconds per frequency to a 1e-8 true residual: FGMRES(30) with the Jacobi (Eq. Precond diagonal)
-    right preconditioner, complex64 inner + FP64 refinement ("mixed") or complex128 throughout ("c128").
+    """Seconds per frequency to a 1e-8 true residual with the Jacobi (Eq. Precond diagonal)
+    preconditioner.  Each kind is "[method-]precision": method fgmres (FGMRES(30), the default), cocg
+    or bicgstab; precision "mixed" (complex64 inner solve inside FP64 refinement) or "c128".
     Inputs are resident on the device; the timed region is the fit_solve call."""
     import fitgen as G
     w = 2 * np.pi * float(case["freqs"][0])
@@ -185,17 +186,21 @@ def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
     with fit.Grid.from_case(case) as g:
         b = (-1j * w) * j  # b = -j w j (masked source edges carry no current in these workloads)
         for kind in kinds:
+            mname, _, pname = kind.rpartition("-")
+            mname = mname or "fgmres"
+            method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname]
+            label = {"fgmres": "FGMRES(30)+Jacobi", "cocg": "COCG+Jacobi", "bicgstab": "BiCGStab+Jacobi"}[mname]
             x = torch.zeros_like(b)
-            prec = fit.FIT_SOLVE_MIXED if kind == "mixed" else fit.FIT_SOLVE_C128
+            prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st, rep = g.solve([w], b, x, 1e-8, precision=prec, method=fit.FIT_FGMRES, restart=30,
+            st, rep = g.solve([w], b, x, 1e-8, precision=prec, method=method, restart=30,
                               precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter, use_graph=use_graph)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             out[kind] = {"s_per_freq": dt, "iterations": rep[0]["iterations"], "outer": rep[0]["outer"],
                          "relres": rep[0]["relres"], "status": fit.status_str(rep[0]["status"]),
-                         "method": "FGMRES(30)+Jacobi", "tol": 1e-8}
+                         "method": label, "tol": 1e-8}
     return out
 
 
@@ -242,7 +247,9 @@ def main():
     ap.add_argument("--batch", type=int, default=1, help="systems (frequencies) per apply in the apply mode")
     ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet"],
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
-    ap.add_argument("--solve", default="mixed", help="comma list of solves to time: mixed, c128, none")
+    ap.add_argument("--solve", default="mixed,cocg-mixed",
+                    help="comma list of solves to time, each [method-]precision with method fgmres (default), "
+                         "cocg or bicgstab and precision mixed or c128; none for no solve")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
     ap.add_argument("--graph", type=int, default=1, help="1: the solve runs as one CUDA graph; 0: host-driven loop "
                     "(for per-kernel profiling)")
@@ -270,7 +277,8 @@ def main():
     fit.lib()
 
     case = _workload(args.workload)
-    kinds = [k for k in args.solve.split(",") if k in ("mixed", "c128")]
+    kinds = [k for k in args.solve.split(",") if k.rpartition("-")[2] in ("mixed", "c128")
+             and k.rpartition("-")[0] in ("", "fgmres", "cocg", "bicgstab")]
     if args.mode == "unet":
         if rank == 0:
             print(json.dumps(time_unet(fit, torch, case, args.steps, args.warmup)), flush=True)

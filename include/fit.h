@@ -112,12 +112,19 @@ fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x
 fit_status fit_apply_noalloc(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
                              fit_prec prec, void* stream);
 
-typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1 } fit_method;
+/* Krylov methods (Sec. IV lists the PETSc solvers tried; bcgs and the gmres family are kept, and
+ * "cg" on this complex symmetric system (A^T = A, Eq. e2) is read as CG with the unconjugated
+ * bilinear form, i.e. COCG):
+ *   FIT_BICGSTAB  BiCGStab, r^ = r0, conjugated inner products
+ *   FIT_FGMRES    restarted flexible GMRES(restart), CGS2 orthogonalisation, Givens least squares
+ *   FIT_COCG      conjugate orthogonal CG: one apply and three fused vector passes per iteration,
+ *                 no stored basis; preconditioner none or Jacobi (diagonal, so A stays symmetric) */
+typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1, FIT_COCG = 2 } fit_method;
 typedef enum { FIT_SOLVE_C128 = 0, FIT_SOLVE_MIXED = 1 } fit_solve_precision;
 typedef enum { FIT_PC_NONE = 0, FIT_PC_JACOBI = 1, FIT_PC_UNET = 2 } fit_pc_kind;
 
 typedef struct fit_solve_opts {
-  int method;        /* fit_method: BiCGStab or FGMRES(restart) (Sec. IV, Fig. Iterative) */
+  int method;        /* fit_method: BiCGStab, FGMRES(restart) or COCG (Sec. IV, Fig. Iterative) */
   int restart;       /* FGMRES restart length m (1..64); default 30 */
   int precision;     /* fit_solve_precision: plain complex128 Krylov, or complex64 inner Krylov
                         inside FP64 iterative refinement (true residual b - A x in FP64) */
@@ -127,7 +134,8 @@ typedef struct fit_solve_opts {
   double inner_tol;  /* relative tolerance of each inner complex64 solve; default 1e-4 */
   int batch;         /* systems solved together in one batched launch; 0 = all nfreq */
   int use_graph;     /* nonzero: run the Krylov loop as one CUDA graph with a device-side loop */
-  int precond;       /* fit_pc_kind applied as the right preconditioner (BiCGStab: Jacobi only) */
+  int precond;       /* fit_pc_kind applied as the right preconditioner (BiCGStab and COCG: none or
+                        Jacobi; the learned one needs FGMRES with FIT_SOLVE_MIXED) */
   void* stream;      /* cudaStream_t (as void*) for all work; NULL = legacy default stream */
   void* history;     /* optional DEVICE buffer of history_len * nfreq * n_e double2: the iterate x
                         after every history_every-th outer step, slot h of system f at

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE (see ``oracle/__init__.py``).  complex128 throughout.  The Krylov methods
 follow the short-listed solvers of Sec. IV (bcgs and the gmres family, Fig. Iterative) as
-textbook algorithms: BiCGStab (van der Vorst 1992) and restarted (F)GMRES (Saad 1993) with
-modified Gram-Schmidt and Givens rotations.  Conventions (readings): conjugated inner products
+textbook algorithms: BiCGStab (van der Vorst 1992), restarted (F)GMRES (Saad 1993) with
+modified Gram-Schmidt and Givens rotations, and COCG (the paper's "cg" on a complex symmetric A).  Conventions (readings): conjugated inner products
 <u, v> = u^H v, x0 = 0, shadow residual r^ = r0, stop on the true relative residual
 ||b - A x|| / ||b|| (Sec. IV fixes only "a relative decrease of the residual norm").
 """
@@ -26,6 +26,44 @@ def sparse_solve(A, b):
 def relres(A, x, b):
     """||b - A x||_2 / ||b||_2 in complex128."""
     return float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
+
+
+def cocg(A, b, tol=1e-10, maxiter=10000, dinv=None):
+    """Conjugate orthogonal CG (van der Vorst and Melissen 1990) for complex symmetric A = A^T: the
+    CG recurrences with the unconjugated bilinear form (u, v) = u^T v, the reading of the "cg"
+    solver of Sec. IV on the complex symmetric system of Eq. e2.  ``dinv`` (optional) is the
+    diagonal of a symmetric preconditioner M = diag(dinv).  Per step:
+        q = A p,  alpha = rho / (p, q),  x += alpha p,  r -= alpha q,
+        z = M r,  rho' = (r, z),  beta = rho' / rho,  p = z + beta p.
+    Returns (x, iterations, true relative residual, status), status 0 = converged, 1 = iteration
+    cap, 2 = breakdown (|(p, q)| or |rho| < 1e-300)."""
+    b = np.asarray(b, dtype=np.complex128)
+    nb = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if nb == 0:
+        return x, 0, 0.0, 0
+    m = (lambda v: v) if dinv is None else (lambda v: dinv * v)
+    r = b.copy()
+    z = m(r)
+    p = z.copy()
+    rho = r @ z  # unconjugated
+    for it in range(1, maxiter + 1):
+        q = A @ p
+        pq = p @ q
+        if abs(pq) < 1e-300 or abs(rho) < 1e-300:
+            return x, it, relres(A, x, b), 2
+        alpha = rho / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        if np.linalg.norm(r) <= tol * nb:
+            rr = relres(A, x, b)
+            if rr <= tol:
+                return x, it, rr, 0
+        z = m(r)
+        rho_new = r @ z
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+    return x, maxiter, relres(A, x, b), 1
 
 
 def bicgstab(A, b, tol=1e-10, maxiter=10000):

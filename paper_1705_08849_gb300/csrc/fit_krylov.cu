@@ -56,7 +56,8 @@ struct Sys {
   int hist;            // history snapshots written
   int hist_pad;
   int rin_min_it;      // iteration at which it was reached
-  int reject;          // 1: the last correction raised the true residual and is undone
+  int mr;              // 1: the step length amr of this refinement step is still to be applied
+  double2 amr;         // minimal-residual step length along this step's correction
 };
 
 struct Ctl {
@@ -141,7 +142,7 @@ struct OpOuterInit {  // q2 = ||b||^2
     s.outer = 0;
     s.iters = 0;
     s.stagn = 0;
-    s.reject = 0;
+    s.mr = 0;
     s.inner_status = SYS_CONV;
     s.inner_it = 0;
     if (!isfinite(q[2])) s.outer_status = SYS_NAN;
@@ -150,26 +151,32 @@ struct OpOuterInit {  // q2 = ||b||^2
   }
 };
 
-struct OpOuter {  // after r = b - A x: q2 = ||r||^2
+// After the correction c d: with r0 = b - A x (before) and r1 = b - A (x + c d) (after, both
+// computed in FP64), u = r0 - r1 = A c d.  The step length along the correction that minimises
+// the true residual, amr = <u, r0> / <u, u>, gives x + amr c d with residual (1 - amr) r0 + amr r1
+// (linear in the step, so again b - A x exactly up to rounding), whose norm never exceeds that of
+// r0 or r1: a correction that would raise the residual is shortened instead, down to none.
+// q0 = ||r0||^2, q1, q2 = Re, Im <r1, r0>, q3 = ||r1||^2.
+struct OpOuter {
   __device__ bool active(const Sys& s) const { return s.outer_status == SYS_RUN; }
   __device__ void apply(Sys& s, const double* q, const P& p, int) const {
-    double r2 = q[2];
+    const double a = q[0], c = q[3];
+    const double2 bb = make_double2(q[1], q[2]);
     s.outer += 1;
     s.iters += s.inner_it;
-    // A correction that raised the true residual (or made it non-finite) is undone by k_revert,
-    // which restores x and r; the loop stops there, since the deterministic inner solve would
-    // return the same correction from the same residual.
-    if (!isfinite(r2)) {
-      s.reject = 1;
-      s.outer_status = SYS_NAN;
-      return;
+    s.mr = 1;
+    double2 al = make_double2(0.0, 0.0);
+    double r2 = a;
+    const double den = a - 2.0 * bb.x + c;  // ||u||^2
+    if (isfinite(c) && cfinite(bb) && den > 0.0) {
+      al = make_double2((a - bb.x) / den, -bb.y / den);  // <u, r0> / ||u||^2
+      // ||(1 - amr) r0 + amr r1||^2 = a - |a - bb|^2 / den = c - |c - bb|^2 / den; evaluated from the
+      // smaller of a and c, so that its rounding error is relative to the smaller residual
+      const double base = fmin(a, c);
+      r2 = fmax(0.0, base - ((base - bb.x) * (base - bb.x) + bb.y * bb.y) / den);
     }
-    if (r2 > s.rnorm2) {
-      s.reject = 1;
-      s.outer_status = SYS_MAXIT;
-      return;
-    }
-    s.reject = 0;
+    s.amr = al;
+    if (!isfinite(a)) { s.outer_status = SYS_NAN; return; }
     s.rnorm2 = r2;
     s.rscale = sqrt(r2);
     if (r2 <= s.tol2) { s.outer_status = SYS_CONV; return; }
@@ -201,6 +208,54 @@ struct OpInnerStart {
     double it = p.mixed ? fmax(p.inner_tol, need) : fmax(need, 1e-15);
     s.inner_tol2 = it * it * q[0];
     s.max_inner = max(1, p.max_iter - s.iters);
+  }
+};
+
+// ---- COCG operations ---------------------------------------------------------------------------
+// Conjugate orthogonal CG for the complex symmetric A (A^T = A): CG with the unconjugated bilinear
+// form (u, v) = sum_i u_i v_i in place of the inner product, right/left-symmetric Jacobi
+// preconditioner z = D^-1 r.  Per iteration: q = A p, alpha = rho / (p, q), d += alpha p,
+// r -= alpha q, rho' = (r, D^-1 r), beta = rho' / rho, p = D^-1 r + beta p.
+struct OpCocgStart {  // q0,q1 = (r~, D^-1 r~), q2 = ||r~||^2
+  __device__ bool active(const Sys&) const { return true; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int b) const {
+    const double qq[3] = {q[2], 0.0, 0.0};
+    OpInnerStart{}.apply(s, qq, p, b);
+    s.rho = make_double2(q[0], q[1]);
+    if (s.inner_status == SYS_RUN && !cfinite(s.rho)) s.inner_status = SYS_NAN;
+  }
+};
+
+struct OpCocgAlpha {  // q0,q1 = (p, A p)
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    double2 sig = make_double2(q[0], q[1]);
+    if (!cfinite(sig)) { s.inner_status = SYS_NAN; return; }
+    if (sqrt(cabs2(sig)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
+    s.alpha = cdiv(s.rho, sig);
+  }
+};
+
+struct OpCocgRho {  // q0,q1 = (r, D^-1 r), q2 = ||r||^2
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    double2 rn = make_double2(q[0], q[1]);
+    double rr = q[2];
+    s.inner_it += 1;
+    s.rin2 = rr;
+    if (!cfinite(rn) || !isfinite(rr)) { s.inner_status = SYS_NAN; return; }
+    if (rr <= s.inner_tol2) { s.inner_status = SYS_CONV; return; }
+    if (s.inner_it >= s.max_inner) { s.inner_status = SYS_MAXIT; return; }
+    if (rr < s.rin_min2) { s.rin_min2 = rr; s.rin_min_it = s.inner_it; }
+    // a stalled or diverging inner solve hands back to the refinement loop (as for BiCGStab)
+    if (s.inner_it - s.rin_min_it > p.stall || rr > 1e8 * s.rin_min2) {
+      s.inner_status = SYS_MAXIT;
+      if (rr > s.rin0) s.corr = 0.0;
+      return;
+    }
+    if (sqrt(cabs2(rn)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
+    s.beta = cdiv(rn, s.rho);
+    s.rho = rn;
   }
 };
 
@@ -488,29 +543,148 @@ __global__ void __launch_bounds__(256) k_copy_r(const double2* __restrict__ r, d
   VEC_LOOP(p) rprev[off + e] = r[off + e];
 }
 
-// undo a rejected correction: x -= corr d, r = r_prev
-template <typename T>
-__global__ void __launch_bounds__(256) k_revert(double2* x, const typename cplx<T>::t* __restrict__ d, double2* r,
-                                                const double2* __restrict__ rprev, const Sys* __restrict__ sys, P p) {
+// partials ||r0||^2, Re <r1, r0>, Im <r1, r0>, ||r1||^2 (r0 = r before the correction, r1 after)
+__global__ void __launch_bounds__(256) k_mr_dots(const double2* __restrict__ r0, const double2* __restrict__ r1,
+                                                 const Sys* __restrict__ sys, double* part, P p) {
   const int b = blockIdx.y;
-  if (!sys[b].reject) return;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (sys[b].outer_status == SYS_RUN) {
+    const long long off = (long long)b * p.ne;
+    VEC_LOOP(p) {
+      const double2 u = r0[off + e], v = r1[off + e];
+      acc[0] += u.x * u.x + u.y * u.y;
+      acc[1] += v.x * u.x + v.y * u.y;
+      acc[2] += v.x * u.y - v.y * u.x;
+      acc[3] += v.x * v.x + v.y * v.y;
+    }
+  }
+  fit_block_sum<double, 4>(acc, part + PSLOT(p, b));
+}
+
+// apply the step length: x += (amr - 1) corr d, r = (1 - amr) r0 + amr r1 (r holds r1)
+template <typename T>
+__global__ void __launch_bounds__(256) k_mr_combine(double2* x, const typename cplx<T>::t* __restrict__ d,
+                                                    double2* r, const double2* __restrict__ r0,
+                                                    const Sys* __restrict__ sys, P p) {
+  const int b = blockIdx.y;
+  if (!sys[b].mr) return;
   const long long off = (long long)b * p.ne;
+  const double2 al = sys[b].amr;
   const double c = sys[b].corr;
+  const double2 f = make_double2(c * (al.x - 1.0), c * al.y);  // (amr - 1) corr
+  const double2 g = make_double2(1.0 - al.x, -al.y);          // 1 - amr
   VEC_LOOP(p) {
-    auto dd = d[off + e];
+    const auto dd = d[off + e];
+    const double dx = (double)dd.x, dy = (double)dd.y;
     double2 xx = x[off + e];
-    xx.x -= c * (double)dd.x;
-    xx.y -= c * (double)dd.y;
+    xx.x += f.x * dx - f.y * dy;
+    xx.y += f.x * dy + f.y * dx;
     x[off + e] = xx;
-    r[off + e] = rprev[off + e];
+    const double2 u = r0[off + e], v = r[off + e];
+    r[off + e] = make_double2(g.x * u.x - g.y * u.y + al.x * v.x - al.y * v.y,
+                              g.x * u.y + g.y * u.x + al.x * v.y + al.y * v.x);
   }
 }
 
-// the revert of this refinement step is done: no later step may repeat it (the loop keeps running
-// while any system of the batch is active)
-__global__ void k_clear_reject(Sys* sys, int B) {
+// COCG start: r~ = r / ||r|| (vector precision), d = 0, p = z = D^-1 r~; partials (r~, z), ||r~||^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocg_start(const double2* __restrict__ r128, const Sys* __restrict__ sys,
+                                                    typename cplx<T>::t* rin, typename cplx<T>::t* pv,
+                                                    typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ dinv,
+                                                    double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  if (sys[b].outer_status == SYS_RUN) {
+    const long long off = (long long)b * p.ne;
+    const double sc = 1.0 / sys[b].rscale;
+    VEC_LOOP(p) {
+      const double2 r = r128[off + e];
+      const V rz = mkc<T>(r.x * sc, r.y * sc);
+      const V z = dinv ? cmulv(dinv[off + e], rz) : rz;
+      rin[off + e] = rz;
+      pv[off + e] = z;
+      d[off + e] = czero<V>();
+      acc[0] += rz.x * z.x - rz.y * z.y;
+      acc[1] += rz.x * z.y + rz.y * z.x;
+      acc[2] += rz.x * rz.x + rz.y * rz.y;
+    }
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// COCG: partials of (p, q) with q = A p (unconjugated)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocg_pq(const typename cplx<T>::t* __restrict__ pv,
+                                                 const typename cplx<T>::t* __restrict__ q, const Sys* __restrict__ sys,
+                                                 double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    const V a = pv[off + e], c = q[off + e];
+    acc[0] += a.x * c.x - a.y * c.y;
+    acc[1] += a.x * c.y + a.y * c.x;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// COCG: d += alpha p, r -= alpha q; partials (r, D^-1 r), ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocg_xr(typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ pv,
+                                                 typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ q,
+                                                 const typename cplx<T>::t* __restrict__ dinv, const Sys* __restrict__ sys,
+                                                 double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const T ar = (T)sys[b].alpha.x, ai = (T)sys[b].alpha.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    const V pp = pv[off + e], qq = q[off + e];
+    V dd = d[off + e], rr = r[off + e];
+    dd.x += ar * pp.x - ai * pp.y;
+    dd.y += ar * pp.y + ai * pp.x;
+    rr.x -= ar * qq.x - ai * qq.y;
+    rr.y -= ar * qq.y + ai * qq.x;
+    d[off + e] = dd;
+    r[off + e] = rr;
+    const V z = dinv ? cmulv(dinv[off + e], rr) : rr;
+    acc[0] += rr.x * z.x - rr.y * z.y;
+    acc[1] += rr.x * z.y + rr.y * z.x;
+    acc[2] += rr.x * rr.x + rr.y * rr.y;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// COCG: p = D^-1 r + beta p
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocg_p(const typename cplx<T>::t* __restrict__ r, typename cplx<T>::t* pv,
+                                                const typename cplx<T>::t* __restrict__ dinv, const Sys* __restrict__ sys,
+                                                P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const T br = (T)sys[b].beta.x, bi = (T)sys[b].beta.y;
+  VEC_LOOP(p) {
+    const V rr = r[off + e], pp = pv[off + e];
+    const V z = dinv ? cmulv(dinv[off + e], rr) : rr;
+    V o;
+    o.x = z.x + br * pp.x - bi * pp.y;
+    o.y = z.y + br * pp.y + bi * pp.x;
+    pv[off + e] = o;
+  }
+}
+
+// the step length of this refinement step is applied: no later step may apply it again (the loop
+// keeps running while any system of the batch is active)
+__global__ void k_clear_mr(Sys* sys, int B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B) sys[b].reject = 0;
+  if (b < B) sys[b].mr = 0;
 }
 
 // ---- FGMRES(m) vector kernels ---------------------------------------------------------------
@@ -905,6 +1079,7 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   size_t vec = ne * B * esz;
   size_t bytes = ne * B * 32;  // r128 and r_prev
   if (method == FIT_BICGSTAB) bytes += 6 * vec + (pc != FIT_PC_NONE ? 2 * vec : 0);
+  else if (method == FIT_COCG) bytes += 4 * vec;
   else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
   if (pc == FIT_PC_JACOBI || pc == FIT_PC_UNET) bytes += ne * esz / 2 + vec;
   size_t napply = (size_t)std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
@@ -938,6 +1113,11 @@ fit_status setup(Work& w, int B) {
       ALLOC(w.phat, vec);
       ALLOC(w.shat, vec);
     }
+  } else if (w.method == FIT_COCG) {
+    ALLOC(w.rin, vec);
+    ALLOC(w.pv, vec);
+    ALLOC(w.v, vec);
+    ALLOC(w.d, vec);
   } else {
     ALLOC(w.Vb, (size_t)(w.m + 1) * vec);
     if (w.pc != FIT_PC_NONE) {
@@ -986,7 +1166,10 @@ fit_status setup(Work& w, int B) {
   w.p.mixed = w.mixed;
   w.p.s_in = w.mixed ? g->coef_scale : 1.0;
   w.p.tiny = w.mixed ? 1e-30 : 1e-300;
-  w.p.stall = 1000;
+  // iterations without a new smallest inner residual before the inner solve hands back: COCG's
+  // residual norm is not monotone (A is complex symmetric, not Hermitian) and can wander above its
+  // minimum for thousands of iterations before it falls again, so it gets a far longer window
+  w.p.stall = w.method == FIT_COCG ? 20000 : 1000;
   w.p.precond = w.pc;
   if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {
     long long nc = g->ncell;
@@ -1049,6 +1232,13 @@ struct Seq {
   void inner_start() {
     using V = typename cplx<T>::t;
     k_reset_guard<<<1, 1, 0, s>>>(w.ctl, 0, h_inner, use_h_inner);
+    if (w.method == FIT_COCG) {
+      k_cocg_start<T><<<vgrid(), 256, 0, s>>>(w.r128, w.sys, (V*)w.rin, (V*)w.pv, (V*)w.d, (const V*)w.dinv,
+                                              w.part_vec, w.p);
+      check();
+      fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocgStart{});
+      return;
+    }
     bool bicg = w.method == FIT_BICGSTAB;
     if (bicg)
       k_inner_start<T, true><<<vgrid(), 256, 0, s>>>(w.r128, w.sys, (V*)w.rin, (V*)w.rhat, (V*)w.pv, (V*)w.v,
@@ -1062,6 +1252,29 @@ struct Seq {
       k_fg_reset<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.G, w.sys, w.p);
       check();
     }
+  }
+
+  // one COCG iteration (predicated on inner status): q = A p, then alpha, the x/r update, beta, p
+  template <typename T>
+  void cocg_iter(const int* st_inner) {
+    using V = typename cplx<T>::t;
+    apply(w.pv, w.v, FIT_EPI_NONE, nullptr, w.inner, st_inner);
+    k_cocg_pq<T><<<vgrid(), 256, 0, s>>>((const V*)w.pv, (const V*)w.v, w.sys, w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocgAlpha{});
+    k_cocg_xr<T><<<vgrid(), 256, 0, s>>>((V*)w.d, (const V*)w.pv, (V*)w.rin, (const V*)w.v, (const V*)w.dinv, w.sys,
+                                         w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocgRho{});
+    k_cocg_p<T><<<vgrid(), 256, 0, s>>>((const V*)w.rin, (V*)w.pv, (const V*)w.dinv, w.sys, w.p);
+    check();
+  }
+
+  // one iteration of the single-vector methods (BiCGStab or COCG)
+  template <typename T>
+  void loop_iter(const int* st_inner) {
+    if (w.method == FIT_COCG) cocg_iter<T>(st_inner);
+    else bicg_iter<T>(st_inner);
   }
 
   // one BiCGStab iteration (predicated on inner status)
@@ -1178,10 +1391,12 @@ struct Seq {
     k_copy_r<<<vgrid(), 256, 0, s>>>(w.r128, w.rprev, w.sys, w.p);
     k_update_x<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.sys, w.p);
     check();
-    long long n3 = apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
-    fin<3>(w.part_apply, n3, 4, OpOuter{});
-    k_revert<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.r128, w.rprev, w.sys, w.p);
-    k_clear_reject<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.sys, w.p.B);
+    apply(x, w.r128, FIT_EPI_RESID, rhs, FIT_C128, st_outer);
+    k_mr_dots<<<vgrid(), 256, 0, s>>>(w.rprev, w.r128, w.sys, w.part_vec, w.p);
+    check();
+    fin<4>(w.part_vec, w.p.nblk, w.p.pstride, OpOuter{});
+    k_mr_combine<T><<<vgrid(), 256, 0, s>>>(x, (const V*)w.d, w.r128, w.rprev, w.sys, w.p);
+    k_clear_mr<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.sys, w.p.B);
     check();
     if (hist) {
       k_history<<<vgrid(), 256, 0, s>>>(x, hist, w.sys, hist_every, hist_len, w.p);
@@ -1227,8 +1442,8 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
   }
   // pick the apply kernels (autotuner) now: timing cannot run inside a stream capture
   {
-    void* ti = w.method == FIT_BICGSTAB ? w.pv : w.Vb;
-    void* to = w.method == FIT_BICGSTAB ? w.v : w.d;
+    void* ti = w.method == FIT_FGMRES ? w.Vb : w.pv;
+    void* to = w.method == FIT_FGMRES ? w.d : w.v;
     FIT_CHECK_CUDA(cudaMemsetAsync(ti, 0, (size_t)w.p.ne * w.p.B * w.esz, s));
     fit_status ts = fit_tune_apply(w.g, w.p.B, w.omega, ti, to, w.inner, s);
     if (ts == FIT_OK) ts = fit_tune_apply(w.g, w.p.B, w.omega, rhs, w.r128, FIT_C128, s);
@@ -1237,7 +1452,7 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
   auto mirror = [&](cudaStream_t ss) {
     k_mirror_status<<<(w.p.B + 127) / 128, 128, 0, ss>>>(w.sys, st_inner, st_outer, w.p.B);
   };
-  const bool bicg = w.method == FIT_BICGSTAB;
+  const bool bicg = w.method == FIT_BICGSTAB || w.method == FIT_COCG;  // single-vector loop methods
 
   // FIT_TRACE_SOLVE=1 prints the scalars of system 0 after every host-loop step (stderr)
   const char* tr = getenv("FIT_TRACE_SOLVE");
@@ -1261,7 +1476,7 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
       mirror(s);
       if (bicg) {
         for (int it = 0; it < max_inner_guard; ++it) {
-          q.bicg_iter<T>(st_inner);
+          q.loop_iter<T>(st_inner);
           mirror(s);
           if (it % 100 == 99) dump("bicg it", it + 1);
           q.cond(0, max_inner_guard, 0, 0);
@@ -1366,7 +1581,7 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
            "capture inner body");
       if (result != FIT_OK) break;
       q.s = s_inner;
-      q.bicg_iter<T>(st_inner);
+      q.loop_iter<T>(st_inner);
       mirror(s_inner);
       q.cond(0, max_inner_guard, h_inner, 1);
       cudaGraph_t tmp;
@@ -1491,9 +1706,10 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
   fit_solve_opts o;
   fit_solve_opts_default(&o);
   if (opts) o = *opts;
-  FIT_REQUIRE(o.method == FIT_BICGSTAB || o.method == FIT_FGMRES, "fit_solve: unknown method");
+  FIT_REQUIRE(o.method == FIT_BICGSTAB || o.method == FIT_FGMRES || o.method == FIT_COCG,
+              "fit_solve: unknown method");
   FIT_REQUIRE(o.precision == FIT_SOLVE_C128 || o.precision == FIT_SOLVE_MIXED, "fit_solve: unknown precision");
-  FIT_REQUIRE(o.method == FIT_BICGSTAB || (o.restart >= 1 && o.restart <= FG_MAXV - 1),
+  FIT_REQUIRE(o.method != FIT_FGMRES || (o.restart >= 1 && o.restart <= FG_MAXV - 1),
               "fit_solve: FGMRES restart must be in 1..64");
   FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET,
               "fit_solve: unknown preconditioner");

@@ -35,7 +35,7 @@ def _oracle_relres(case, w, x, b):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("method", [0, 1, 2])
 def test_cavity16_solve(precision, method):
     """The cavity workload: 16^3 PEC vacuum cube, 5 GHz, centre z-edge source, tol 1e-10."""
     from oracle import krylov as K
@@ -50,7 +50,7 @@ def test_cavity16_solve(precision, method):
 
 
 @pytest.mark.parametrize("use_graph", [0, 1])
-@pytest.mark.parametrize("method,precond", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("method,precond", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
 def test_small_lossy_batch(method, precond, use_graph):
     case = G.small_random(20, 18, 11, seed=31, pec_frac=0.05)
     n = 3 * 20 * 18 * 11
@@ -93,7 +93,8 @@ def test_every_fused_variant_in_a_solve(monkeypatch):
                 assert rr <= 1e-9, (k, len(fs), i, rr, rep[i])
 
 
-def test_graph_and_host_loop_agree_exactly(monkeypatch):
+@pytest.mark.parametrize("method", [0, 2])
+def test_graph_and_host_loop_agree_exactly(monkeypatch, method):
     """The device-side loop (graph) and the host-driven loop run the same kernels in the same order.
     Each solve uses its own grid handle, whose autotuner could pick a different apply variant (a
     different summation order), so one kernel is forced for both."""
@@ -101,8 +102,8 @@ def test_graph_and_host_loop_agree_exactly(monkeypatch):
     case = G.small_random(16, 12, 10, seed=41, pec_frac=0.0)
     n = 3 * 16 * 12 * 10
     rhs = G.random_vector(n, 5)[None]
-    a = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=0)
-    b = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=1)
+    a = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=0, method=method)
+    b = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=1, method=method)
     assert a[1][0]["iterations"] == b[1][0]["iterations"]
     assert np.array_equal(a[2], b[2])
 
@@ -134,6 +135,19 @@ def test_layered64_mixed_vs_c128():
         out[prec] = xs[0]
     diff = np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0])
     assert diff <= 1e-4, diff
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_layered64_cocg_jacobi(precision):
+    """COCG (the paper's "cg" on the complex symmetric system) with the Jacobi diagonal on the 64^3
+    member of the layered family, in complex64 inside FP64 refinement and in complex128, judged by
+    the oracle residual."""
+    case = G.layered_blocks(n=64, seed=1000)
+    st, rep, xs, bs, ws = _solve(case, case["freqs"], 1e-8, precision=precision, method=2, precond=1,
+                                 max_iter=200000, max_outer=4000)
+    assert st == 0, (precision, rep)
+    rr, _ = _oracle_relres(case, ws[0], xs[0], bs[0])
+    assert rr <= 1e-8, (precision, rr, rep)
 
 
 def test_stripline96_batched_subset():

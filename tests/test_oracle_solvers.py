@@ -1,4 +1,4 @@
-"""Pins of the oracle's solvers: dense LU on a 4^3 grid = sparse direct = BiCGStab = GMRES, and
+"""Pins of the oracle's solvers: dense LU on a 4^3 grid = sparse direct = BiCGStab = GMRES = COCG, and
 manufactured solutions b = A e* recovered within kappa * tol (Sec. IV solvers; Eq. e2)."""
 import numpy as np
 import pytest
@@ -64,3 +64,46 @@ def test_cavity16_bicgstab_vs_sparse_direct():
     assert st == 0 and rr <= 1e-10
     assert np.linalg.norm(x - x_d) <= 1e-6 * np.linalg.norm(x_d)
     assert np.all(x[mask != 0] == 0)
+
+
+def test_cocg_is_cg_on_real_spd():
+    """On a real symmetric positive definite matrix the unconjugated form equals the inner product,
+    so COCG must be CG: it matches the dense solution, and with 6 distinct eigenvalues (a
+    block-diagonal matrix built from them) it terminates within 6 steps up to rounding."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(3)
+    lam = np.array([0.5, 1.0, 2.0, 3.5, 7.0, 11.0])
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    A = sp.csr_matrix(Q @ np.diag(np.repeat(lam, 10)) @ Q.T)
+    b = rng.standard_normal(60) + 0j
+    x, it, rr, st = K.cocg(A, b, tol=1e-12, maxiter=100)
+    assert st == 0 and it <= 7, (it, rr)
+    assert np.allclose(x, np.linalg.solve(A.toarray(), b), rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_cocg_on_complex_symmetric_4cubed(precond):
+    """The lossy 4^3 FIT system is complex symmetric (A^T = A, not Hermitian): COCG, with or without
+    the Jacobi diagonal, reaches the dense solution; a conjugated CG on it does not."""
+    c = G.small_random(4, 4, 4, seed=5, lossy=True)
+    A, mask = _system(c, 2e9)
+    assert abs(A - A.T).max() == 0 and abs(A - A.conj().T).max() > 0
+    b = G.random_vector(A.shape[0], seed=6) * (1 - mask)
+    x_dense = K.dense_solve(A, b)
+    dinv = 1.0 / A.diagonal() if precond else None
+    x, it, rr, st = K.cocg(A, b, tol=1e-12, maxiter=5000, dinv=dinv)
+    assert st == 0 and rr <= 1e-12
+    cond = np.linalg.cond(A.toarray())
+    assert np.linalg.norm(x - x_dense) <= 10 * cond * 1e-12 * np.linalg.norm(x_dense)
+    # the Hermitian CG recurrence (conjugated dots) on this non-Hermitian A stalls far above tol
+    xr = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rho = np.vdot(r, r)
+    for _ in range(3 * A.shape[0]):
+        q = A @ p
+        a = rho / np.vdot(p, q)
+        xr, r = xr + a * p, r - a * q
+        rho2 = np.vdot(r, r)
+        p, rho = r + (rho2 / rho) * p, rho2
+    assert K.relres(A, xr, b) > 1e-6
