@@ -174,6 +174,48 @@ fit_status tconv_fwd(const bf16* in, const float* w, const float* b, bf16* out, 
   return FIT_OK;
 }
 
+// tcgen05 conv3: same z-chunking rule as launch_conv3, 32 x 4 voxel tiles, NC output channels per CTA
+template <int CIN, int NC>
+fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
+  auto kern = unet::conv3_tc_kernel<CIN, NC>;
+  constexpr int smem = unet::TcShape<CIN, NC>::smem();
+  constexpr int TY = unet::TcShape<CIN, NC>::TY;
+  static int per_sm = 0, nsm = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    FIT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FIT_CHECK_CUDA(cudaGetDevice(&dev));
+    FIT_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int p = 0;
+    FIT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kern, 128, smem));
+    if (p < 1) {
+      fit_set_error("U-Net: tcgen05 conv tile does not fit on an SM");
+      return FIT_EINVAL;
+    }
+    per_sm = p;
+  }
+  const int gx = (a.nx + unet::CX - 1) / unet::CX, gy = (a.ny + TY - 1) / TY, nblk = (a.cout + NC - 1) / NC;
+  const long long cols = (long long)gx * gy * nblk;
+  const long long per_col = std::max(1LL, (long long)per_sm * nsm / cols);
+  const int tz = (int)std::max(2LL, ((long long)a.nz + per_col - 1) / per_col);
+  const int nzc = (a.nz + tz - 1) / tz;
+  dim3 grid(gx, gy, (unsigned)(nzc * nblk));
+  kern<<<grid, 128, smem, s>>>(a, tz);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+// The 16-input-channel convs run on mma.sync by default; FIT_CONV=tc selects the tcgen05 kernel.
+// Both pass the same parity tests.  With N = 16 output channels each tcgen05 MMA is 128 x 16 x 16,
+// and the 27 taps accumulate into one TMEM tile as a dependent chain, so one CTA spends about 5 us
+// per plane on issue, commit and wait: 2.06 ms per 128^3 network application against 1.59 ms on
+// mma.sync.  Interleaving independent accumulators (more row tiles or planes per CTA) is what it
+// needs next.
+static bool conv_use_tc() {
+  const char* e = getenv("FIT_CONV");
+  return e && !strcmp(e, "tc");
+}
+
 // conv3 launch: picks the (CIN, NC, TY) instantiation; in2/out2 implement concat / split
 fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w, const float* bias, bf16* out1, int o1,
                  bf16* out2, int o2, int nx, int ny, int nz, int relu, cudaStream_t s) {
@@ -194,6 +236,10 @@ fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w
   a.nz = nz;
   a.relu = relu;
   const int cin = c1 + c2;
+  if (cin == 16 && conv_use_tc()) {
+    if (a.cout <= 16) return launch_conv3_tc<16, 16>(a, s);
+    return launch_conv3_tc<16, 32>(a, s);
+  }
   // shared memory per CTA: (16,16,8) 86 KB, (16,32,8) 107 KB, (32,16,4) 100 KB, (64,16,4) 180 KB
   if (cin == 16 && a.cout <= 16) return launch_conv3<16, 16, 8>(a, s);
   if (cin == 16) return launch_conv3<16, 32, 8>(a, s);

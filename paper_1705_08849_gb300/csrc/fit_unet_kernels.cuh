@@ -200,6 +200,212 @@ __global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a, int tz) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// The same 3x3x3 convolution on the 5th-generation tensor cores (tcgen05.mma, accumulator in TMEM).
+// A CTA of 4 warps owns 32 x 4 output voxels (M = 128) per z-plane, all NC output channels (N), and
+// marches a chunk of z-planes.  Per plane and tap (dz, dy, dx) the A operand (128 voxels x CIN) is a
+// window of a staged input plane, and one elected thread issues the 27 * CIN / 16 MMAs of K = 16.
+// Layouts (canonical, no swizzle, K-major; a "line" is 8 bf16 channels = 16 bytes):
+//   input plane, staged 3 times (shifted by dx = 0, 1, 2 voxels): [g = CIN/8][r = 6 rows][v = 32] lines,
+//     so the 128 rows of a window (rows dy .. dy+3, voxels 0 .. 31) are 128 consecutive lines:
+//     core matrices of 8 rows are 128 B apart (SBO), channel groups 6 * 32 * 16 B apart (LBO);
+//   weights: [tap][g][n = NC] lines: SBO = 128 B, LBO = NC * 16 B.
+// The ring holds 4 planes (z-1 .. z+1 in use, z+2 arriving by cp.async).  Every mbarrier wait is
+// bounded; on a timeout the CTA records it in g_conv_timeout, waits (bounded) for its MMAs, frees
+// its TMEM and leaves.
+// ------------------------------------------------------------------------------------------------
+__device__ int g_conv_timeout;
+
+template <int CIN, int NC>
+struct TcShape {
+  static constexpr int TY = 4, ROWS = TY + 2, LINES = ROWS * 32;  // lines per channel group of a copy
+  static constexpr int COPY = (CIN / 8) * LINES * 16;              // bytes of one shifted copy
+  static constexpr int PLANE = 3 * COPY;
+  static constexpr int WBYTES = 27 * (CIN / 8) * NC * 16;
+  static constexpr int OFF_RING = ((WBYTES + 1023) / 1024) * 1024;
+  static constexpr int OFF_BAR = OFF_RING + 4 * PLANE;             // mbarrier (8 B) + TMEM address (4 B)
+  static constexpr int smem() { return OFF_BAR + 16 + 1024; }  // + slack for 1 KB alignment
+};
+
+__device__ inline uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // version 1, no swizzle, base offset 0
+}
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ inline bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <int CIN, int NC>
+__global__ void __launch_bounds__(128) conv3_tc_kernel(ConvArgs a, int tz) {
+  using SH = TcShape<CIN, NC>;
+  constexpr int TY = SH::TY, CG = CIN / 8;
+  static_assert(CIN % 16 == 0 && (NC == 16 || NC == 32), "tcgen05 conv shape");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* w_s = smem;
+  unsigned char* ring = smem + SH::OFF_RING;
+  const uint32_t bar = smem_addr(smem + SH::OFF_BAR);
+  uint32_t* tmem_slot = (uint32_t*)(smem + SH::OFF_BAR + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * TY;
+  const int nblk_n = (a.cout + NC - 1) / NC;
+  const int zc = blockIdx.z / nblk_n, n0 = (blockIdx.z % nblk_n) * NC;
+  const int z0 = zc * tz, z1 = min(a.nz, z0 + tz);
+  if (z0 >= z1) return;  // uniform over the CTA, before any TMEM is taken
+
+  if (warp == 0) {  // TMEM: 32 columns of 128 lanes x 32 bit hold the 128 x NC FP32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // plane p -> ring slot (p - (z0 - 1)) % 4; copy dx, line (g, r, v) at dx*COPY + (g*LINES + r*32 + v)*16
+  auto load_plane = [&](int p) {
+    unsigned char* dst = ring + ((p - (z0 - 1)) & 3) * SH::PLANE;
+    for (int q = tid; q < 3 * CG * SH::LINES; q += 128) {
+      const int v = q & 31, r = (q >> 5) % SH::ROWS, g = (q / SH::LINES) % CG, dx = q / (CG * SH::LINES);
+      const int gx = x0 - 1 + dx + v, gy = y0 - 1 + r;
+      const bool in = gx >= 0 && gy >= 0 && p >= 0 && gx < a.nx && gy < a.ny && p < a.nz;
+      const void* src = a.in1;
+      if (in) {
+        const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * p);
+        const int c = g * 8;
+        src = c < a.c1 ? (const void*)(a.in1 + gv * a.c1 + c) : (const void*)(a.in2 + gv * a.c2 + (c - a.c1));
+      }
+      cp_async16(smem_addr(dst + dx * SH::COPY + (g * SH::LINES + r * 32 + v) * 16), src, in ? 16 : 0);
+    }
+  };
+  // weights [tap][g][n] lines, output channels n0 .. n0 + NC - 1
+  for (int q = tid; q < 27 * CG * NC; q += 128) {
+    const int n = q % NC, g = (q / NC) % CG, tap = q / (NC * CG);
+    const bool in = n0 + n < a.cout;
+    const void* src = in ? (const void*)(a.w + ((long long)tap * a.cout + n0 + n) * CIN + g * 8) : (const void*)a.w;
+    cp_async16(smem_addr(w_s + q * 16), src, in ? 16 : 0);
+  }
+  load_plane(z0 - 1);
+  load_plane(z0);
+  load_plane(z0 + 1);
+  cp_async_commit();
+
+  constexpr uint32_t IDESC = tc_idesc_bf16(128, NC);
+  bool bad = false;
+  int step = 0;
+  for (int z = z0; z < z1 && !bad; ++z, ++step) {
+    if (z + 2 <= z1) load_plane(z + 2);
+    cp_async_commit();
+    cp_async_wait<1>();  // planes z-1 .. z+1 (and the weights) have landed
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core's reads
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t wbase = smem_addr(w_s), rbase = smem_addr(ring);
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const uint32_t abase = rbase + ((z - 1 + dz - (z0 - 1)) & 3) * SH::PLANE + dx * SH::COPY + dy * 32 * 16;
+        const uint32_t bbase = wbase + tap * CG * NC * 16;
+#pragma unroll
+        for (int kk = 0; kk < CIN / 16; ++kk) {
+          const uint64_t ad = tc_smem_desc(abase + kk * 2 * SH::LINES * 16, SH::LINES * 16, 128);
+          const uint64_t bd = tc_smem_desc(bbase + kk * 2 * NC * 16, NC * 16, 128);
+          const uint32_t acc = (tap | kk) != 0 ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                   : "memory");
+    }
+    if (!tc_mbar_wait(bar, step & 1)) {  // the MMAs of this plane are done (smem read, TMEM written)
+      bad = true;
+      if (tid == 0) atomicExch(&g_conv_timeout, 1);
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w reads TMEM lanes 32w .. 32w+31 = tile row w, voxel x0 + lane
+    float v[NC];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+    if (NC == 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+    } else {
+#pragma unroll
+      for (int h = 0; h < NC / 16; ++h) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + 16 * h));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[16 * h + c] = __uint_as_float(r[c]);
+      }
+    }
+    const int gx = x0 + lane, gy = y0 + warp;
+    if (gx < a.nx && gy < a.ny) {
+      const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * z);
+#pragma unroll
+      for (int c = 0; c < NC; c += 2) {
+        const int co = n0 + c;
+        if (co >= a.cout) break;
+        float v0 = v[c], v1 = v[c + 1];
+        if (a.bias) {
+          v0 += a.bias[co];
+          v1 += a.bias[co + 1];
+        }
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        const __nv_bfloat162 pv = __floats2bfloat162_rn(v0, v1);
+        if (co < a.o1) *reinterpret_cast<__nv_bfloat162*>(a.out1 + gv * a.o1 + co) = pv;
+        else *reinterpret_cast<__nv_bfloat162*>(a.out2 + gv * a.o2 + (co - a.o1)) = pv;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM read out and plane z-1's slot free before the next plane's MMAs and copies
+  }
+  if (bad) (void)tc_mbar_wait(bar, step & 1);  // bounded: let this plane's MMAs finish before freeing TMEM
+  cp_async_wait<0>();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Weight gradient of a 3x3x3 convolution (FP32 on the CUDA cores):
 //   dW[tap][co][ci] += sum_v dy[v][co] * x[v + off(tap)][ci],   db[co] += sum_v dy[v][co]
 // Grid (voxel chunks, 27 taps); each thread owns a 4 x 4 block of (co, ci) and accumulates over

@@ -32,8 +32,15 @@ def _net_and_input(seed, shape, head_scale=0.5):
     return net, p, x
 
 
+@pytest.fixture(params=["mma", "tc"])
+def conv_kernel(request, monkeypatch):
+    """Every network test runs with the mma.sync convolutions and with the tcgen05 ones."""
+    monkeypatch.setenv("FIT_CONV", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("shape", [(8, 8, 8), (8, 12, 16), (12, 8, 36)])
-def test_forward_matches_oracle(shape):
+def test_forward_matches_oracle(shape, conv_kernel):
     torch = torch_cuda()
     from oracle import unet as U
     net, p, x = _net_and_input(11, shape)
@@ -47,7 +54,7 @@ def test_forward_matches_oracle(shape):
     assert rel <= 5e-3, rel
 
 
-def test_gradients_match_oracle():
+def test_gradients_match_oracle(conv_kernel):
     torch = torch_cuda()
     from oracle import unet as U
     shape = (8, 8, 12)
@@ -69,7 +76,7 @@ def test_gradients_match_oracle():
         off += n
 
 
-def test_training_reduces_loss():
+def test_training_reduces_loss(conv_kernel):
     torch = torch_cuda()
     shape = (8, 8, 8)
     net, p, x = _net_and_input(13, shape, head_scale=0.0)
