@@ -210,6 +210,49 @@ def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
     return out
 
 
+def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None):
+    """A wide-band sweep: nfreq of the workload's frequencies (evenly picked), b_f = -j w_f j, solved
+    to a 1e-8 true residual with the Jacobi preconditioner, once as one batch (one graph launch for
+    all systems) and once as nfreq sequential single-frequency solves.  Wall time of fit_solve."""
+    import fitgen as G
+    if band:  # nfreq frequencies evenly spaced over [fmin, fmax]
+        sel = np.linspace(band[0], band[1], max(1, nfreq))
+    else:
+        fr = np.asarray(case["freqs"], dtype=np.float64)
+        sel = fr[np.unique(np.linspace(0, len(fr) - 1, max(1, min(nfreq, len(fr)))).round().astype(int))]
+    ws = 2 * np.pi * sel
+    mname, _, pname = kind.rpartition("-")
+    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname or "fgmres"]
+    prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
+    j = torch.from_numpy(G.source_vector(case)).cuda()
+    ne = j.numel()
+    b = torch.stack([(-1j * w) * j for w in ws]).reshape(-1)
+    opts = dict(precision=prec, method=method, restart=30, precond=fit.FIT_PC_JACOBI, max_iter=max_iter,
+                max_outer=max_iter)
+    out = {"frequencies_hz": sel.tolist(), "method": kind}
+    with fit.Grid.from_case(case) as g:
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = g.solve(ws, b, x, 1e-8, batch=0, **opts)
+        torch.cuda.synchronize()
+        out["batched"] = {"s": time.perf_counter() - t0, "statuses": [fit.status_str(r["status"]) for r in rep],
+                          "iterations": [r["iterations"] for r in rep], "relres": [r["relres"] for r in rep]}
+        seq_t, seq_rep = 0.0, []
+        for f, w in enumerate(ws):
+            xf = torch.zeros(ne, dtype=b.dtype, device="cuda")
+            bf = b[f * ne:(f + 1) * ne].contiguous()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, rep1 = g.solve([w], bf, xf, 1e-8, **opts)
+            torch.cuda.synchronize()
+            seq_t += time.perf_counter() - t0
+            seq_rep.append(rep1[0])
+        out["sequential"] = {"s": seq_t, "statuses": [fit.status_str(r["status"]) for r in seq_rep],
+                             "iterations": [r["iterations"] for r in seq_rep]}
+    return out
+
+
 def time_unet(fit, torch, case, steps, warmup):
     """One application of the learned preconditioner's network (bf16 NDHWC input of 16 channels ->
     6 FP32 channels) on the workload's grid, CUDA-event timed after warm-up; flops from the layer
@@ -251,7 +294,9 @@ def main():
     ap.add_argument("--workload", default="layered128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=1, help="systems (frequencies) per apply in the apply mode")
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet"],
+    ap.add_argument("--nfreq", type=int, default=8, help="frequencies of the sweep mode")
+    ap.add_argument("--band", default="", help="sweep mode: fmin,fmax in Hz (default: the workload's own frequencies)")
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet", "sweep"],
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
     ap.add_argument("--solve", default="mixed,cocg-mixed",
                     help="comma list of solves to time, each [method-]precision with method fgmres (default), "
@@ -285,6 +330,14 @@ def main():
     case = _workload(args.workload)
     kinds = [k for k in args.solve.split(",") if k.rpartition("-")[2] in ("mixed", "c128")
              and k.rpartition("-")[0] in ("", "fgmres", "cocg", "bicgstab")]
+    if args.mode == "sweep":
+        if rank == 0:
+            kind = kinds[0] if kinds else "cocg-mixed"
+            print(json.dumps({"metric": "wide-band sweep s to 1e-8", "unit": "s", "workload": args.workload,
+                              "sweep": time_sweep(fit, torch, case, args.nfreq, kind, args.max_iter,
+                                                  [float(v) for v in args.band.split(",")] if args.band else None)}),
+                  flush=True)
+        return
     if args.mode == "unet":
         if rank == 0:
             print(json.dumps(time_unet(fit, torch, case, args.steps, args.warmup)), flush=True)

@@ -57,6 +57,7 @@ struct Sys {
   int hist_pad;
   int rin_min_it;      // iteration at which it was reached
   int mr;              // 1: the step length amr of this refinement step is still to be applied
+  int replay;          // > 0: the last inner solve failed; stop the next one at this iteration
   double2 amr;         // minimal-residual step length along this step's correction
 };
 
@@ -143,6 +144,7 @@ struct OpOuterInit {  // q2 = ||b||^2
     s.iters = 0;
     s.stagn = 0;
     s.mr = 0;
+    s.replay = 0;
     s.inner_status = SYS_CONV;
     s.inner_it = 0;
     if (!isfinite(q[2])) s.outer_status = SYS_NAN;
@@ -168,7 +170,9 @@ struct OpOuter {
     double2 al = make_double2(0.0, 0.0);
     double r2 = a;
     const double den = a - 2.0 * bb.x + c;  // ||u||^2
-    if (isfinite(c) && cfinite(bb) && den > 0.0) {
+    // a dropped correction (corr = 0) keeps r = r0 bit for bit, so that a replayed inner solve
+    // starts from exactly the residual the failed one started from
+    if (s.corr != 0.0 && isfinite(c) && cfinite(bb) && den > 0.0) {
       al = make_double2((a - bb.x) / den, -bb.y / den);  // <u, r0> / ||u||^2
       // ||(1 - amr) r0 + amr r1||^2 = a - |a - bb|^2 / den = c - |c - bb|^2 / den; evaluated from the
       // smaller of a and c, so that its rounding error is relative to the smaller residual
@@ -177,8 +181,12 @@ struct OpOuter {
     }
     s.amr = al;
     if (!isfinite(a)) { s.outer_status = SYS_NAN; return; }
-    s.rnorm2 = r2;
-    s.rscale = sqrt(r2);
+    if (s.corr != 0.0) {  // a dropped step leaves the residual and its scale exactly as they were
+      s.rnorm2 = r2;
+      s.rscale = sqrt(r2);
+    } else {
+      r2 = s.rnorm2;
+    }
     if (r2 <= s.tol2) { s.outer_status = SYS_CONV; return; }
     if (r2 < 0.99 * s.best2) { s.best2 = r2; s.stagn = 0; }
     else s.stagn += 1;
@@ -208,6 +216,13 @@ struct OpInnerStart {
     double it = p.mixed ? fmax(p.inner_tol, need) : fmax(need, 1e-15);
     s.inner_tol2 = it * it * q[0];
     s.max_inner = max(1, p.max_iter - s.iters);
+    // The previous inner solve ended above its start and its correction was dropped.  This one
+    // starts from the same residual (x and r are unchanged) and runs the same kernels, so it retraces
+    // the same iterates: stop it where the last one had its smallest residual and keep that iterate.
+    if (s.replay > 0) {
+      s.max_inner = min(s.max_inner, s.replay);
+      s.replay = 0;
+    }
   }
 };
 
@@ -250,7 +265,10 @@ struct OpCocgRho {  // q0,q1 = (r, D^-1 r), q2 = ||r||^2
     // a stalled or diverging inner solve hands back to the refinement loop (as for BiCGStab)
     if (s.inner_it - s.rin_min_it > p.stall || rr > 1e8 * s.rin_min2) {
       s.inner_status = SYS_MAXIT;
-      if (rr > s.rin0) s.corr = 0.0;
+      if (rr > s.rin0) {
+        s.corr = 0.0;
+        s.replay = s.rin_min_it;
+      }
       return;
     }
     if (sqrt(cabs2(rn)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
@@ -295,7 +313,10 @@ struct OpRho {  // q0,q1 = <r^, r_new>, q2 = ||r_new||^2
     if (s.inner_it - s.rin_min_it > p.stall || rr > 1e8 * s.rin_min2) {  // 1e4 in norm
       s.inner_status = SYS_MAXIT;
       // an inner solve that ends above its starting residual would make x worse: drop it
-      if (rr > s.rin0) s.corr = 0.0;
+      if (rr > s.rin0) {
+        s.corr = 0.0;
+        s.replay = s.rin_min_it;
+      }
       return;
     }
     if (sqrt(cabs2(rn)) < p.tiny || sqrt(cabs2(s.omega)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
@@ -525,6 +546,7 @@ __global__ void __launch_bounds__(256) k_update_x(double2* x, const typename cpl
   if (sys[b].outer_status != SYS_RUN) return;
   const long long off = (long long)b * p.ne;
   const double c = sys[b].corr;
+  if (c == 0.0) return;  // a dropped correction: 0 * d would turn an overflowed d into NaN
   VEC_LOOP(p) {
     auto dd = d[off + e];
     double2 xx = x[off + e];
@@ -574,15 +596,19 @@ __global__ void __launch_bounds__(256) k_mr_combine(double2* x, const typename c
   const double2 f = make_double2(c * (al.x - 1.0), c * al.y);  // (amr - 1) corr
   const double2 g = make_double2(1.0 - al.x, -al.y);          // 1 - amr
   VEC_LOOP(p) {
-    const auto dd = d[off + e];
-    const double dx = (double)dd.x, dy = (double)dd.y;
-    double2 xx = x[off + e];
-    xx.x += f.x * dx - f.y * dy;
-    xx.y += f.x * dy + f.y * dx;
-    x[off + e] = xx;
+    if (c != 0.0) {
+      const auto dd = d[off + e];
+      const double dx = (double)dd.x, dy = (double)dd.y;
+      double2 xx = x[off + e];
+      xx.x += f.x * dx - f.y * dy;
+      xx.y += f.x * dy + f.y * dx;
+      x[off + e] = xx;
+    }
     const double2 u = r0[off + e], v = r[off + e];
-    r[off + e] = make_double2(g.x * u.x - g.y * u.y + al.x * v.x - al.y * v.y,
-                              g.x * u.y + g.y * u.x + al.x * v.y + al.y * v.x);
+    if (al.x == 0.0 && al.y == 0.0) r[off + e] = u;  // no step: r0 bit for bit
+    else
+      r[off + e] = make_double2(g.x * u.x - g.y * u.y + al.x * v.x - al.y * v.y,
+                                g.x * u.y + g.y * u.x + al.x * v.y + al.y * v.x);
   }
 }
 
