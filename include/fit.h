@@ -165,6 +165,11 @@ void fit_solve_opts_default(fit_solve_opts* opts);
  *   tol      relative residual target (> 0)
  *   opts     NULL for defaults
  *   report   HOST array of nfreq reports (may be NULL)
+ * Refinement: every outer step solves A d = r approximately (complex64 inner solve in
+ * FIT_SOLVE_MIXED) and recomputes the true residual in FP64.  x then moves along d by the complex
+ * step length that minimises ||b - A x||, so the true residual never grows.  An inner solve that
+ * ends above its starting residual gives no step, and the next one (from the same residual, so
+ * along the same iterates) stops where that one was smallest.
  * Returns FIT_OK if every system converged, else the first non-OK per-system status, or an
  * error.  Synchronous on opts->stream.  FIT_EBUDGET if the Krylov workspace for the batch does
  * not fit the handle's HBM budget (checked before any allocation). */
