@@ -686,6 +686,9 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
         const int i = i0 + tx, j = j0 + ty;
         const bool valid = i < a.nx && j < a.ny;
         const int nvalid = 3 * max(0, min(TX, a.nx - i0));
+        // two planes per trip: the values carried from plane k to k+1 stay in place instead of being
+        // copied between registers every step
+#pragma unroll 2
         for (int k = k0; k < k1; ++k) {
           const int qk = k - k0 + 1, qn = qk + 1;
           if (__any_sync(0xffffffffu, !mbar_wait_handoff(&ready[(G0 + qn) % S], ((G0 + qn) / S) & 1))) {
@@ -1121,15 +1124,15 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
   FIT_CHECK_CUDA(cudaEventCreate(&e0));
   FIT_CHECK_CUDA(cudaEventCreate(&e1));
   fit_epi none;
-  // two passes over the candidates (so that slow clocks or a neighbour's traffic during one pass
-  // do not decide), each candidate timed as the median of 5 launches; a candidate keeps its better pass
+  // three passes over the candidates (so that slow clocks or a neighbour's traffic during one pass
+  // do not decide), each candidate timed as the median of 7 launches; a candidate keeps its best pass
   std::vector<float> t(n + 1, 1e30f);
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < 3; ++pass) {
     for (int c = -1; c < n; ++c) {
       fit_status st = launch_choice(g, c, nbatch, omega_dev, x, y, prec, 1.0, s, none);  // warm-up
       if (st != FIT_OK) continue;
-      float ms[5];
-      for (int r = 0; r < 5; ++r) {
+      float ms[7];
+      for (int r = 0; r < 7; ++r) {
         cool();
         cudaEventRecord(e0, s);
         launch_choice(g, c, nbatch, omega_dev, x, y, prec, 1.0, s, none);
@@ -1138,8 +1141,8 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
         ms[r] = 0.f;
         cudaEventElapsedTime(&ms[r], e0, e1);
       }
-      std::sort(ms, ms + 5);
-      t[c + 1] = std::min(t[c + 1], ms[2]);
+      std::sort(ms, ms + 7);
+      t[c + 1] = std::min(t[c + 1], ms[3]);
     }
   }
   float best_ms = 1e30f;
