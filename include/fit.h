@@ -258,6 +258,63 @@ fit_status fit_jacobi(fit_grid* g, int nbatch, const double* omega, const void* 
  * s * (SI values): s = 1 / max M_nu.  Materials must be set. */
 fit_status fit_coef_scale(const fit_grid* g, double* s);
 
+/* Ports (Sec. IV: structures are driven by time-harmonic currents impressed on the edges of input
+ * ports; the edge voltages along a probe are summed; impedance parameters follow, and S parameters
+ * with a 50 Ohm source impedance).  A port (or probe) is a list of public edge indices
+ * 3*(i + nx*(j + ny*k)) + w, each with an orientation s_k = +1 or -1 relative to the port's
+ * reference direction.  Exciting a port with current I impresses the edge currents I s_k; its
+ * voltage is V = - sum_k s_k x[edge_k], counted against the current so that the power a source
+ * delivers, Re(V conj(I)) / 2, is >= 0 for a passive structure.  Z_ij = V_i / I_j with port j
+ * excited alone. */
+
+/* fit_port_rhs -- b_f = -j omega_f (I s) on the port's unmasked edges, zero elsewhere (Eq. e2), for
+ * f = 0 .. nfreq-1: the right-hand sides of one port excited at nfreq frequencies.
+ *   omega    HOST array of nfreq angular frequencies [rad/s]
+ *   nedge    edges in the port (>= 0); edges / signs: HOST arrays of nedge indices in [0, n_e) and
+ *            orientations (an edge listed twice adds up)
+ *   current  impressed current I [A]
+ *   b        DEVICE array of nfreq * n_e double2, overwritten
+ * Materials must be set (they fix the mask).  FIT_EINVAL on a null pointer or an edge out of range,
+ * checked before anything is written.  Synchronous on the stream. */
+fit_status fit_port_rhs(fit_grid* g, int nfreq, const double* omega, int nedge, const long long* edges,
+                        const double* signs, double current, void* b, void* stream);
+
+/* fit_probe_voltages -- V[f][q] = - sum over the edges of probe q of s_k x_f[edge_k], summed in FP64
+ * in a fixed order (the same bits on every run).
+ *   x        DEVICE array of nfreq * n_e double2 (solutions of fit_solve)
+ *   nprobe   >= 1 probes; off: HOST array of nprobe + 1 offsets (off[0] = 0, non-decreasing): the
+ *            edges of probe q are edges[off[q] .. off[q+1]-1], with orientations signs[...]
+ *   V        HOST array of nfreq * nprobe (re, im) double pairs, probe fastest
+ * FIT_EINVAL on bad offsets or an edge out of range.  Synchronous on the stream. */
+fit_status fit_probe_voltages(fit_grid* g, int nfreq, const void* x, int nprobe, const int* off,
+                              const long long* edges, const double* signs, double* V, void* stream);
+
+/* fit_z_to_s -- S = (Z - z0 1)(Z + z0 1)^{-1} for a P x P complex impedance matrix (Sec. IV, z0 = 50
+ * Ohm in the paper).  Z and S are HOST arrays of P * P (re, im) double pairs, row-major; S may not
+ * alias Z.  Host computation (Gauss-Jordan with partial pivoting), no device work.  FIT_EINVAL if
+ * z0 <= 0 or Z + z0 1 is singular. */
+fit_status fit_z_to_s(int P, const double* Z, double z0, double* S);
+
+/* fit_z_parameters -- the impedance matrices of nport ports at nfreq frequencies (Sec. IV: one
+ * right-hand side per excited port and frequency, all solved together).  Builds the nport * nfreq
+ * right-hand sides with fit_port_rhs (system j * nfreq + f: port j excited alone with current I at
+ * omega_f), solves them as one fit_solve batch, reads every port's voltage with fit_probe_voltages
+ * and returns Z[f][i][j] = V_i / I.
+ *   omega      HOST array of nfreq angular frequencies
+ *   nport, off, edges, signs   the ports, laid out as in fit_probe_voltages (each port is also the
+ *              probe that reads its own voltage)
+ *   current    I [A], finite and nonzero (Z does not depend on it up to the solver's tolerance)
+ *   tol, opts  passed to fit_solve (opts NULL = defaults; opts->stream carries all the work)
+ *   Z          HOST array of nfreq * nport * nport (re, im) double pairs: Z[f] is row-major P x P
+ *   report     HOST array of nport * nfreq reports in system order j * nfreq + f (may be NULL)
+ * Holds 2 * nport * nfreq * n_e double2 of device memory (right-hand sides and solutions) plus the
+ * Krylov workspace while it runs, all counted against the HBM budget and freed before return.
+ * Returns what fit_solve returns (Z is filled for FIT_NOT_CONVERGED / FIT_BREAKDOWN too), or an
+ * error; FIT_EINVAL on bad ports, checked before any device work. */
+fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int nport, const int* off,
+                            const long long* edges, const double* signs, double current, double tol,
+                            const fit_solve_opts* opts, double* Z, fit_solve_report* report);
+
 /* fit_grid_destroy -- free the handle and all its device memory (NULL is a no-op). */
 void fit_grid_destroy(fit_grid* g);
 

@@ -97,6 +97,15 @@ def lib():
                      "fit_unet_backward", "fit_unet_train_step", "fit_unet_pack", "fit_unet_pack_target",
                      "fit_unet_unpack", "fit_set_preconditioner"):
             getattr(L, name).restype = ct.c_int
+        pll = ct.POINTER(ct.c_longlong)
+        pi = ct.POINTER(ct.c_int)
+        L.fit_port_rhs.argtypes = [vp, i, pd, i, pll, pd, d, vp, vp]
+        L.fit_probe_voltages.argtypes = [vp, i, vp, i, pi, pll, pd, pd, vp]
+        L.fit_z_to_s.argtypes = [i, pd, d, pd]
+        L.fit_z_parameters.argtypes = [vp, i, pd, i, pi, pll, pd, d, d, ct.POINTER(fit_solve_opts),
+                                       pd, ct.POINTER(fit_solve_report)]
+        for name in ("fit_port_rhs", "fit_probe_voltages", "fit_z_to_s", "fit_z_parameters"):
+            getattr(L, name).restype = ct.c_int
         L.fit_last_error.argtypes = []
         L.fit_last_error.restype = ct.c_char_p
         for name in ("fit_grid_create", "fit_set_materials", "fit_set_material_matrices", "fit_apply", "fit_solve",
@@ -258,6 +267,87 @@ def fit_coef_scale(g):
 
 def _ptr(t):
     return ct.c_void_p(t.data_ptr())
+
+
+def _ports(ports):
+    """[(edges, signs), ...] -> (n, off int32, edges int64, signs float64) in the CSR layout of the ABI."""
+    off = np.zeros(len(ports) + 1, dtype=np.int32)
+    es, ss = [], []
+    for q, (e, sg) in enumerate(ports):
+        e = np.asarray(e, dtype=np.int64).ravel()
+        sg = np.asarray(sg, dtype=np.float64).ravel()
+        if e.shape != sg.shape:
+            raise ValueError(f"port {q}: {e.size} edges but {sg.size} signs")
+        off[q + 1] = off[q] + e.size
+        es.append(e)
+        ss.append(sg)
+    e = np.ascontiguousarray(np.concatenate(es) if es else np.zeros(0, np.int64))
+    sg = np.ascontiguousarray(np.concatenate(ss) if ss else np.zeros(0, np.float64))
+    return len(ports), off, e, sg
+
+
+def fit_port_rhs(g, omega, edges, signs, b, current=1.0, stream=None):
+    """b_f = -j omega_f (I s) on the port's unmasked edges (complex128 CUDA tensor of len(omega) x n_e)."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    e, pe = _dptr(np.asarray(edges, dtype=np.int64).ravel(), np.int64)
+    sg, ps = _dptr(np.asarray(signs, dtype=np.float64).ravel(), np.float64)
+    if e.size != sg.size:
+        raise ValueError(f"{e.size} edges but {sg.size} signs")
+    _check_vec(b, grid_info(g)["ne"], len(om), FIT_C128, "b")
+    _check(lib().fit_port_rhs(g, len(om), pom, e.size, pe, ps, float(current), _ptr(b), _stream_ptr(stream)),
+           "fit_port_rhs")
+
+
+def fit_probe_voltages(g, x, probes, stream=None):
+    """V[f, q] = - sum_k s_k x_f[edge_k] for probes [(edges, signs), ...]; x is a complex128 CUDA tensor of
+    nsys x n_e values.  Returns a complex128 numpy array of shape (nsys, nprobe)."""
+    ne = grid_info(g)["ne"]
+    if x.numel() % ne:
+        raise ValueError("x must hold whole vectors of n_e values")
+    nsys = x.numel() // ne
+    _check_vec(x, ne, nsys, FIT_C128, "x")
+    n, off, e, sg = _ports(probes)
+    V = np.zeros((nsys, n), dtype=np.complex128)
+    pv = V.view(np.float64).ctypes.data_as(ct.POINTER(ct.c_double))
+    _check(lib().fit_probe_voltages(g, nsys, _ptr(x), n, off.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                    e.ctypes.data_as(ct.POINTER(ct.c_longlong)),
+                                    sg.ctypes.data_as(ct.POINTER(ct.c_double)), pv, _stream_ptr(stream)),
+           "fit_probe_voltages")
+    return V
+
+
+def fit_z_to_s(Z, z0=50.0):
+    """S = (Z - z0 1)(Z + z0 1)^-1 for a P x P complex matrix (numpy in and out)."""
+    Zc = np.ascontiguousarray(Z, dtype=np.complex128)
+    if Zc.ndim != 2 or Zc.shape[0] != Zc.shape[1]:
+        raise ValueError("Z must be square")
+    S = np.zeros_like(Zc)
+    _check(lib().fit_z_to_s(Zc.shape[0], Zc.view(np.float64).ctypes.data_as(ct.POINTER(ct.c_double)), float(z0),
+                            S.view(np.float64).ctypes.data_as(ct.POINTER(ct.c_double))), "fit_z_to_s")
+    return S
+
+
+def fit_z_parameters(g, omega, ports, tol, current=1.0, opts=None, **kw):
+    """Impedance matrices of ``ports`` ([(edges, signs), ...]) at every frequency, all (port, frequency)
+    systems solved as one batch.  Returns (status, Z of shape (nfreq, P, P) complex128, reports in system
+    order port-major).  Keyword arguments override fields of the options struct."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    n, off, e, sg = _ports(ports)
+    o = opts if opts is not None else fit_solve_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    if o.stream is None:
+        o.stream = _stream_ptr(None).value
+    Z = np.zeros((len(om), n, n), dtype=np.complex128)
+    reps = (fit_solve_report * (n * len(om)))()
+    st = lib().fit_z_parameters(g, len(om), pom, n, off.ctypes.data_as(ct.POINTER(ct.c_int)),
+                                e.ctypes.data_as(ct.POINTER(ct.c_longlong)), sg.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                float(current), float(tol), ct.byref(o),
+                                Z.view(np.float64).ctypes.data_as(ct.POINTER(ct.c_double)), reps)
+    if st not in (FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN, FIT_ENAN):
+        _check(st, "fit_z_parameters")
+    return st, Z, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres,
+                        seconds=r.seconds, snapshots=r.snapshots) for r in reps]
 
 
 class UNet:

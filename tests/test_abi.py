@@ -59,3 +59,32 @@ def test_library_has_no_oracle_dependency():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(f).read()
             assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", src), f
+
+
+def test_port_entry_points_reject_bad_arguments(L):
+    from paper_1705_08849_gb300 import fit
+    assert L.fit_port_rhs(None, 1, None, 0, None, None, 1.0, None, None) == fit.FIT_EINVAL
+    assert L.fit_probe_voltages(None, 1, None, 1, None, None, None, None, None) == fit.FIT_EINVAL
+    assert L.fit_z_parameters(None, 1, None, 1, None, None, None, 1.0, 1e-8, None, None, None) == fit.FIT_EINVAL
+    z = (ct.c_double * 2)(1.0, 0.0)
+    s = (ct.c_double * 2)()
+    assert L.fit_z_to_s(1, z, 0.0, s) == fit.FIT_EINVAL  # z0 must be > 0
+    zs = (ct.c_double * 2)(-50.0, 0.0)  # Z + z0 1 = 0
+    assert L.fit_z_to_s(1, zs, 50.0, s) == fit.FIT_EINVAL
+    assert b"singular" in L.fit_last_error()
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8])
+def test_z_to_s_matches_the_oracle(L, P):
+    """fit_z_to_s is host code: the same S as the oracle's (Z - z0 1)(Z + z0 1)^-1 on random complex
+    impedances, including ones that need row pivoting (a zero leading entry of Z + z0 1)."""
+    import numpy as np
+    from oracle import ports as PT
+    from paper_1705_08849_gb300 import fit
+    rng = np.random.default_rng(100 + P)
+    Z = 80 * (rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P)))
+    if P > 1:
+        Z[0, 0] = -50.0  # Z + z0 1 has a zero pivot in its first column: rows must be exchanged
+    S = fit.fit_z_to_s(Z, 50.0)
+    want = PT.z_to_s(Z, 50.0)
+    assert np.allclose(S, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
