@@ -253,6 +253,50 @@ def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None):
     return out
 
 
+def port_columns(case, nport, seed=77, height=8, margin=16):
+    """nport seeded z-edge columns (ports from the ground wall z = 0 up ``height`` edges) at distinct
+    (i, j) positions at least ``margin`` cells from the side walls, orientation +z."""
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    rng = np.random.default_rng(seed)
+    picks = set()
+    while len(picks) < nport:
+        picks.add((int(rng.integers(margin, nx - margin)), int(rng.integers(margin, ny - margin))))
+    top = min(nz, height)
+    return [([3 * (i + nx * (j + ny * k)) + 2 for k in range(top)], [1.0] * top) for i, j in sorted(picks)]
+
+
+def time_ports(fit, torch, case, nport, nfreq, kind, max_iter, batch):
+    """Multi-port Z/S extraction: nport z-edge column ports, each excited alone with 1 A at nfreq of
+    the workload's frequencies, every system solved to 1e-8 (Jacobi preconditioner) inside one
+    fit_z_parameters call (right-hand sides, solves, probe sums and Z all on the device); wall time
+    of that call, then S = (Z - 50)(Z + 50)^-1 per frequency."""
+    fr = np.asarray(case["freqs"], dtype=np.float64)
+    sel = fr[np.unique(np.linspace(0, len(fr) - 1, max(1, min(nfreq, len(fr)))).round().astype(int))]
+    ws = 2 * np.pi * sel
+    mname, _, pname = kind.rpartition("-")
+    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname or "fgmres"]
+    prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
+    ports = port_columns(case, nport)
+    with fit.Grid.from_case(case) as g:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, Z, rep = fit.fit_z_parameters(g.h, ws, ports, 1e-8, method=method, precision=prec, restart=30,
+                                          precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter,
+                                          batch=batch)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    zmax = float(np.abs(Z).max())
+    recip = float(max(np.abs(Z[f] - Z[f].T).max() for f in range(len(ws))) / zmax) if zmax > 0 else 0.0
+    smax = float(max(np.linalg.norm(fit.fit_z_to_s(Z[f]), 2) for f in range(len(ws))))
+    nsys = len(ports) * len(ws)
+    return {"metric": "Z-parameter extraction s per (port, frequency) system to 1e-8", "unit": "s",
+            "value": dt / nsys, "systems": nsys, "ports": len(ports), "edges_per_port": len(ports[0][0]),
+            "frequencies_hz": sel.tolist(), "method": kind, "batch": batch, "s_total": dt,
+            "status": fit.status_str(st), "iterations": [r["iterations"] for r in rep],
+            "relres_max": float(max(r["relres"] for r in rep)), "reciprocity_rel": recip, "max_norm_S": smax,
+            "Z_ohm_first_freq": [[[float(z.real), float(z.imag)] for z in row] for row in Z[0]]}
+
+
 def time_unet(fit, torch, case, steps, warmup):
     """One application of the learned preconditioner's network (bf16 NDHWC input of 16 channels ->
     6 FP32 channels) on the workload's grid, CUDA-event timed after warm-up; flops from the layer
@@ -296,7 +340,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1, help="systems (frequencies) per apply in the apply mode")
     ap.add_argument("--nfreq", type=int, default=8, help="frequencies of the sweep mode")
     ap.add_argument("--band", default="", help="sweep mode: fmin,fmax in Hz (default: the workload's own frequencies)")
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet", "sweep"],
+    ap.add_argument("--ports", type=int, default=4, help="ports of the ports mode (z-edge columns)")
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet", "sweep", "ports"],
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
     ap.add_argument("--solve", default="mixed,cocg-mixed",
                     help="comma list of solves to time, each [method-]precision with method fgmres (default), "
@@ -336,6 +381,13 @@ def main():
             print(json.dumps({"metric": "wide-band sweep s to 1e-8", "unit": "s", "workload": args.workload,
                               "sweep": time_sweep(fit, torch, case, args.nfreq, kind, args.max_iter,
                                                   [float(v) for v in args.band.split(",")] if args.band else None)}),
+                  flush=True)
+        return
+    if args.mode == "ports":
+        if rank == 0:
+            kind = "cocg-mixed" if "cocg-mixed" in kinds else (kinds[0] if kinds else "cocg-mixed")
+            print(json.dumps({"workload": args.workload, **time_ports(fit, torch, case, args.ports, args.nfreq, kind,
+                                                                     args.max_iter, max(1, args.batch))}),
                   flush=True)
         return
     if args.mode == "unet":

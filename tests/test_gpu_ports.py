@@ -119,7 +119,7 @@ def test_z_parameters_three_port_lossy(method, precision):
     ws = 2 * np.pi * np.array([1e9, 3e9])
     with fit.Grid.from_case(case) as g:
         st, Z, rep = fit.fit_z_parameters(g.h, ws, ports, 1e-10, current=2.0, method=method, precision=precision,
-                                          max_iter=20000)
+                                          max_iter=20000, max_outer=1000)
     assert st == 0, rep
     assert len(rep) == 6 and all(r["status"] == 0 and r["relres"] <= 1e-10 for r in rep)
     for f, w in enumerate(ws):
