@@ -180,11 +180,34 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def parse_kind(fit, kind):
+    """"[method-]precision[+pc]": method fgmres (FGMRES(30), the default), cocg or bicgstab; precision
+    "mixed" (complex64 inner solve inside FP64 refinement) or "c128"; pc jacobi (the Eq. Precond
+    diagonal, the default), eps (M_eps^-1: the symmetrised form's change of variable, Eq. e2s) or none.
+    Returns (method, precision, precond, label)."""
+    base, _, pcname = kind.partition("+")
+    pcname = pcname or "jacobi"
+    mname, _, pname = base.rpartition("-")
+    mname = mname or "fgmres"
+    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname]
+    pc = {"jacobi": fit.FIT_PC_JACOBI, "eps": fit.FIT_PC_EPS, "none": fit.FIT_PC_NONE}[pcname]
+    prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
+    label = {"fgmres": "FGMRES(30)", "cocg": "COCG", "bicgstab": "BiCGStab"}[mname] + \
+        {"jacobi": "+Jacobi", "eps": "+M_eps^-1", "none": ""}[pcname]
+    return method, prec, pc, label
+
+
+def valid_kind(kind):
+    base, _, pcname = kind.partition("+")
+    mname, _, pname = base.rpartition("-")
+    return pname in ("mixed", "c128") and mname in ("", "fgmres", "cocg", "bicgstab") and \
+        pcname in ("", "jacobi", "eps", "none")
+
+
 def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
-    """Seconds per frequency to a 1e-8 true residual with the Jacobi (Eq. Precond diagonal)
-    preconditioner.  Each kind is "[method-]precision": method fgmres (FGMRES(30), the default), cocg
-    or bicgstab; precision "mixed" (complex64 inner solve inside FP64 refinement) or "c128".
-    Inputs are resident on the device; the timed region is the fit_solve call."""
+    """Seconds per frequency to a 1e-8 true residual, one system at the workload's first frequency,
+    for each kind of ``parse_kind``.  Inputs are resident on the device; the timed region is the
+    fit_solve call."""
     import fitgen as G
     w = 2 * np.pi * float(case["freqs"][0])
     j = torch.from_numpy(G.source_vector(case)).cuda()
@@ -192,16 +215,12 @@ def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
     with fit.Grid.from_case(case) as g:
         b = (-1j * w) * j  # b = -j w j (masked source edges carry no current in these workloads)
         for kind in kinds:
-            mname, _, pname = kind.rpartition("-")
-            mname = mname or "fgmres"
-            method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname]
-            label = {"fgmres": "FGMRES(30)+Jacobi", "cocg": "COCG+Jacobi", "bicgstab": "BiCGStab+Jacobi"}[mname]
+            method, prec, pc, label = parse_kind(fit, kind)
             x = torch.zeros_like(b)
-            prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, rep = g.solve([w], b, x, 1e-8, precision=prec, method=method, restart=30,
-                              precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter, use_graph=use_graph)
+                              precond=pc, max_iter=max_iter, max_outer=max_iter, use_graph=use_graph)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             out[kind] = {"s_per_freq": dt, "iterations": rep[0]["iterations"], "outer": rep[0]["outer"],
@@ -221,14 +240,11 @@ def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None):
         fr = np.asarray(case["freqs"], dtype=np.float64)
         sel = fr[np.unique(np.linspace(0, len(fr) - 1, max(1, min(nfreq, len(fr)))).round().astype(int))]
     ws = 2 * np.pi * sel
-    mname, _, pname = kind.rpartition("-")
-    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname or "fgmres"]
-    prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
+    method, prec, pc, _ = parse_kind(fit, kind)
     j = torch.from_numpy(G.source_vector(case)).cuda()
     ne = j.numel()
     b = torch.stack([(-1j * w) * j for w in ws]).reshape(-1)
-    opts = dict(precision=prec, method=method, restart=30, precond=fit.FIT_PC_JACOBI, max_iter=max_iter,
-                max_outer=max_iter)
+    opts = dict(precision=prec, method=method, restart=30, precond=pc, max_iter=max_iter, max_outer=max_iter)
     out = {"frequencies_hz": sel.tolist(), "method": kind}
     with fit.Grid.from_case(case) as g:
         x = torch.zeros_like(b)
@@ -273,16 +289,13 @@ def time_ports(fit, torch, case, nport, nfreq, kind, max_iter, batch):
     fr = np.asarray(case["freqs"], dtype=np.float64)
     sel = fr[np.unique(np.linspace(0, len(fr) - 1, max(1, min(nfreq, len(fr)))).round().astype(int))]
     ws = 2 * np.pi * sel
-    mname, _, pname = kind.rpartition("-")
-    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname or "fgmres"]
-    prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
+    method, prec, pc, _ = parse_kind(fit, kind)
     ports = port_columns(case, nport)
     with fit.Grid.from_case(case) as g:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, Z, rep = fit.fit_z_parameters(g.h, ws, ports, 1e-8, method=method, precision=prec, restart=30,
-                                          precond=fit.FIT_PC_JACOBI, max_iter=max_iter, max_outer=max_iter,
-                                          batch=batch)
+                                          precond=pc, max_iter=max_iter, max_outer=max_iter, batch=batch)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     zmax = float(np.abs(Z).max())
@@ -344,8 +357,9 @@ def main():
     ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet", "sweep", "ports"],
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
     ap.add_argument("--solve", default="mixed,cocg-mixed",
-                    help="comma list of solves to time, each [method-]precision with method fgmres (default), "
-                         "cocg or bicgstab and precision mixed or c128; none for no solve")
+                    help="comma list of solves to time, each [method-]precision[+pc] with method fgmres (default), "
+                         "cocg or bicgstab, precision mixed or c128, pc jacobi (default), eps or none; "
+                         "none for no solve")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
     ap.add_argument("--graph", type=int, default=1, help="1: the solve runs as one CUDA graph; 0: host-driven loop "
                     "(for per-kernel profiling)")
@@ -373,8 +387,7 @@ def main():
     fit.lib()
 
     case = _workload(args.workload)
-    kinds = [k for k in args.solve.split(",") if k.rpartition("-")[2] in ("mixed", "c128")
-             and k.rpartition("-")[0] in ("", "fgmres", "cocg", "bicgstab")]
+    kinds = [k for k in args.solve.split(",") if valid_kind(k)]
     if args.mode == "sweep":
         if rank == 0:
             kind = kinds[0] if kinds else "cocg-mixed"

@@ -94,6 +94,17 @@ fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const dou
 fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
                      fit_prec prec, void* stream);
 
+/* fit_apply_sym -- y'_b = A_s(omega_b) x'_b with the symmetrised operator of Eq. e2s (Sec. II,
+ * change of variable e' = M_eps^{1/2} e; Eq. e2tt writes the same operator as cal_A^T cal_A - w^2 I
+ * with cal_A = M_mu^{-1/2} C M_eps^{-1/2}):
+ *     A_s(w) = D C^T M_nu C D - w^2 I + j w M_kappa / M_eps,   D = M_eps^{-1/2},   = D A(w) D,
+ * on unmasked edges; masked rows return y' = x'.  A solution e' of A_s e' = D b gives e = D e'.
+ * Same arguments and conventions as fit_apply.  One generic (L1-cached, untiled) kernel pass: this
+ * is the operator for callers that work in the symmetrised variable; fit_solve reaches the same
+ * Krylov iterates with FIT_PC_EPS on the fused apply. */
+fit_status fit_apply_sym(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
+                         fit_prec prec, void* stream);
+
 /* fit_apply_noalloc -- the same operator apply as fit_apply, for callers that must not allocate
  * device memory (the paper has no counterpart).  fit_apply keeps the batch's frequencies in a buffer
  * owned by the handle and may cudaMalloc a larger one on a call with a larger batch; a host thread
@@ -121,7 +132,12 @@ fit_status fit_apply_noalloc(fit_grid* g, int nbatch, const double* omega, const
  *                 no stored basis; preconditioner none or Jacobi (diagonal, so A stays symmetric) */
 typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1, FIT_COCG = 2 } fit_method;
 typedef enum { FIT_SOLVE_C128 = 0, FIT_SOLVE_MIXED = 1 } fit_solve_precision;
-typedef enum { FIT_PC_NONE = 0, FIT_PC_JACOBI = 1, FIT_PC_UNET = 2 } fit_pc_kind;
+/* FIT_PC_EPS: the diagonal (w^2 M_eps)^-1 (1 on masked edges), a constant multiple of M_eps^-1.  It is the
+ * change of variable e' = M_eps^{1/2} e of the symmetrised form (Eq. e2s): COCG with FIT_PC_EPS takes
+ * exactly the iterates of COCG on M_eps^{-1/2} A M_eps^{-1/2} e' = M_eps^{-1/2} b, mapped back by
+ * e = M_eps^{-1/2} e' (the constant w^2 changes no iterate; it keeps the complex64 inner vectors of order
+ * one).  With BiCGStab and FGMRES it is a right preconditioner like Jacobi. */
+typedef enum { FIT_PC_NONE = 0, FIT_PC_JACOBI = 1, FIT_PC_UNET = 2, FIT_PC_EPS = 3 } fit_pc_kind;
 
 typedef struct fit_solve_opts {
   int method;        /* fit_method: BiCGStab, FGMRES(restart) or COCG (Sec. IV, Fig. Iterative) */
@@ -134,8 +150,8 @@ typedef struct fit_solve_opts {
   double inner_tol;  /* relative tolerance of each inner complex64 solve; default 1e-4 */
   int batch;         /* systems solved together in one batched launch; 0 = all nfreq */
   int use_graph;     /* nonzero: run the Krylov loop as one CUDA graph with a device-side loop */
-  int precond;       /* fit_pc_kind applied as the right preconditioner (BiCGStab and COCG: none or
-                        Jacobi; the learned one needs FGMRES with FIT_SOLVE_MIXED) */
+  int precond;       /* fit_pc_kind applied as the right preconditioner (BiCGStab and COCG: none,
+                        Jacobi or eps; the learned one needs FGMRES with FIT_SOLVE_MIXED) */
   void* stream;      /* cudaStream_t (as void*) for all work; NULL = legacy default stream */
   void* history;     /* optional DEVICE buffer of history_len * nfreq * n_e double2: the iterate x
                         after every history_every-th outer step, slot h of system f at

@@ -366,6 +366,21 @@ fit_status fit_grid_info(const fit_grid* g, long long* out6) {
   return FIT_OK;
 }
 
+// the batch's frequencies into the handle's device buffer (grown on demand, counted in the budget)
+static fit_status stage_omega(fit_grid* g, int nbatch, const double* omega, cudaStream_t s) {
+  if (nbatch > g->omega_cap) {
+    if (g->omega_dev) fit_dev_free(g, g->omega_dev, g->omega_cap * sizeof(double));
+    g->omega_dev = nullptr;
+    g->omega_cap = 0;
+    int cap = std::max(nbatch, 64);
+    fit_status st = fit_dev_alloc(g, (void**)&g->omega_dev, cap * sizeof(double));
+    if (st != FIT_OK) return st;
+    g->omega_cap = cap;
+  }
+  FIT_CHECK_CUDA(cudaMemcpyAsync(g->omega_dev, omega, nbatch * sizeof(double), cudaMemcpyHostToDevice, s));
+  return FIT_OK;
+}
+
 fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x, void* y, fit_prec prec,
                      void* stream) {
   FIT_REQUIRE(g && omega && x && y, "fit_apply: null argument");
@@ -380,18 +395,29 @@ fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x
   FIT_REQUIRE(xb + vbytes <= yb || yb + vbytes <= xb, "fit_apply: x and y overlap");
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (nbatch > g->omega_cap) {
-    if (g->omega_dev) fit_dev_free(g, g->omega_dev, g->omega_cap * sizeof(double));
-    g->omega_dev = nullptr;
-    g->omega_cap = 0;
-    int cap = std::max(nbatch, 64);
-    fit_status st = fit_dev_alloc(g, (void**)&g->omega_dev, cap * sizeof(double));
-    if (st != FIT_OK) return st;
-    g->omega_cap = cap;
-  }
-  FIT_CHECK_CUDA(cudaMemcpyAsync(g->omega_dev, omega, nbatch * sizeof(double), cudaMemcpyHostToDevice, s));
+  fit_status st = stage_omega(g, nbatch, omega, s);
+  if (st != FIT_OK) return st;
   double out_scale = prec == FIT_C64 ? 1.0 / g->coef_scale : 1.0;
   return fit_launch_apply(g, nbatch, g->omega_dev, x, y, prec, out_scale, s);
+}
+
+fit_status fit_apply_sym(fit_grid* g, int nbatch, const double* omega, const void* x, void* y, fit_prec prec,
+                         void* stream) {
+  FIT_REQUIRE(g && omega && x && y, "fit_apply_sym: null argument");
+  FIT_REQUIRE(nbatch >= 1, "fit_apply_sym: nbatch must be >= 1");
+  FIT_REQUIRE(prec == FIT_C64 || prec == FIT_C128, "fit_apply_sym: unknown precision");
+  FIT_REQUIRE(g->has_materials, "fit_apply_sym: materials not set");
+  for (int b = 0; b < nbatch; ++b) FIT_REQUIRE(isfinite(omega[b]), "fit_apply_sym: omega must be finite");
+  size_t esz = prec == FIT_C64 ? sizeof(float2) : sizeof(double2);
+  size_t vbytes = (size_t)g->ne * esz * nbatch;
+  const char* xb = (const char*)x;
+  const char* yb = (const char*)y;
+  FIT_REQUIRE(xb + vbytes <= yb || yb + vbytes <= xb, "fit_apply_sym: x and y overlap");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  fit_status st = stage_omega(g, nbatch, omega, s);
+  if (st != FIT_OK) return st;
+  return fit_launch_apply_sym(g, nbatch, g->omega_dev, x, y, prec, s);
 }
 
 }  // extern "C"

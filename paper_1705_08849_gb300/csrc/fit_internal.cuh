@@ -100,6 +100,9 @@ struct fit_epi {
 // device array of nbatch angular frequencies.  x/y are float2 (FIT_C64) or double2 (FIT_C128).
 fit_status fit_launch_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
                             fit_prec prec, double out_scale, cudaStream_t stream, fit_epi* epi = nullptr);
+// the symmetrised operator of Eq. e2s (generic kernel), omega already on the device
+fit_status fit_launch_apply_sym(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                                fit_prec prec, cudaStream_t s);
 // Time the apply variants for (nbatch, prec) on the given buffers and cache the fastest; no-op if
 // already tuned.  Must not be called while the stream is being captured.
 fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, fit_prec prec,

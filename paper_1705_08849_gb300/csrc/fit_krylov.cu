@@ -426,12 +426,17 @@ __global__ void __launch_bounds__(256) k_bicg_s(typename cplx<T>::t* r, const ty
   }
 }
 
-// D^-1 of the Jacobi preconditioner per system: diag(A_in(w_b)) = nusum - w^2 M_eps + j w M_kappa
-// (the Eq. Precond column-sum construction on the unsymmetrised operator); masked edges: 1
+// D^-1 of the diagonal preconditioner per system; masked edges: 1.  Jacobi: diag(A_in(w_b)) =
+// nusum - w^2 M_eps + j w M_kappa (the Eq. Precond column-sum construction on the unsymmetrised
+// operator).  eps_only: w^2 M_eps, the change of variable e' = M_eps^{1/2} e of the symmetrised form
+// (Eq. e2s) applied as a split diagonal preconditioner (nusum is not read).  The constant factor w^2
+// leaves the Krylov iterates unchanged and makes the preconditioned operator K / (w^2 M_eps) - 1 of
+// order one: with M_eps^-1 alone the complex64 vectors reach ~1e20 and their products overflow FP32.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dinv(const T* __restrict__ nusum, const T* __restrict__ ek,
                                               const uint8_t* __restrict__ mask, const double* __restrict__ omega,
-                                              int nx, int ny, int nxp, typename cplx<T>::t* dinv, P p) {
+                                              int nx, int ny, int nxp, typename cplx<T>::t* dinv, P p,
+                                              int eps_only) {
   using V = typename cplx<T>::t;
   const int b = blockIdx.y;
   const double w = omega[b];
@@ -444,6 +449,10 @@ __global__ void __launch_bounds__(256) k_dinv(const T* __restrict__ nusum, const
     V o;
     if ((mask[cp] >> q) & 1) {
       o.x = T(1);
+      o.y = T(0);
+    } else if (eps_only) {
+      const double me = (double)ek[6 * cp + q], wme = w * w * me;
+      o.x = (T)(1.0 / (wme > 0.0 ? wme : me));  // w = 0: M_eps^-1 itself
       o.y = T(0);
     } else {
       double dr = (double)nusum[e] - w * w * (double)ek[6 * cp + q];
@@ -1108,6 +1117,7 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   else if (method == FIT_COCG) bytes += 4 * vec;
   else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
   if (pc == FIT_PC_JACOBI || pc == FIT_PC_UNET) bytes += ne * esz / 2 + vec;
+  else if (pc == FIT_PC_EPS) bytes += vec;
   size_t napply = (size_t)std::max(fit_apply_partials(g, FIT_C64), fit_apply_partials(g, FIT_C128));
   bytes += (size_t)B * napply * 4 * 8;
   bytes += (size_t)B * 1216 * 2 * FG_MAXV * 8;
@@ -1156,6 +1166,8 @@ fit_status setup(Work& w, int B) {
   }
   if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {  // the learned preconditioner adds to Jacobi
     ALLOC(w.nusum, ne * w.esz / 2);
+    ALLOC(w.dinv, vec);
+  } else if (w.pc == FIT_PC_EPS) {
     ALLOC(w.dinv, vec);
   }
   if (w.pc == FIT_PC_UNET) {
@@ -1359,7 +1371,7 @@ struct Seq {
     const char* vj = (const char*)w.Vb + (size_t)j * vecb;
     char* wj1 = (char*)w.Vb + (size_t)(j + 1) * vecb;
     const void* zin = vj;
-    if (w.pc == FIT_PC_JACOBI) {
+    if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_EPS) {
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
@@ -1459,11 +1471,11 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
   q.hist = hist;
   q.hist_len = hist_len;
   q.hist_every = hist_every;
-  if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {  // D^-1 per system, once per solve
+  if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET || w.pc == FIT_PC_EPS) {  // D^-1 per system, once per solve
     const fit_grid* g = w.g;
     k_dinv<T><<<dim3(w.p.nblk, w.p.B), 256, 0, s>>>((const T*)w.nusum, w.mixed ? (const T*)g->ek32 : (const T*)g->ek64,
                                                      g->mask, w.omega, g->nx, g->ny, g->nxp,
-                                                     (typename cplx<T>::t*)w.dinv, w.p);
+                                                     (typename cplx<T>::t*)w.dinv, w.p, w.pc == FIT_PC_EPS);
     FIT_CHECK_CUDA(cudaGetLastError());
   }
   // pick the apply kernels (autotuner) now: timing cannot run inside a stream capture
@@ -1737,7 +1749,8 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
   FIT_REQUIRE(o.precision == FIT_SOLVE_C128 || o.precision == FIT_SOLVE_MIXED, "fit_solve: unknown precision");
   FIT_REQUIRE(o.method != FIT_FGMRES || (o.restart >= 1 && o.restart <= FG_MAXV - 1),
               "fit_solve: FGMRES restart must be in 1..64");
-  FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET,
+  FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET ||
+                  o.precond == FIT_PC_EPS,
               "fit_solve: unknown preconditioner");
   FIT_REQUIRE(o.precond != FIT_PC_UNET || g->unet != nullptr,
               "fit_solve: FIT_PC_UNET needs a network attached with fit_set_preconditioner");

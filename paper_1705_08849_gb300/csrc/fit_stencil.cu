@@ -14,6 +14,11 @@
 // This file holds the generic kernel: one thread per cell, operands read straight from global
 // memory (through L1), any grid size and batch.  It is the reference launch for the fused
 // shared-memory kernels in fit_fused.cu and the fallback for shapes they do not take.
+//
+// With SYM it applies the symmetrised operator of Eq. e2s instead (D = M_eps^{-1/2} per edge):
+//     y' = D C^T M_nu C (D x') - w^2 x' + j w (M_kappa / M_eps) x'   on unmasked edges, y' = x' on masked,
+// i.e. D A(w) D x' with the unsymmetrised A above.  D is formed from M_eps as it is read, so a common
+// scale of the coefficients cancels and no output scale applies.
 #include "fit_internal.cuh"
 
 template <typename T>
@@ -31,7 +36,7 @@ struct ApplyArgs {
   T out_scale;
 };
 
-template <typename T>
+template <typename T, bool SYM = false>
 struct GenericView {
   using V = typename cplx<T>::t;
   const ApplyArgs<T>& a;
@@ -44,7 +49,13 @@ struct GenericView {
     if (!inside(i, j, k)) return czero<V>();
     long long cp = i + (long long)a.nxp * (j + (long long)a.ny * k);
     if ((a.mask[cp] >> w) & 1) return czero<V>();
-    return x[3 * (i + (long long)a.nx * (j + (long long)a.ny * k)) + w];
+    V v = x[3 * (i + (long long)a.nx * (j + (long long)a.ny * k)) + w];
+    if constexpr (SYM) {
+      const T d = T(1) / sqrt(a.ek[6 * cp + w]);  // D = M_eps^{-1/2}
+      v.x *= d;
+      v.y *= d;
+    }
+    return v;
   }
   __device__ T nu(int i, int j, int k, int w) const {
     if (!inside(i, j, k)) return T(0);
@@ -62,7 +73,7 @@ struct GenericView {
   }
 };
 
-template <typename T, int EPI>
+template <typename T, int EPI, bool SYM = false>
 __global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a, fit_epi epi) {
   using V = typename cplx<T>::t;
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -76,7 +87,7 @@ __global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a, fit_
     V* y = a.y + (long long)b * a.ne;
     T acc[3] = {T(0), T(0), T(0)};
     if (valid) {
-      GenericView<T> g{a, x};
+      GenericView<T, SYM> g{a, x};
       V hx = g.hx(i, j, k), hy = g.hy(i, j, k), hz = g.hz(i, j, k);
       V cx = g.hy(i, j, k - 1) - hy + hz - g.hz(i, j - 1, k);
       V cy = g.hz(i - 1, j, k) - hz + hx - g.hx(i, j, k - 1);
@@ -93,6 +104,12 @@ __global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a, fit_
         V out;
         if ((m >> q) & 1) {
           out = xv;
+        } else if constexpr (SYM) {
+          const T eps = a.ek[6 * cp + q];
+          const T d = T(1) / sqrt(eps);
+          const T ai = w * (a.ek[6 * cp + 3 + q] / eps);  // w M_kappa / M_eps
+          out.x = d * curl[q].x - w2 * xv.x - ai * xv.y;
+          out.y = d * curl[q].y - w2 * xv.y + ai * xv.x;
         } else {
           T ar = -w2 * a.ek[6 * cp + q];    // -w^2 M_eps
           T ai = w * a.ek[6 * cp + 3 + q];  // w M_kappa
@@ -154,6 +171,38 @@ static fit_status launch_generic(fit_grid* g, int nbatch, const double* omega_de
   }
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
+}
+
+template <typename T>
+static fit_status launch_sym(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
+                             const T* ek, cudaStream_t s) {
+  ApplyArgs<T> a;
+  a.x = (const typename cplx<T>::t*)x;
+  a.y = (typename cplx<T>::t*)y;
+  a.nu = nu;
+  a.ek = ek;
+  a.mask = g->mask;
+  a.omega = omega_dev;
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nz = g->nz;
+  a.nxp = g->nxp;
+  a.ne = g->ne;
+  a.nbatch = nbatch;
+  a.out_scale = T(1);
+  fit_epi e;
+  dim3 block(32, 8, 1);
+  long long gz = (long long)g->nz * nbatch;
+  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (unsigned)(gz < 65535 ? gz : 65535));
+  apply_generic_kernel<T, FIT_EPI_NONE, true><<<grid, block, 0, s>>>(a, e);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_launch_apply_sym(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
+                                fit_prec prec, cudaStream_t s) {
+  if (prec == FIT_C64) return launch_sym<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, s);
+  return launch_sym<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, s);
 }
 
 long long fit_apply_partials_generic(const fit_grid* g) {

@@ -19,7 +19,7 @@ FIT_C64, FIT_C128 = 0, 1
 FIT_BC_PEC_ALL = 0x3F
 FIT_BICGSTAB, FIT_FGMRES, FIT_COCG = 0, 1, 2
 FIT_SOLVE_C128, FIT_SOLVE_MIXED = 0, 1
-FIT_PC_NONE, FIT_PC_JACOBI, FIT_PC_UNET = 0, 1, 2
+FIT_PC_NONE, FIT_PC_JACOBI, FIT_PC_UNET, FIT_PC_EPS = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfitgb300.so")
@@ -59,6 +59,8 @@ def lib():
         L.fit_set_materials.argtypes = [vp, pf, pf, pf, pu8]
         L.fit_set_material_matrices.argtypes = [vp, pd, pd, pd, pu8]
         L.fit_apply.argtypes = [vp, i, pd, vp, vp, i, vp]
+        L.fit_apply_sym.argtypes = [vp, i, pd, vp, vp, i, vp]
+        L.fit_apply_sym.restype = ct.c_int
         L.fit_solve.argtypes = [vp, i, pd, vp, vp, d, ct.POINTER(fit_solve_opts), ct.POINTER(fit_solve_report)]
         L.fit_solve_opts_default.argtypes = [ct.POINTER(fit_solve_opts)]
         L.fit_solve_opts_default.restype = None
@@ -197,6 +199,15 @@ def fit_apply(g, omega, x, y, prec=FIT_C64, stream=None):
     _check_vec(y, ne, len(om), prec, "y")
     _check(lib().fit_apply(g, len(om), pom, ct.c_void_p(x.data_ptr()), ct.c_void_p(y.data_ptr()), prec,
                            _stream_ptr(stream)), "fit_apply")
+
+
+def fit_apply_sym(g, omega, x, y, prec=FIT_C64, stream=None):
+    """y'_b = A_s(omega_b) x'_b, the symmetrised operator M_eps^-1/2 A M_eps^-1/2 of Eq. e2s."""
+    om, pom = _dptr(np.atleast_1d(np.asarray(omega, dtype=np.float64)), np.float64)
+    ne = grid_info(g)["ne"]
+    _check_vec(x, ne, len(om), prec, "x")
+    _check_vec(y, ne, len(om), prec, "y")
+    _check(lib().fit_apply_sym(g, len(om), pom, _ptr(x), _ptr(y), prec, _stream_ptr(stream)), "fit_apply_sym")
 
 
 def fit_apply_noalloc(g, omega, x, y, prec=FIT_C64, stream=None):
