@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE (see ``oracle/__init__.py``).  complex128 throughout.  The Krylov methods
 follow the short-listed solvers of Sec. IV (bcgs and the gmres family, Fig. Iterative) as
 textbook algorithms: BiCGStab (van der Vorst 1992), restarted (F)GMRES (Saad 1993) with
-modified Gram-Schmidt and Givens rotations, and COCG (the paper's "cg" on a complex symmetric A).  Conventions (readings): conjugated inner products
+modified Gram-Schmidt and Givens rotations, and COCG and COCR (the paper's "cg" and "cr" on a
+complex symmetric A).  Conventions (readings): conjugated inner products
 <u, v> = u^H v, x0 = 0, shadow residual r^ = r0, stop on the true relative residual
 ||b - A x|| / ||b|| (Sec. IV fixes only "a relative decrease of the residual norm").
 """
@@ -62,6 +63,49 @@ def cocg(A, b, tol=1e-10, maxiter=10000, dinv=None):
         z = m(r)
         rho_new = r @ z
         p = z + (rho_new / rho) * p
+        rho = rho_new
+    return x, maxiter, relres(A, x, b), 1
+
+
+def cocr(A, b, tol=1e-10, maxiter=10000, dinv=None):
+    """Conjugate orthogonal conjugate residual (Sogabe and Zhang 2007) for complex symmetric A = A^T:
+    the conjugate-residual recurrences with the unconjugated bilinear form (u, v) = u^T v, the
+    reading of the "cr" solver of Sec. IV.  ``dinv`` (optional) is the diagonal of a symmetric
+    preconditioner M = diag(dinv); the recurrences are those of COCR on M^{1/2} A M^{1/2} written in
+    the original variables.  Start: z = M r, w = A z, p = z, q = w, rho = (z, w).  Per step:
+        alpha = rho / (q, M q),  x += alpha p,  r -= alpha q,  z = M r,  w = A z,
+        rho' = (z, w),  beta = rho' / rho,  p = z + beta p,  q = w + beta q   (q = A p throughout).
+    Returns (x, iterations, true relative residual, status), status 0 = converged, 1 = iteration
+    cap, 2 = breakdown (|(q, M q)| or |rho| < 1e-300)."""
+    b = np.asarray(b, dtype=np.complex128)
+    nb = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if nb == 0:
+        return x, 0, 0.0, 0
+    m = (lambda v: v) if dinv is None else (lambda v: dinv * v)
+    r = b.copy()
+    z = m(r)
+    w = A @ z
+    p = z.copy()
+    q = w.copy()
+    rho = z @ w  # unconjugated
+    for it in range(1, maxiter + 1):
+        sig = q @ m(q)
+        if abs(sig) < 1e-300 or abs(rho) < 1e-300:
+            return x, it, relres(A, x, b), 2
+        alpha = rho / sig
+        x = x + alpha * p
+        r = r - alpha * q
+        if np.linalg.norm(r) <= tol * nb:
+            rr = relres(A, x, b)
+            if rr <= tol:
+                return x, it, rr, 0
+        z = m(r)
+        w = A @ z
+        rho_new = z @ w
+        beta = rho_new / rho
+        p = z + beta * p
+        q = w + beta * q
         rho = rho_new
     return x, maxiter, relres(A, x, b), 1
 

@@ -107,3 +107,56 @@ def test_cocg_on_complex_symmetric_4cubed(precond):
         rho2 = np.vdot(r, r)
         p, rho = r + (rho2 / rho) * p, rho2
     assert K.relres(A, xr, b) > 1e-6
+
+
+def test_cocr_is_minimal_residual_on_real_spd():
+    """On a real SPD matrix COCR is the conjugate residual method, which minimises ||b - A x||_2 over
+    the Krylov space: its k-th iterate must equal GMRES(k)'s (a different algorithm, Arnoldi +
+    least squares) at every k, its residual norms must not increase, and with 6 distinct eigenvalues
+    it terminates within 6 steps up to rounding."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(4)
+    lam = np.array([0.5, 1.0, 2.0, 3.5, 7.0, 11.0])
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    A = sp.csr_matrix(Q @ np.diag(np.repeat(lam, 10)) @ Q.T)
+    b = rng.standard_normal(60) + 0j
+    prev = np.inf
+    for k in range(1, 6):
+        xc, _, _, _ = K.cocr(A, b, tol=0.0, maxiter=k)
+        xg, _, _, _ = K.fgmres(A, b, tol=0.0, restart=k, maxiter=k)
+        assert np.allclose(xc, xg, rtol=0, atol=1e-10 * np.linalg.norm(xg)), k
+        rk = np.linalg.norm(b - A @ xc)
+        assert rk <= prev * (1 + 1e-12)
+        prev = rk
+    x, it, rr, st = K.cocr(A, b, tol=1e-12, maxiter=100)
+    assert st == 0 and it <= 7, (it, rr)
+    assert np.allclose(x, np.linalg.solve(A.toarray(), b), rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_cocr_on_complex_symmetric_4cubed(precond):
+    """COCR, with or without the Jacobi diagonal, reaches the dense solution of the lossy 4^3 system."""
+    c = G.small_random(4, 4, 4, seed=5, lossy=True)
+    A, mask = _system(c, 2e9)
+    b = G.random_vector(A.shape[0], seed=6) * (1 - mask)
+    x_dense = K.dense_solve(A, b)
+    dinv = 1.0 / A.diagonal() if precond else None
+    x, it, rr, st = K.cocr(A, b, tol=1e-12, maxiter=5000, dinv=dinv)
+    assert st == 0 and rr <= 1e-12
+    cond = np.linalg.cond(A.toarray())
+    assert np.linalg.norm(x - x_dense) <= 10 * cond * 1e-12 * np.linalg.norm(x_dense)
+
+
+def test_preconditioned_cocr_is_cocr_on_the_scaled_system():
+    """COCR with a diagonal M takes the iterates of plain COCR on M^{1/2} A M^{1/2} (x = M^{1/2} x^)."""
+    c = G.small_random(5, 4, 4, seed=9, lossy=True, pec_frac=0.1)
+    A, mask = _system(c, 1.5e9)
+    b = G.random_vector(A.shape[0], seed=2) * (1 - mask)
+    dinv = np.abs(1.0 / A.diagonal())  # a positive diagonal, so that M^{1/2} is real
+    s = np.sqrt(dinv)
+    import scipy.sparse as sp
+    As = (sp.diags(s) @ A @ sp.diags(s)).tocsr()
+    for k in (2, 5, 10):
+        xh, _, _, _ = K.cocr(As, s * b, tol=0.0, maxiter=k)
+        x, _, _, _ = K.cocr(A, b, tol=0.0, maxiter=k, dinv=dinv)
+        assert np.allclose(s * xh, x, rtol=0, atol=1e-10 * np.abs(x).max()), k
