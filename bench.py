@@ -181,7 +181,7 @@ def run_reference(args, rank):
 
 
 def parse_kind(fit, kind):
-    """"[method-]precision[+pc]": method fgmres (FGMRES(30), the default), cocg or bicgstab; precision
+    """"[method-]precision[+pc]": method fgmres (FGMRES(30), the default), cocg, cocr or bicgstab; precision
     "mixed" (complex64 inner solve inside FP64 refinement) or "c128"; pc jacobi (the Eq. Precond
     diagonal, the default), eps (M_eps^-1: the symmetrised form's change of variable, Eq. e2s) or none.
     Returns (method, precision, precond, label)."""
@@ -189,10 +189,10 @@ def parse_kind(fit, kind):
     pcname = pcname or "jacobi"
     mname, _, pname = base.rpartition("-")
     mname = mname or "fgmres"
-    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "bicgstab": fit.FIT_BICGSTAB}[mname]
+    method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "cocr": fit.FIT_COCR, "bicgstab": fit.FIT_BICGSTAB}[mname]
     pc = {"jacobi": fit.FIT_PC_JACOBI, "eps": fit.FIT_PC_EPS, "none": fit.FIT_PC_NONE}[pcname]
     prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
-    label = {"fgmres": "FGMRES(30)", "cocg": "COCG", "bicgstab": "BiCGStab"}[mname] + \
+    label = {"fgmres": "FGMRES(30)", "cocg": "COCG", "cocr": "COCR", "bicgstab": "BiCGStab"}[mname] + \
         {"jacobi": "+Jacobi", "eps": "+M_eps^-1", "none": ""}[pcname]
     return method, prec, pc, label
 
@@ -200,7 +200,7 @@ def parse_kind(fit, kind):
 def valid_kind(kind):
     base, _, pcname = kind.partition("+")
     mname, _, pname = base.rpartition("-")
-    return pname in ("mixed", "c128") and mname in ("", "fgmres", "cocg", "bicgstab") and \
+    return pname in ("mixed", "c128") and mname in ("", "fgmres", "cocg", "cocr", "bicgstab") and \
         pcname in ("", "jacobi", "eps", "none")
 
 
@@ -358,7 +358,7 @@ def main():
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
     ap.add_argument("--solve", default="mixed,cocg-mixed",
                     help="comma list of solves to time, each [method-]precision[+pc] with method fgmres (default), "
-                         "cocg or bicgstab, precision mixed or c128, pc jacobi (default), eps or none; "
+                         "cocg, cocr or bicgstab, precision mixed or c128, pc jacobi (default), eps or none; "
                          "none for no solve")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
     ap.add_argument("--graph", type=int, default=1, help="1: the solve runs as one CUDA graph; 0: host-driven loop "

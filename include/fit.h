@@ -124,13 +124,16 @@ fit_status fit_apply_noalloc(fit_grid* g, int nbatch, const double* omega, const
                              fit_prec prec, void* stream);
 
 /* Krylov methods (Sec. IV lists the PETSc solvers tried; bcgs and the gmres family are kept, and
- * "cg" on this complex symmetric system (A^T = A, Eq. e2) is read as CG with the unconjugated
- * bilinear form, i.e. COCG):
+ * "cg" and "cr" on this complex symmetric system (A^T = A, Eq. e2) are read as CG and CR with the
+ * unconjugated bilinear form, i.e. COCG and COCR):
  *   FIT_BICGSTAB  BiCGStab, r^ = r0, conjugated inner products
  *   FIT_FGMRES    restarted flexible GMRES(restart), CGS2 orthogonalisation, Givens least squares
  *   FIT_COCG      conjugate orthogonal CG: one apply and three fused vector passes per iteration,
- *                 no stored basis; preconditioner none or Jacobi (diagonal, so A stays symmetric) */
-typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1, FIT_COCG = 2 } fit_method;
+ *                 no stored basis; preconditioner none, Jacobi or eps (diagonal, so A stays symmetric)
+ *   FIT_COCR      conjugate orthogonal conjugate residual: one apply and three fused vector passes per
+ *                 iteration over six vectors; the same preconditioners.  Its residual recurrence is
+ *                 fragile in complex64: prefer FIT_SOLVE_C128 */
+typedef enum { FIT_BICGSTAB = 0, FIT_FGMRES = 1, FIT_COCG = 2, FIT_COCR = 3 } fit_method;
 typedef enum { FIT_SOLVE_C128 = 0, FIT_SOLVE_MIXED = 1 } fit_solve_precision;
 /* FIT_PC_EPS: the diagonal (w^2 M_eps)^-1 (1 on masked edges), a constant multiple of M_eps^-1.  It is the
  * change of variable e' = M_eps^{1/2} e of the symmetrised form (Eq. e2s): COCG with FIT_PC_EPS takes

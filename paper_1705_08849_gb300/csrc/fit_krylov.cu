@@ -277,6 +277,64 @@ struct OpCocgRho {  // q0,q1 = (r, D^-1 r), q2 = ||r||^2
   }
 };
 
+// ---- COCR operations ---------------------------------------------------------------------------
+// Conjugate orthogonal conjugate residual for the complex symmetric A: the conjugate-residual
+// recurrences with the unconjugated bilinear form and a symmetric diagonal preconditioner M = D^-1
+// (COCR on M^{1/2} A M^{1/2}, written in the original variables).  The start sets z = M r~, p = q = 0;
+// every iteration then runs
+//   w = A z;  rho' = (z, w);  beta = rho' / rho (0 on the first);  p = z + beta p;  q = w + beta q;
+//   alpha = rho' / (q, M q);  d += alpha p;  r -= alpha q;  z = M r
+// so that q = A p throughout and each iteration costs one apply.
+struct OpCocrStart {  // q2 = ||r~||^2
+  __device__ bool active(const Sys&) const { return true; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int b) const {
+    const double qq[3] = {q[2], 0.0, 0.0};
+    OpInnerStart{}.apply(s, qq, p, b);
+    s.beta = make_double2(0.0, 0.0);
+  }
+};
+
+struct OpCocrBeta {  // q0,q1 = (z, A z)
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    const double2 rn = make_double2(q[0], q[1]);
+    if (!cfinite(rn)) { s.inner_status = SYS_NAN; return; }
+    if (sqrt(cabs2(rn)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
+    s.beta = s.inner_it == 0 ? make_double2(0.0, 0.0) : cdiv(rn, s.rho);
+    s.rho = rn;
+  }
+};
+
+struct OpCocrAlpha {  // q0,q1 = (q, M q)
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    const double2 sig = make_double2(q[0], q[1]);
+    if (!cfinite(sig)) { s.inner_status = SYS_NAN; return; }
+    if (sqrt(cabs2(sig)) < p.tiny) { s.inner_status = SYS_BREAK; return; }
+    s.alpha = cdiv(s.rho, sig);
+  }
+};
+
+struct OpCocrRes {  // q2 = ||r||^2 after the update
+  __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
+  __device__ void apply(Sys& s, const double* q, const P& p, int) const {
+    const double rr = q[2];
+    s.inner_it += 1;
+    s.rin2 = rr;
+    if (!isfinite(rr)) { s.inner_status = SYS_NAN; return; }
+    if (rr <= s.inner_tol2) { s.inner_status = SYS_CONV; return; }
+    if (s.inner_it >= s.max_inner) { s.inner_status = SYS_MAXIT; return; }
+    if (rr < s.rin_min2) { s.rin_min2 = rr; s.rin_min_it = s.inner_it; }
+    if (s.inner_it - s.rin_min_it > p.stall || rr > 1e8 * s.rin_min2) {  // as for COCG
+      s.inner_status = SYS_MAXIT;
+      if (rr > s.rin0) {
+        s.corr = 0.0;
+        s.replay = s.rin_min_it;
+      }
+    }
+  }
+};
+
 // ---- BiCGStab operations -----------------------------------------------------------------------
 struct OpAlpha {  // q0,q1 = <r^, v>
   __device__ bool active(const Sys& s) const { return s.inner_status == SYS_RUN; }
@@ -715,6 +773,104 @@ __global__ void __launch_bounds__(256) k_cocg_p(const typename cplx<T>::t* __res
   }
 }
 
+// COCR start: r~ = r / ||r|| (vector precision), z = D^-1 r~, p = q = d = 0; partials ||r~||^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocr_start(const double2* __restrict__ r128, const Sys* __restrict__ sys,
+                                                    typename cplx<T>::t* rin, typename cplx<T>::t* z,
+                                                    typename cplx<T>::t* pv, typename cplx<T>::t* q,
+                                                    typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ dinv,
+                                                    double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  if (sys[b].outer_status == SYS_RUN) {
+    const long long off = (long long)b * p.ne;
+    const double sc = 1.0 / sys[b].rscale;
+    VEC_LOOP(p) {
+      const double2 r = r128[off + e];
+      const V rz = mkc<T>(r.x * sc, r.y * sc);
+      rin[off + e] = rz;
+      z[off + e] = dinv ? cmulv(dinv[off + e], rz) : rz;
+      pv[off + e] = czero<V>();
+      q[off + e] = czero<V>();
+      d[off + e] = czero<V>();
+      acc[2] += rz.x * rz.x + rz.y * rz.y;
+    }
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// COCR: partials of (z, w) with w = A z (unconjugated)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocr_rho(const typename cplx<T>::t* __restrict__ z,
+                                                  const typename cplx<T>::t* __restrict__ wv, const Sys* __restrict__ sys,
+                                                  double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    const V a = z[off + e], c = wv[off + e];
+    acc[0] += a.x * c.x - a.y * c.y;
+    acc[1] += a.x * c.y + a.y * c.x;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// COCR: p = z + beta p, q = w + beta q; partials (q, D^-1 q) (unconjugated)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocr_pq(const typename cplx<T>::t* __restrict__ z,
+                                                 const typename cplx<T>::t* __restrict__ wv, typename cplx<T>::t* pv,
+                                                 typename cplx<T>::t* q, const typename cplx<T>::t* __restrict__ dinv,
+                                                 const Sys* __restrict__ sys, double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const T br = (T)sys[b].beta.x, bi = (T)sys[b].beta.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    const V zz = z[off + e], ww = wv[off + e];
+    V pp = pv[off + e], qq = q[off + e];
+    pp = V{zz.x + br * pp.x - bi * pp.y, zz.y + br * pp.y + bi * pp.x};
+    qq = V{ww.x + br * qq.x - bi * qq.y, ww.y + br * qq.y + bi * qq.x};
+    pv[off + e] = pp;
+    q[off + e] = qq;
+    const V mq = dinv ? cmulv(dinv[off + e], qq) : qq;
+    acc[0] += qq.x * mq.x - qq.y * mq.y;
+    acc[1] += qq.x * mq.y + qq.y * mq.x;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
+// COCR: d += alpha p, r -= alpha q, z = D^-1 r; partials ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_cocr_xr(typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ pv,
+                                                 typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ q,
+                                                 typename cplx<T>::t* z, const typename cplx<T>::t* __restrict__ dinv,
+                                                 const Sys* __restrict__ sys, double* part, P p) {
+  using V = typename cplx<T>::t;
+  const int b = blockIdx.y;
+  if (sys[b].inner_status != SYS_RUN) return;
+  const long long off = (long long)b * p.ne;
+  const T ar = (T)sys[b].alpha.x, ai = (T)sys[b].alpha.y;
+  T acc[3] = {T(0), T(0), T(0)};
+  VEC_LOOP(p) {
+    const V pp = pv[off + e], qq = q[off + e];
+    V dd = d[off + e], rr = r[off + e];
+    dd.x += ar * pp.x - ai * pp.y;
+    dd.y += ar * pp.y + ai * pp.x;
+    rr.x -= ar * qq.x - ai * qq.y;
+    rr.y -= ar * qq.y + ai * qq.x;
+    d[off + e] = dd;
+    r[off + e] = rr;
+    z[off + e] = dinv ? cmulv(dinv[off + e], rr) : rr;
+    acc[2] += rr.x * rr.x + rr.y * rr.y;
+  }
+  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+}
+
 // the step length of this refinement step is applied: no later step may apply it again (the loop
 // keeps running while any system of the batch is active)
 __global__ void k_clear_mr(Sys* sys, int B) {
@@ -1115,6 +1271,7 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   size_t bytes = ne * B * 32;  // r128 and r_prev
   if (method == FIT_BICGSTAB) bytes += 6 * vec + (pc != FIT_PC_NONE ? 2 * vec : 0);
   else if (method == FIT_COCG) bytes += 4 * vec;
+  else if (method == FIT_COCR) bytes += 6 * vec;
   else bytes += (size_t)(m + 1) * vec + (pc != FIT_PC_NONE ? (size_t)m * vec : 0) + 2 * vec;
   if (pc == FIT_PC_JACOBI || pc == FIT_PC_UNET) bytes += ne * esz / 2 + vec;
   else if (pc == FIT_PC_EPS) bytes += vec;
@@ -1152,6 +1309,13 @@ fit_status setup(Work& w, int B) {
   } else if (w.method == FIT_COCG) {
     ALLOC(w.rin, vec);
     ALLOC(w.pv, vec);
+    ALLOC(w.v, vec);
+    ALLOC(w.d, vec);
+  } else if (w.method == FIT_COCR) {  // r, z (in t), p, q (in rhat), w = A z (in v), the correction d
+    ALLOC(w.rin, vec);
+    ALLOC(w.t, vec);
+    ALLOC(w.pv, vec);
+    ALLOC(w.rhat, vec);
     ALLOC(w.v, vec);
     ALLOC(w.d, vec);
   } else {
@@ -1207,7 +1371,7 @@ fit_status setup(Work& w, int B) {
   // iterations without a new smallest inner residual before the inner solve hands back: COCG's
   // residual norm is not monotone (A is complex symmetric, not Hermitian) and can wander above its
   // minimum for thousands of iterations before it falls again, so it gets a far longer window
-  w.p.stall = w.method == FIT_COCG ? 20000 : 1000;
+  w.p.stall = (w.method == FIT_COCG || w.method == FIT_COCR) ? 20000 : 1000;
   w.p.precond = w.pc;
   if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {
     long long nc = g->ncell;
@@ -1277,6 +1441,13 @@ struct Seq {
       fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocgStart{});
       return;
     }
+    if (w.method == FIT_COCR) {
+      k_cocr_start<T><<<vgrid(), 256, 0, s>>>(w.r128, w.sys, (V*)w.rin, (V*)w.t, (V*)w.pv, (V*)w.rhat, (V*)w.d,
+                                              (const V*)w.dinv, w.part_vec, w.p);
+      check();
+      fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocrStart{});
+      return;
+    }
     bool bicg = w.method == FIT_BICGSTAB;
     if (bicg)
       k_inner_start<T, true><<<vgrid(), 256, 0, s>>>(w.r128, w.sys, (V*)w.rin, (V*)w.rhat, (V*)w.pv, (V*)w.v,
@@ -1308,10 +1479,29 @@ struct Seq {
     check();
   }
 
-  // one iteration of the single-vector methods (BiCGStab or COCG)
+  // one COCR iteration (predicated on inner status): w = A z, beta, p and q, alpha, the x/r/z update
+  template <typename T>
+  void cocr_iter(const int* st_inner) {
+    using V = typename cplx<T>::t;
+    apply(w.t, w.v, FIT_EPI_NONE, nullptr, w.inner, st_inner);
+    k_cocr_rho<T><<<vgrid(), 256, 0, s>>>((const V*)w.t, (const V*)w.v, w.sys, w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocrBeta{});
+    k_cocr_pq<T><<<vgrid(), 256, 0, s>>>((const V*)w.t, (const V*)w.v, (V*)w.pv, (V*)w.rhat, (const V*)w.dinv,
+                                         w.sys, w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocrAlpha{});
+    k_cocr_xr<T><<<vgrid(), 256, 0, s>>>((V*)w.d, (const V*)w.pv, (V*)w.rin, (const V*)w.rhat, (V*)w.t,
+                                         (const V*)w.dinv, w.sys, w.part_vec, w.p);
+    check();
+    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocrRes{});
+  }
+
+  // one iteration of the single-vector methods (BiCGStab, COCG or COCR)
   template <typename T>
   void loop_iter(const int* st_inner) {
     if (w.method == FIT_COCG) cocg_iter<T>(st_inner);
+    else if (w.method == FIT_COCR) cocr_iter<T>(st_inner);
     else bicg_iter<T>(st_inner);
   }
 
@@ -1490,7 +1680,7 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
   auto mirror = [&](cudaStream_t ss) {
     k_mirror_status<<<(w.p.B + 127) / 128, 128, 0, ss>>>(w.sys, st_inner, st_outer, w.p.B);
   };
-  const bool bicg = w.method == FIT_BICGSTAB || w.method == FIT_COCG;  // single-vector loop methods
+  const bool bicg = w.method == FIT_BICGSTAB || w.method == FIT_COCG || w.method == FIT_COCR;  // single-vector loops
 
   // FIT_TRACE_SOLVE=1 prints the scalars of system 0 after every host-loop step (stderr)
   const char* tr = getenv("FIT_TRACE_SOLVE");
@@ -1744,7 +1934,7 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
   fit_solve_opts o;
   fit_solve_opts_default(&o);
   if (opts) o = *opts;
-  FIT_REQUIRE(o.method == FIT_BICGSTAB || o.method == FIT_FGMRES || o.method == FIT_COCG,
+  FIT_REQUIRE(o.method == FIT_BICGSTAB || o.method == FIT_FGMRES || o.method == FIT_COCG || o.method == FIT_COCR,
               "fit_solve: unknown method");
   FIT_REQUIRE(o.precision == FIT_SOLVE_C128 || o.precision == FIT_SOLVE_MIXED, "fit_solve: unknown precision");
   FIT_REQUIRE(o.method != FIT_FGMRES || (o.restart >= 1 && o.restart <= FG_MAXV - 1),

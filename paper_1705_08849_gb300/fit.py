@@ -17,7 +17,7 @@ FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN = 0, 1, 2
 FIT_EINVAL, FIT_ENOMEM, FIT_ECUDA, FIT_ETIMEOUT, FIT_EBUDGET, FIT_ENAN = -1, -2, -3, -4, -5, -6
 FIT_C64, FIT_C128 = 0, 1
 FIT_BC_PEC_ALL = 0x3F
-FIT_BICGSTAB, FIT_FGMRES, FIT_COCG = 0, 1, 2
+FIT_BICGSTAB, FIT_FGMRES, FIT_COCG, FIT_COCR = 0, 1, 2, 3
 FIT_SOLVE_C128, FIT_SOLVE_MIXED = 0, 1
 FIT_PC_NONE, FIT_PC_JACOBI, FIT_PC_UNET, FIT_PC_EPS = 0, 1, 2, 3
 

@@ -35,7 +35,7 @@ def _oracle_relres(case, w, x, b):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("method", [0, 1, 2, 3])
 def test_cavity16_solve(precision, method):
     """The cavity workload: 16^3 PEC vacuum cube, 5 GHz, centre z-edge source, tol 1e-10."""
     from oracle import krylov as K
@@ -50,7 +50,7 @@ def test_cavity16_solve(precision, method):
 
 
 @pytest.mark.parametrize("use_graph", [0, 1])
-@pytest.mark.parametrize("method,precond", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
+@pytest.mark.parametrize("method,precond", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)])
 def test_small_lossy_batch(method, precond, use_graph):
     case = G.small_random(20, 18, 11, seed=31, pec_frac=0.05)
     n = 3 * 20 * 18 * 11
@@ -93,7 +93,7 @@ def test_every_fused_variant_in_a_solve(monkeypatch):
                 assert rr <= 1e-9, (k, len(fs), i, rr, rep[i])
 
 
-@pytest.mark.parametrize("method", [0, 2])
+@pytest.mark.parametrize("method", [0, 2, 3])
 def test_graph_and_host_loop_agree_exactly(monkeypatch, method):
     """The device-side loop (graph) and the host-driven loop run the same kernels in the same order.
     Each solve uses its own grid handle, whose autotuner could pick a different apply variant (a
@@ -106,6 +106,30 @@ def test_graph_and_host_loop_agree_exactly(monkeypatch, method):
     b = _solve(case, [3e9], 1e-8, rhs=rhs, use_graph=1, method=method)
     assert a[1][0]["iterations"] == b[1][0]["iterations"]
     assert np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_cocr_c128_iterations_match_oracle(precond):
+    """Complex128 COCR (the "cr" reading) against the oracle's COCR on the same system: the same
+    recurrences and stop test, so the iteration counts agree up to rounding; the solution passes the
+    oracle's residual."""
+    from oracle import fit as F
+    from oracle import krylov as K
+    case = G.small_random(12, 10, 8, seed=44, pec_frac=0.05)
+    w = 2 * np.pi * 3e9
+    A, mask = oracle_A(case, w)
+    me, mk, mn, _ = F.material_diagonals(case["dx"], case["dy"], case["dz"], case["eps_r"], case["sigma"],
+                                         case["inv_mu_r"], case["pec"])
+    b = F.rhs_from_current(w, G.random_vector(A.shape[0], 7), mask)
+    dinv = 1.0 / F.jacobi_diagonal(w, 12, 10, 8, me, mk, mn, mask) if precond else None
+    _, it_o, _, st_o = K.cocr(A, b, tol=1e-9, maxiter=20000, dinv=dinv)
+    assert st_o == 0
+    st, rep, xs, bs, ws = _solve(case, [3e9], 1e-9, rhs=b[None], method=3, precision=0, precond=precond,
+                                 max_iter=20000)
+    assert st == 0, rep
+    rr, _ = _oracle_relres(case, ws[0], xs[0], bs[0])
+    assert rr <= 1e-9, rr
+    assert abs(rep[0]["iterations"] - it_o) <= max(5, 0.1 * it_o), (rep[0]["iterations"], it_o)
 
 
 def test_layered128_mixed_fgmres_jacobi():
