@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import fitgen as G
-from tests._gpu_util import fitlib, oracle_A, torch_cuda
+from tests._gpu_util import fitlib, oracle_A, oracle_matrices, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -162,3 +162,40 @@ def test_z_parameters_rejects_bad_ports():
             fit.fit_z_parameters(g.h, [1e9], [([ne], [1.0])], 1e-8)
         with pytest.raises(fit.FitError):
             fit.fit_z_parameters(g.h, [1e9], ports, 1e-8, current=0.0)
+
+
+def test_port_rhs_and_probes_full_size():
+    """layered128 at full size: four 8-edge z-column ports at two frequencies.  b is checked on every port
+    edge and on sampled other edges; probe sums of a random device vector against the oracle's."""
+    from oracle import ports as PT
+    torch = torch_cuda()
+    fit = fitlib()
+    case = G.layered_blocks()
+    nx, ny, nz = 128, 128, 128
+    ne = 3 * nx * ny * nz
+    _, _, _, mask = oracle_matrices(case)
+    ports = [_zcol(case, i, j, 0, 8) for i, j in ((20, 90), (76, 68), (92, 39), (99, 48))]
+    ws = 2 * np.pi * np.array([1e9, 3e9])
+    rng = np.random.default_rng(8)
+    others = rng.choice(ne, 500, replace=False)
+    with fit.Grid.from_case(case) as g:
+        b = torch.empty(len(ws) * ne, dtype=torch.complex128, device="cuda")
+        for e, s in ports:
+            fit.fit_port_rhs(g.h, ws, e, s, b, current=1.0)
+            torch.cuda.synchronize()
+            idx = np.unique(np.concatenate([np.asarray(e), others]))
+            for f, w in enumerate(ws):
+                got = b[f * ne + torch.from_numpy(idx).cuda()].cpu().numpy()
+                want = PT.port_rhs(w, ne, e, s, mask)[idx]
+                assert np.allclose(got, want, rtol=1e-15, atol=0)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        x = torch.randn(2 * ne, dtype=torch.complex128, device="cuda", generator=gen)
+        V = fit.fit_probe_voltages(g.h, x, ports)
+        for f in range(2):
+            for q, (e, s) in enumerate(ports):
+                xe = x[f * ne + torch.tensor(e, device="cuda")].cpu().numpy()
+                xf = np.zeros(ne, np.complex128)
+                xf[e] = xe
+                want = PT.probe_voltage(xf, e, s)
+                assert abs(V[f, q] - want) <= 1e-14 * np.sum(np.abs(xe))

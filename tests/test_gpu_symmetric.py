@@ -117,3 +117,41 @@ def test_cocg_eps_iterations_match_oracle():
                           precond=fit.FIT_PC_EPS, max_iter=20000)
     assert st == 0, rep
     assert abs(rep[0]["iterations"] - it_o) <= max(5, 0.1 * it_o), (rep[0]["iterations"], it_o)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("workload", ["layered128", "stripline96"])
+def test_apply_sym_sampled_full_size(prec, workload):
+    """The full-size workloads: the GPU applies A_s to the whole vector; the oracle forms sampled rows of
+    D A D one by one (rows of A from the definition of C, scaled by D = M_eps^-1/2; masked rows are the
+    identity)."""
+    from oracle import fit as F
+    from oracle import symmetric as S
+    torch = torch_cuda()
+    fit = fitlib()
+    case = G.layered_blocks() if workload == "layered128" else G.stripline()
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    ne = 3 * nx * ny * nz
+    w = 2 * np.pi * float(case["freqs"][0])
+    dt = torch.complex64 if prec == 0 else torch.complex128
+    with fit.Grid.from_case(case) as g:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        x = torch.randn(ne, dtype=dt, device="cuda", generator=gen)
+        y = torch.empty_like(x)
+        fit.fit_apply_sym(g.h, [w], x, y, prec)
+        torch.cuda.synchronize()
+        me, mk, mn, mask = oracle_matrices(case)
+        d = S.eps_scaling(me, mask)
+        rng = np.random.default_rng(5)
+        rows = np.unique(np.concatenate([rng.choice(ne, 200, replace=False), np.arange(12), np.arange(ne - 12, ne)]))
+        R = F.system_rows(w, nx, ny, nz, rows, me, mk, mn, mask).tocoo()
+        vals = R.data * d[rows[R.row]] * d[R.col]
+        vals = np.where(mask[rows[R.row]] != 0, R.data, vals)  # identity rows stay 1
+        cols = np.unique(R.col)
+        xs = np.zeros(ne, np.complex128)
+        xs[cols] = x[torch.from_numpy(cols).cuda()].cpu().numpy().astype(np.complex128)
+        want = np.zeros(len(rows), np.complex128)
+        np.add.at(want, R.row, vals * xs[R.col])
+        got = y[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.complex128)
+    assert relerr(got, want) <= (1e-5 if prec == 0 else 1e-12), relerr(got, want)
