@@ -71,7 +71,8 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
  *   eps_r, sigma, inv_mu_r   host float arrays of nx*ny*nz cells, index i + nx*(j + ny*k):
  *                            relative permittivity (> 0), conductivity [S/m] (>= 0), 1/mu_r (> 0)
  *   pec_cell                 host uint8 array of nx*ny*nz (nonzero = PEC cell) or NULL
- * Synchronous.  FIT_EINVAL on null pointers. */
+ * Synchronous.  FIT_EINVAL on null pointers or a value outside its range (checked on the host before
+ * anything is copied). */
 fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma,
                              const float* inv_mu_r, const unsigned char* pec_cell);
 
@@ -79,7 +80,8 @@ fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma
  *   m_eps, m_kappa   host double arrays of n_e edge values (interleaved ordering)
  *   m_nu             host double array of n_e facet values (facet w of cell c at 3*c + w)
  *   edge_mask        host uint8 array of n_e (nonzero = masked edge) or NULL (no mask)
- * Replaces whatever fit_set_materials built.  Synchronous. */
+ * Replaces whatever fit_set_materials built.  Synchronous.  fit_apply_sym and FIT_PC_EPS additionally
+ * need m_eps finite and > 0 on every unmasked edge; they return FIT_EINVAL otherwise. */
 fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const double* m_kappa,
                                      const double* m_nu, const unsigned char* edge_mask);
 

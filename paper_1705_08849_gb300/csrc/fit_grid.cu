@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -285,8 +286,14 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
 fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma, const float* inv_mu_r,
                              const unsigned char* pec_cell) {
   FIT_REQUIRE(g && eps_r && sigma && inv_mu_r, "fit_set_materials: null argument");
-  FIT_CHECK_CUDA(cudaSetDevice(g->device));
   size_t n = (size_t)g->ncell;
+  for (size_t c = 0; c < n; ++c) {
+    FIT_REQUIRE(std::isfinite(eps_r[c]) && eps_r[c] > 0.0f, "fit_set_materials: eps_r must be finite and > 0");
+    FIT_REQUIRE(std::isfinite(sigma[c]) && sigma[c] >= 0.0f, "fit_set_materials: sigma must be finite and >= 0");
+    FIT_REQUIRE(std::isfinite(inv_mu_r[c]) && inv_mu_r[c] > 0.0f, "fit_set_materials: inv_mu_r must be finite and > 0");
+  }
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  g->eps_positive = true;  // positive cell permittivities and widths give a positive M_eps on every edge
   float *d_eps = nullptr, *d_sig = nullptr, *d_imu = nullptr;
   uint8_t* d_pec = nullptr;
   FIT_CHECK_CUDA(cudaMalloc(&d_eps, n * sizeof(float)));
@@ -320,6 +327,10 @@ fit_status fit_set_material_matrices(fit_grid* g, const double* m_eps, const dou
                                      const unsigned char* edge_mask) {
   FIT_REQUIRE(g && m_eps && m_kappa && m_nu, "fit_set_material_matrices: null argument");
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  bool eps_pos = true;
+  for (long long e = 0; e < g->ne; ++e)
+    if (!(edge_mask && edge_mask[e]) && !(std::isfinite(m_eps[e]) && m_eps[e] > 0.0)) eps_pos = false;
+  g->eps_positive = eps_pos;
   size_t np = (size_t)g->ncellp;
   std::vector<double> nu(np * 3, 0.0), ek(np * 6, 0.0);
   std::vector<uint8_t> mk(np, 0);
@@ -407,6 +418,7 @@ fit_status fit_apply_sym(fit_grid* g, int nbatch, const double* omega, const voi
   FIT_REQUIRE(nbatch >= 1, "fit_apply_sym: nbatch must be >= 1");
   FIT_REQUIRE(prec == FIT_C64 || prec == FIT_C128, "fit_apply_sym: unknown precision");
   FIT_REQUIRE(g->has_materials, "fit_apply_sym: materials not set");
+  FIT_REQUIRE(g->eps_positive, "fit_apply_sym: M_eps must be finite and > 0 on every unmasked edge");
   for (int b = 0; b < nbatch; ++b) FIT_REQUIRE(isfinite(omega[b]), "fit_apply_sym: omega must be finite");
   size_t esz = prec == FIT_C64 ? sizeof(float2) : sizeof(double2);
   size_t vbytes = (size_t)g->ne * esz * nbatch;

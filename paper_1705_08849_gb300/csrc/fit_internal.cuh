@@ -36,6 +36,7 @@ struct fit_grid {
   uint8_t* mask = nullptr; // [ncellp] bit w set = w-edge of the cell is masked (PEC/wall)
   double coef_scale = 1.0; // c64 coefficients are coef_scale * SI values (1 / max M_nu)
   bool has_materials = false;
+  bool eps_positive = false;  // M_eps > 0 and finite on every unmasked edge (the symmetrised form divides by it)
   double* omega_dev = nullptr;  // per-batch angular frequencies for fit_apply
   int omega_cap = 0;
   size_t bytes_held = 0;

@@ -1939,6 +1939,8 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
   FIT_REQUIRE(o.precision == FIT_SOLVE_C128 || o.precision == FIT_SOLVE_MIXED, "fit_solve: unknown precision");
   FIT_REQUIRE(o.method != FIT_FGMRES || (o.restart >= 1 && o.restart <= FG_MAXV - 1),
               "fit_solve: FGMRES restart must be in 1..64");
+  FIT_REQUIRE(o.precond != FIT_PC_EPS || g->eps_positive,
+              "fit_solve: FIT_PC_EPS needs M_eps finite and > 0 on every unmasked edge");
   FIT_REQUIRE(o.precond == FIT_PC_NONE || o.precond == FIT_PC_JACOBI || o.precond == FIT_PC_UNET ||
                   o.precond == FIT_PC_EPS,
               "fit_solve: unknown preconditioner");

@@ -155,3 +155,34 @@ def test_apply_sym_sampled_full_size(prec, workload):
         np.add.at(want, R.row, vals * xs[R.col])
         got = y[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.complex128)
     assert relerr(got, want) <= (1e-5 if prec == 0 else 1e-12), relerr(got, want)
+
+
+def test_material_ranges_are_checked_on_the_host():
+    """Out-of-range materials are refused before any device work: a non-positive eps_r in
+    fit_set_materials, and a zero M_eps on an unmasked edge for the symmetrised form (whose D divides
+    by it) after fit_set_material_matrices; the unsymmetrised apply still accepts those matrices."""
+    torch = torch_cuda()
+    fit = fitlib()
+    case = G.small_random(6, 5, 4, seed=3)
+    with fit.Grid(6, 5, 4, case["dx"], case["dy"], case["dz"]) as g:
+        bad = case["eps_r"].copy()
+        bad[1, 2, 3] = 0.0
+        with pytest.raises(fit.FitError):
+            fit.fit_set_materials(g.h, bad, case["sigma"], case["inv_mu_r"], case["pec"])
+        neg = case["sigma"].copy()
+        neg[0, 0, 0] = -1.0
+        with pytest.raises(fit.FitError):
+            fit.fit_set_materials(g.h, case["eps_r"], neg, case["inv_mu_r"], case["pec"])
+        me, mk, mn, mask = oracle_matrices(case)
+        free = np.flatnonzero(mask == 0)
+        me = me.copy()
+        me[free[7]] = 0.0
+        fit.fit_set_material_matrices(g.h, me, mk, mn, mask)
+        ne = 3 * 6 * 5 * 4
+        x = torch.zeros(ne, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        fit.fit_apply(g.h, [1e9], x, y, fit.FIT_C128)
+        with pytest.raises(fit.FitError):
+            fit.fit_apply_sym(g.h, [1e9], x, y, fit.FIT_C128)
+        with pytest.raises(fit.FitError):
+            g.solve([1e9], x, y, 1e-8, precond=fit.FIT_PC_EPS)
