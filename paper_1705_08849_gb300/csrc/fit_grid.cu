@@ -293,33 +293,27 @@ fit_status fit_set_materials(fit_grid* g, const float* eps_r, const float* sigma
     FIT_REQUIRE(std::isfinite(inv_mu_r[c]) && inv_mu_r[c] > 0.0f, "fit_set_materials: inv_mu_r must be finite and > 0");
   }
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
-  g->eps_positive = true;  // positive cell permittivities and widths give a positive M_eps on every edge
-  float *d_eps = nullptr, *d_sig = nullptr, *d_imu = nullptr;
-  uint8_t* d_pec = nullptr;
-  FIT_CHECK_CUDA(cudaMalloc(&d_eps, n * sizeof(float)));
-  FIT_CHECK_CUDA(cudaMalloc(&d_sig, n * sizeof(float)));
-  FIT_CHECK_CUDA(cudaMalloc(&d_imu, n * sizeof(float)));
-  if (pec_cell) FIT_CHECK_CUDA(cudaMalloc(&d_pec, n));
-  cudaMemcpy(d_eps, eps_r, n * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(d_sig, sigma, n * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(d_imu, inv_mu_r, n * sizeof(float), cudaMemcpyHostToDevice);
-  if (pec_cell) cudaMemcpy(d_pec, pec_cell, n, cudaMemcpyHostToDevice);
+  FitDevTmp tmp(g);  // the per-cell inputs live only for this call
+  void *d_eps = nullptr, *d_sig = nullptr, *d_imu = nullptr, *d_pec = nullptr;
+  fit_status st;
+  if ((st = tmp.copy(&d_eps, eps_r, n * sizeof(float), nullptr)) != FIT_OK) return st;
+  if ((st = tmp.copy(&d_sig, sigma, n * sizeof(float), nullptr)) != FIT_OK) return st;
+  if ((st = tmp.copy(&d_imu, inv_mu_r, n * sizeof(float), nullptr)) != FIT_OK) return st;
+  if (pec_cell && (st = tmp.copy(&d_pec, pec_cell, n, nullptr)) != FIT_OK) return st;
   int threads = 256;
   long long blocks = ((long long)n + threads - 1) / threads;
-  assemble_kernel<<<(unsigned)blocks, threads>>>(g->dx, g->dy, g->dz, d_eps, d_sig, d_imu, d_pec, g->nx, g->ny,
-                                                 g->nz, g->nxp, g->nu64, g->ek64, g->mask);
-  mat16_kernel<<<(unsigned)blocks, threads>>>(d_eps, d_sig, d_imu, g->dx, g->dy, g->dz, g->nx, g->ny, g->nz,
+  const float *pe = (const float*)d_eps, *ps = (const float*)d_sig, *pm = (const float*)d_imu;
+  assemble_kernel<<<(unsigned)blocks, threads>>>(g->dx, g->dy, g->dz, pe, ps, pm, (const uint8_t*)d_pec, g->nx,
+                                                 g->ny, g->nz, g->nxp, g->nu64, g->ek64, g->mask);
+  mat16_kernel<<<(unsigned)blocks, threads>>>(pe, ps, pm, g->dx, g->dy, g->dz, g->nx, g->ny, g->nz,
                                               (__nv_bfloat16*)g->mat16);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(d_eps);
-  cudaFree(d_sig);
-  cudaFree(d_imu);
-  if (d_pec) cudaFree(d_pec);
   if (e != cudaSuccess) {
     fit_set_error(std::string("fit_set_materials: ") + cudaGetErrorString(e));
     return FIT_ECUDA;
   }
+  g->eps_positive = true;  // positive cell permittivities and widths give a positive M_eps on every edge
   return finish_coefficients(g);
 }
 

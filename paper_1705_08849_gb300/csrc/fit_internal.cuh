@@ -6,6 +6,8 @@
 
 #include <map>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/fit.h"
 
@@ -80,6 +82,31 @@ const char* fit_get_error();
 // Device allocation accounted against the handle's budget.
 fit_status fit_dev_alloc(fit_grid* g, void** p, size_t bytes);
 void fit_dev_free(fit_grid* g, void* p, size_t bytes);
+
+// Transient device buffers of one call, counted against the handle's budget and freed when the
+// object goes out of scope (on every return path).
+struct FitDevTmp {
+  fit_grid* g;
+  std::vector<std::pair<void*, size_t>> held;
+  explicit FitDevTmp(fit_grid* gg) : g(gg) {}
+  FitDevTmp(const FitDevTmp&) = delete;
+  FitDevTmp& operator=(const FitDevTmp&) = delete;
+  ~FitDevTmp() {
+    for (auto& h : held) fit_dev_free(g, h.first, h.second);
+  }
+  fit_status alloc(void** dst, size_t bytes) {
+    fit_status st = fit_dev_alloc(g, dst, bytes);
+    if (st == FIT_OK && *dst) held.push_back({*dst, bytes});
+    return st;
+  }
+  // allocate and copy a host array in (stream-ordered on s)
+  fit_status copy(void** dst, const void* src, size_t bytes, cudaStream_t s) {
+    fit_status st = alloc(dst, bytes);
+    if (st != FIT_OK) return st;
+    if (bytes) FIT_CHECK_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return FIT_OK;
+  }
+};
 
 // Fused epilogues of the operator apply (all per system b of the batch; sums are written as
 // per-block partials part[(b*nblk + block)*4 + q], reduced later in a fixed order):

@@ -57,23 +57,6 @@ __global__ void __launch_bounds__(256) k_probe(const double2* __restrict__ x, lo
   if (threadIdx.x == 0) V[(long long)f * nprobe + q] = make_double2(red[0][0], red[1][0]);
 }
 
-// transient device copies of small host arrays, freed on scope exit
-struct DevTmp {
-  fit_grid* g;
-  std::vector<std::pair<void*, size_t>> held;
-  explicit DevTmp(fit_grid* gg) : g(gg) {}
-  ~DevTmp() {
-    for (auto& h : held) fit_dev_free(g, h.first, h.second);
-  }
-  fit_status copy(void** dst, const void* src, size_t bytes, cudaStream_t s) {
-    fit_status st = fit_dev_alloc(g, dst, bytes);
-    if (st != FIT_OK) return st;
-    held.push_back({*dst, bytes});
-    if (bytes) FIT_CHECK_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s));
-    return FIT_OK;
-  }
-};
-
 }  // namespace
 
 extern "C" {
@@ -87,7 +70,7 @@ fit_status fit_port_rhs(fit_grid* g, int nfreq, const double* omega, int nedge, 
   cudaStream_t s = (cudaStream_t)stream;
   FIT_CHECK_CUDA(cudaMemsetAsync(b, 0, (size_t)nfreq * g->ne * sizeof(double2), s));
   if (nedge == 0) return FIT_OK;
-  DevTmp tmp(g);
+  FitDevTmp tmp(g);
   void *d_om, *d_e, *d_s;
   fit_status st;
   if ((st = tmp.copy(&d_om, omega, nfreq * sizeof(double), s)) != FIT_OK) return st;
@@ -113,14 +96,13 @@ fit_status fit_probe_voltages(fit_grid* g, int nfreq, const void* x, int nprobe,
   for (int k = 0; k < nedge; ++k)
     FIT_REQUIRE(edges[k] >= 0 && edges[k] < g->ne, "fit_probe_voltages: edge out of range");
   cudaStream_t s = (cudaStream_t)stream;
-  DevTmp tmp(g);
+  FitDevTmp tmp(g);
   void *d_off, *d_e, *d_s, *d_v;
   fit_status st;
   if ((st = tmp.copy(&d_off, off, (nprobe + 1) * sizeof(int), s)) != FIT_OK) return st;
   if ((st = tmp.copy(&d_e, edges, nedge * sizeof(long long), s)) != FIT_OK) return st;
   if ((st = tmp.copy(&d_s, signs, nedge * sizeof(double), s)) != FIT_OK) return st;
-  if ((st = fit_dev_alloc(g, &d_v, (size_t)nfreq * nprobe * sizeof(double2))) != FIT_OK) return st;
-  tmp.held.push_back({d_v, (size_t)nfreq * nprobe * sizeof(double2)});
+  if ((st = tmp.alloc(&d_v, (size_t)nfreq * nprobe * sizeof(double2))) != FIT_OK) return st;
   k_probe<<<(unsigned)((long long)nfreq * nprobe), 256, 0, s>>>((const double2*)x, g->ne, (const int*)d_off, (const long long*)d_e,
                                                (const double*)d_s, nprobe, (double2*)d_v);
   FIT_CHECK_CUDA(cudaGetLastError());
@@ -214,13 +196,11 @@ fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int npo
     fit_solve_opts_default(&o);
   // one batch of nport * nfreq systems: system (j, f) at j * nfreq + f is port j excited alone at omega_f
   const size_t vbytes = (size_t)nsys * g->ne * sizeof(double2);
-  DevTmp tmp(g);
+  FitDevTmp tmp(g);
   void *d_b, *d_x;
   fit_status st;
-  if ((st = fit_dev_alloc(g, &d_b, vbytes)) != FIT_OK) return st;
-  tmp.held.push_back({d_b, vbytes});
-  if ((st = fit_dev_alloc(g, &d_x, vbytes)) != FIT_OK) return st;
-  tmp.held.push_back({d_x, vbytes});
+  if ((st = tmp.alloc(&d_b, vbytes)) != FIT_OK) return st;
+  if ((st = tmp.alloc(&d_x, vbytes)) != FIT_OK) return st;
   std::vector<double> om((size_t)nsys);
   for (int j = 0; j < nport; ++j) {
     for (int f = 0; f < nfreq; ++f) om[(size_t)j * nfreq + f] = omega[f];
