@@ -1227,7 +1227,7 @@ __global__ void k_reset_guard(Ctl* ctl, int which, cudaGraphConditionalHandle h,
 }  // namespace
 
 // ================================================================================================
-// Host driver
+// Host side: workspace, launch sequence, graph capture and the solve loop
 // ================================================================================================
 namespace {
 
