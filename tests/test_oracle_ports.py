@@ -116,3 +116,26 @@ def test_probe_voltage_and_port_rhs_conventions():
     mask[7] = 1
     b = PT.port_rhs(2.0, ne, [4, 7], [1.0, -1.0], mask, current=3.0)
     assert b[4] == -2j * 3.0 and b[7] == 0 and np.count_nonzero(b) == 1
+
+
+def test_z_is_j_omega_s_ainv_s():
+    """From b = -j w I s and V = -sum s x: Z_ij = j w s_i^T A^-1 s_j over unmasked edges.  The oracle's
+    z_matrix (sparse LU solves, probe sums, division by I) against that closed form evaluated with a dense
+    inverse, on a lossy grid with PEC cells, ports of mixed orientation, a shared edge and a masked edge."""
+    c = G.small_random(6, 5, 4, seed=19, pec_frac=0.1)
+    w = 2 * np.pi * 2.5e9
+    A, mask = _A(c, w)
+    nx, ny = c["nx"], c["ny"]
+    e1 = [3 * (2 + nx * (2 + ny * k)) + 2 for k in (1, 2)]
+    ports = [(e1, [1.0, 1.0]),
+             ([e1[1], 3 * (3 + nx * (1 + ny * 2)) + 0], [-1.0, 1.0]),
+             ([3 * (0 + nx * (2 + ny * 1)) + 1, 3 * (4 + nx * (3 + ny * 1)) + 1], [1.0, -1.0])]  # first is masked
+    assert mask[ports[2][0][0]] == 1
+    Z = PT.z_matrix(A, w, ports, mask, current=0.3)
+    ainv = np.linalg.inv(A.toarray())
+    S = np.zeros((A.shape[0], len(ports)))
+    for q, (e, s) in enumerate(ports):
+        for ee, ss in zip(e, s):
+            S[ee, q] += ss * (1 - mask[ee])
+    want = 1j * w * S.T @ ainv @ S
+    assert np.allclose(Z, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
