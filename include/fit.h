@@ -223,8 +223,25 @@ int fit_apply_variant_count(fit_prec prec);
  * buffer of twice the L2 size (counted against fit_set_hbm_budget; if it does not fit, candidates
  * are timed back to back instead).
  * Tests and experiments can force a kernel with the environment variable
- * FIT_APPLY_KERNEL=generic or FIT_APPLY_KERNEL=fused:<k>. */
+ * FIT_APPLY_KERNEL=generic or FIT_APPLY_KERNEL=fused:<k>.
+ * Persistence (opt-in): with FIT_TUNE_CACHE=<file> set, the autotuner first looks the key up in that
+ * file (fit_tuning_lookup) and uses a recorded choice without timing anything; after a search it
+ * appends its result (fit_tuning_record).  The key is the device name and SM count, the grid size, the
+ * precision and the batch. */
 fit_status fit_apply_tuned(const fit_grid* g, fit_prec prec, int nbatch, int* out7);
+
+/* fit_tuning_record -- append one autotuner result to the text cache file at path (created if
+ * missing): key (device name, SM count, nx, ny, nz, prec, nbatch), the number of fused variants this
+ * build has for prec, and choice (-1 generic kernel, k >= 0 fused variant k; see fit_apply_tuned).
+ * Host only.  FIT_EINVAL on a null or out-of-range argument or if the file cannot be written. */
+fit_status fit_tuning_record(const char* path, const char* device, int sm_count, int nx, int ny, int nz,
+                             fit_prec prec, int nbatch, int choice);
+
+/* fit_tuning_lookup -- *choice = the last choice recorded in path for this key by a build with the
+ * same variant table, or -2 if there is none (a missing file is not an error).  Malformed lines and
+ * lines of other keys or builds are skipped.  Host only.  FIT_EINVAL on a null argument. */
+fit_status fit_tuning_lookup(const char* path, const char* device, int sm_count, int nx, int ny, int nz,
+                             fit_prec prec, int nbatch, int* choice);
 
 /* ---- learned right preconditioner (3-level 3D U-Net) ---------------------------------------------
  * Not in the paper: its matrix-free operator "cannot use black-box preconditioners" (Sec. I), and

@@ -1097,6 +1097,19 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
     g->tuned[key] = -1;
     return FIT_OK;
   }
+  // opt-in persistence: a cache file named by FIT_TUNE_CACHE supplies the choice for this device, grid,
+  // precision and batch if it holds one, and records the result of a new search
+  const char* cache = getenv("FIT_TUNE_CACHE");
+  std::string dev_name;
+  int sms = 0;
+  const bool use_cache = cache && *cache && fit_tuning_device_key(&dev_name, &sms) == FIT_OK;
+  if (use_cache) {
+    int c = -2;
+    if (fit_tuning_lookup(cache, dev_name.c_str(), sms, g->nx, g->ny, g->nz, prec, nbatch, &c) == FIT_OK && c >= -1) {
+      g->tuned[key] = c;
+      return FIT_OK;
+    }
+  }
   int n = 0;
   variants(prec, &n);
   // Candidates are timed from a cold L2, as an apply inside a solve or a sweep mostly runs: before
@@ -1160,6 +1173,8 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
   }
   FIT_CHECK_CUDA(cudaGetLastError());
   g->tuned[key] = best;
+  if (use_cache)  // a cache that cannot be written leaves the in-memory choice in force
+    (void)fit_tuning_record(cache, dev_name.c_str(), sms, g->nx, g->ny, g->nz, prec, nbatch, best);
   return FIT_OK;
 }
 

@@ -138,6 +138,8 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
 // The cached choice: out7 = {choice (-1 generic, -2 untuned, >= 0 fused variant), TX, TY, TZ,
 // ring stages, warp-specialised (0/1), L2 prefetch distance in planes}.
 int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out7);
+// name (blanks replaced) and SM count of the current device: the device part of a tuning-cache key
+fit_status fit_tuning_device_key(std::string* name, int* sm_count);
 // Number of partial-sum slots per system that the apply writes for an epilogue.
 long long fit_apply_partials(const fit_grid* g, fit_prec prec);
 

@@ -99,6 +99,10 @@ def lib():
                      "fit_unet_backward", "fit_unet_train_step", "fit_unet_pack", "fit_unet_pack_target",
                      "fit_unet_unpack", "fit_set_preconditioner"):
             getattr(L, name).restype = ct.c_int
+        L.fit_tuning_record.argtypes = [ct.c_char_p, ct.c_char_p, i, i, i, i, i, i, i]
+        L.fit_tuning_record.restype = ct.c_int
+        L.fit_tuning_lookup.argtypes = [ct.c_char_p, ct.c_char_p, i, i, i, i, i, i, ct.POINTER(ct.c_int)]
+        L.fit_tuning_lookup.restype = ct.c_int
         pll = ct.POINTER(ct.c_longlong)
         pi = ct.POINTER(ct.c_int)
         L.fit_port_rhs.argtypes = [vp, i, pd, i, pll, pd, d, vp, vp]
@@ -259,6 +263,20 @@ def fit_apply_tuned(g, prec, nbatch):
     out = (ct.c_int * 7)()
     _check(lib().fit_apply_tuned(g, prec, nbatch, out), "fit_apply_tuned")
     return dict(choice=out[0], tx=out[1], ty=out[2], tz=out[3], stages=out[4], ws=out[5], pf=out[6])
+
+
+def fit_tuning_record(path, device, sm_count, nx, ny, nz, prec, nbatch, choice):
+    """Append one autotuner result to a tuning-cache file (see fit_apply_tuned)."""
+    _check(lib().fit_tuning_record(os.fsencode(path), device.encode(), sm_count, nx, ny, nz, prec, nbatch, choice),
+           "fit_tuning_record")
+
+
+def fit_tuning_lookup(path, device, sm_count, nx, ny, nz, prec, nbatch):
+    """The recorded choice for this key (-1 generic, k >= 0 fused variant k), or -2 if none."""
+    out = ct.c_int()
+    _check(lib().fit_tuning_lookup(os.fsencode(path), device.encode(), sm_count, nx, ny, nz, prec, nbatch,
+                                   ct.byref(out)), "fit_tuning_lookup")
+    return out.value
 
 
 def fit_jacobi(g, omega, x, y, prec=FIT_C128, stream=None):
