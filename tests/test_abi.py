@@ -88,3 +88,43 @@ def test_z_to_s_matches_the_oracle(L, P):
     S = fit.fit_z_to_s(Z, 50.0)
     want = PT.z_to_s(Z, 50.0)
     assert np.allclose(S, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+
+
+def test_header_compiles_as_c99_and_links(L, tmp_path):
+    """include/fit.h is a plain C header: a C99 program that includes it builds with -Wall -Werror, links
+    against the library and calls its host-only entry points (no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "use_fit.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "fit.h"
+int main(void) {
+  double z[2] = {30.0, -20.0}, s[2] = {0.0, 0.0};
+  int choice = 0;
+  fit_solve_opts o;
+  fit_solve_opts_default(&o);
+  if (fit_z_to_s(1, z, 50.0, s) != FIT_OK) return 1;
+  if (fit_tuning_lookup("/nonexistent/fit-tune.txt", "dev", 1, 2, 2, 2, FIT_C64, 1, &choice) != FIT_OK) return 2;
+  if (fit_grid_create(0, 1, 1, NULL, NULL, NULL, FIT_BC_PEC_ALL, NULL) != FIT_EINVAL) return 3;
+  printf("%s %d %.12f %.12f %d %d\n", fit_status_str(FIT_EINVAL), choice, s[0], s[1], o.restart, o.method);
+  return 0;
+}
+''')
+    libdir = os.path.join(ROOT, "paper_1705_08849_gb300")
+    exe = tmp_path / "use_fit"
+    cuda_lib = "/usr/local/cuda/lib64"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-L", libdir, "-lfitgb300", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, LD_LIBRARY_PATH=":".join(p for p in (libdir, cuda_lib, os.environ.get("LD_LIBRARY_PATH", ""))
+                                                     if p))
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    name, choice, sr, si, restart, method = r.stdout.split()
+    w = (30 - 20j - 50) / (30 - 20j + 50)
+    assert name == "FIT_EINVAL" and int(choice) == -2 and int(restart) == 30
+    assert abs(float(sr) - w.real) < 1e-12 and abs(float(si) - w.imag) < 1e-12
