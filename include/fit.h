@@ -312,8 +312,8 @@ fit_status fit_coef_scale(const fit_grid* g, double* s);
  *            orientations (an edge listed twice adds up)
  *   current  impressed current I [A]
  *   b        DEVICE array of nfreq * n_e double2, overwritten
- * Materials must be set (they fix the mask).  FIT_EINVAL on a null pointer or an edge out of range,
- * checked before anything is written.  Synchronous on the stream. */
+ * Materials must be set (they fix the mask).  FIT_EINVAL on a null pointer, an edge out of range or
+ * a non-finite frequency or current, checked before anything is written.  Synchronous on the stream. */
 fit_status fit_port_rhs(fit_grid* g, int nfreq, const double* omega, int nedge, const long long* edges,
                         const double* signs, double current, void* b, void* stream);
 
@@ -347,8 +347,9 @@ fit_status fit_z_to_s(int P, const double* Z, double z0, double* S);
  *   report     HOST array of nport * nfreq reports in system order j * nfreq + f (may be NULL)
  * Holds 2 * nport * nfreq * n_e double2 of device memory (right-hand sides and solutions) plus the
  * Krylov workspace while it runs, all counted against the HBM budget and freed before return.
- * Returns what fit_solve returns (Z is filled for FIT_NOT_CONVERGED / FIT_BREAKDOWN too), or an
- * error; FIT_EINVAL on bad ports, checked before any device work. */
+ * Returns what fit_solve returns (Z is filled for FIT_NOT_CONVERGED / FIT_BREAKDOWN too; the reports
+ * are filled whenever the solve ran, errors included), or an error; FIT_EINVAL on bad ports, a
+ * non-finite frequency or current, checked before any device work. */
 fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int nport, const int* off,
                             const long long* edges, const double* signs, double current, double tol,
                             const fit_solve_opts* opts, double* Z, fit_solve_report* report);

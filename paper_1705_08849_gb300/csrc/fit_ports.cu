@@ -66,6 +66,8 @@ fit_status fit_port_rhs(fit_grid* g, int nfreq, const double* omega, int nedge, 
   FIT_REQUIRE(g && omega && b && nfreq >= 1 && nedge >= 0, "fit_port_rhs: bad argument");
   FIT_REQUIRE(nedge == 0 || (edges && signs), "fit_port_rhs: null edge list");
   FIT_REQUIRE(g->has_materials, "fit_port_rhs: materials not set");
+  FIT_REQUIRE(std::isfinite(current), "fit_port_rhs: current must be finite");
+  for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(std::isfinite(omega[f]), "fit_port_rhs: omega must be finite");
   for (int q = 0; q < nedge; ++q) FIT_REQUIRE(edges[q] >= 0 && edges[q] < g->ne, "fit_port_rhs: edge out of range");
   cudaStream_t s = (cudaStream_t)stream;
   FIT_CHECK_CUDA(cudaMemsetAsync(b, 0, (size_t)nfreq * g->ne * sizeof(double2), s));
@@ -211,6 +213,8 @@ fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int npo
   }
   std::vector<fit_solve_report> rep((size_t)nsys);
   const fit_status solved = fit_solve(g, (int)nsys, om.data(), d_b, d_x, tol, &o, rep.data());
+  if (report)  // per-system outcomes are reported on every path that reached the solve
+    for (long long t = 0; t < nsys; ++t) report[t] = rep[(size_t)t];
   if (solved < 0) return solved;
   std::vector<double> V((size_t)nsys * nport * 2);
   if ((st = fit_probe_voltages(g, (int)nsys, d_x, nport, off, edges, signs, V.data(), o.stream)) != FIT_OK)
@@ -223,8 +227,6 @@ fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int npo
         Z[dst] = V[src] / current;
         Z[dst + 1] = V[src + 1] / current;
       }
-  if (report)
-    for (long long t = 0; t < nsys; ++t) report[t] = rep[(size_t)t];
   return solved;
 }
 
