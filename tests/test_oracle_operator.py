@@ -120,3 +120,33 @@ def test_jacobi_diagonal_is_diag_of_A():
     A = F.system_matrix(w, F.curl(4, 4, 5), me, mk, mn, mask)
     d = F.jacobi_diagonal(w, 4, 4, 5, me, mk, mn, mask)
     assert np.allclose(d, A.diagonal(), rtol=1e-14, atol=0)
+
+
+def test_A_is_singular_exactly_at_a_cavity_resonance():
+    """A(w) of the vacuum PEC cube (restricted to unmasked edges) is singular when w^2 is an eigenvalue
+    of the closed-form discrete spectrum and regular halfway between two of them: this fixes the sign
+    and the scale of the -w^2 M_eps term against the curl-curl part independently of the solvers."""
+    n, h = 4, 1e-3
+    c = G.cavity(n, h)
+    me, mk, mn, mask = _mats(c)
+    free = np.nonzero(mask == 0)[0]
+    lam = np.unique(np.round(F.cavity_eigenvalues(n, h)[F.cavity_eigenvalues(n, h) > 0], -6))
+    for w2, singular in ((lam[0], True), (0.5 * (lam[0] + lam[1]), False)):
+        A = F.system_matrix(np.sqrt(w2), F.curl(n, n, n), me, mk, mn, mask).toarray()[np.ix_(free, free)]
+        smin = np.linalg.svd(A, compute_uv=False).min() / np.abs(A).max()
+        assert (smin < 1e-8) == singular, (w2, smin)
+
+
+def test_a_current_source_delivers_power_into_a_lossy_grid():
+    """Time-harmonic convention of Eq. e2 (b = -j w j): the power a current source delivers to a passive
+    lossy medium, -Re(e^T conj(j)) / 2, is positive.  A sign slip in the right-hand side or in the loss
+    term makes it negative."""
+    c = G.small_random(6, 5, 5, seed=23, pec_frac=0.05)
+    me, mk, mn, mask = _mats(c)
+    w = 2 * np.pi * 2e9
+    A = F.system_matrix(w, F.curl(6, 5, 5), me, mk, mn, mask)
+    for seed in (1, 2, 3):
+        j = G.random_vector(A.shape[0], seed) * (1 - mask)
+        e = spla.spsolve(A.tocsc(), F.rhs_from_current(w, j, mask))
+        p = -0.5 * np.real(e @ np.conj(j))
+        assert p > 0, (seed, p)
