@@ -183,6 +183,7 @@ fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int npo
                             const fit_solve_opts* opts, double* Z, fit_solve_report* report) {
   FIT_REQUIRE(g && omega && off && Z && nfreq >= 1 && nport >= 1, "fit_z_parameters: bad argument");
   FIT_REQUIRE(current != 0.0 && std::isfinite(current), "fit_z_parameters: current must be finite and nonzero");
+  for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(std::isfinite(omega[f]), "fit_z_parameters: omega must be finite");
   FIT_REQUIRE(off[0] == 0, "fit_z_parameters: off[0] must be 0");
   for (int q = 0; q < nport; ++q) FIT_REQUIRE(off[q + 1] >= off[q], "fit_z_parameters: off must not decrease");
   FIT_REQUIRE(off[nport] == 0 || (edges && signs), "fit_z_parameters: null edge list");
