@@ -139,3 +139,18 @@ def test_z_is_j_omega_s_ainv_s():
             S[ee, q] += ss * (1 - mask[ee])
     want = 1j * w * S.T @ ainv @ S
     assert np.allclose(Z, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+
+
+def test_all_pins_in_one_right_hand_side_is_superposition():
+    """Driving every port at once (one port made of all the pins' edges, the single-run excitation Sec. IV
+    mentions) gives, by linearity, an impedance equal to the sum of all entries of the individual
+    ports' Z matrix."""
+    c, ports = _three_port_lossy()
+    w = 2 * np.pi * 2e9
+    A, mask = _A(c, w)
+    Z = PT.z_matrix(A, w, ports, mask)
+    edges = [e for p in ports for e in p[0]]
+    signs = [s for p in ports for s in p[1]]
+    assert len(set(edges)) == len(edges)  # disjoint pins
+    Zc = PT.z_matrix(A, w, [(edges, signs)], mask)[0, 0]
+    assert Zc == pytest.approx(Z.sum(), rel=1e-10)
