@@ -71,7 +71,10 @@ fit_status fit_port_rhs(fit_grid* g, int nfreq, const double* omega, int nedge, 
   for (int q = 0; q < nedge; ++q) FIT_REQUIRE(edges[q] >= 0 && edges[q] < g->ne, "fit_port_rhs: edge out of range");
   cudaStream_t s = (cudaStream_t)stream;
   FIT_CHECK_CUDA(cudaMemsetAsync(b, 0, (size_t)nfreq * g->ne * sizeof(double2), s));
-  if (nedge == 0) return FIT_OK;
+  if (nedge == 0) {
+    FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+    return FIT_OK;
+  }
   FitDevTmp tmp(g);
   void *d_om, *d_e, *d_s;
   fit_status st;
