@@ -148,9 +148,12 @@ def bicgstab(A, b, tol=1e-10, maxiter=10000):
     return x, maxiter, relres(A, x, b), 1
 
 
-def fgmres(A, b, tol=1e-10, restart=30, maxiter=10000, precond=None):
+def fgmres(A, b, tol=1e-10, restart=30, maxiter=10000, precond=None, precond_step=False, history=None):
     """Restarted right-preconditioned FGMRES(m) with modified Gram-Schmidt and Givens rotations.
-    ``precond`` maps a vector v_j to z_j = M(v_j) (identity when None, which is plain GMRES).
+    ``precond`` maps a vector v_j to z_j = M(v_j) (identity when None, which is plain GMRES); with
+    ``precond_step`` it is called as M(v_j, j) with the Arnoldi step j of the current cycle (the
+    flexible method allows the preconditioner to change from step to step).  ``history``, if a list,
+    receives the true relative residual after every restart cycle.
     Returns (x, iterations, true relative residual, status)."""
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
@@ -176,7 +179,7 @@ def fgmres(A, b, tol=1e-10, restart=30, maxiter=10000, precond=None):
         V[0] = r / beta
         jlast = 0
         for jj in range(m):
-            Z[jj] = M(V[jj])
+            Z[jj] = M(V[jj], jj) if precond_step else M(V[jj])
             w = A @ Z[jj]
             for i in range(jj + 1):  # modified Gram-Schmidt
                 H[i, jj] = np.vdot(V[i], w)
@@ -203,6 +206,8 @@ def fgmres(A, b, tol=1e-10, restart=30, maxiter=10000, precond=None):
         y = np.linalg.solve(np.triu(H[:jlast, :jlast]), g[:jlast])
         x = x + Z[:jlast].T @ y
         rr = relres(A, x, b)
+        if history is not None:
+            history.append(rr)
         if rr <= tol:
             return x, total, rr, 0
     return x, total, relres(A, x, b), 1

@@ -144,3 +144,76 @@ def tconv_loops(x, w, b):
                 k = (xx % 2) + 2 * (y % 2) + 4 * (z % 2)
                 out[z, y, xx] = np.asarray(b) + w[k] @ x[z // 2, y // 2, xx // 2]
     return out
+
+
+def conv3_dgrad_loops(dout, w):
+    """Data gradient of ``conv3_loops`` for the loss sum(out * dout): per input voxel u,
+    din[u] = sum over taps with v = u - off(tap) inside the grid of W[tap]^T dout[v]
+    (NDHWC numpy in and out; tiny shapes only)."""
+    nz, ny, nx, co = dout.shape
+    ci = w.shape[2]
+    din = np.zeros((nz, ny, nx, ci))
+    for z in range(nz):
+        for y in range(ny):
+            for xx in range(nx):
+                acc = np.zeros(ci)
+                for tap in range(27):
+                    dz, dy, dx = tap // 9 - 1, (tap // 3) % 3 - 1, tap % 3 - 1
+                    zs, ys, xs = z - dz, y - dy, xx - dx
+                    if 0 <= zs < nz and 0 <= ys < ny and 0 <= xs < nx:
+                        acc += w[tap].T @ dout[zs, ys, xs]
+                din[z, y, xx] = acc
+    return din
+
+
+def conv3_wgrad_loops(x, dout):
+    """Weight and bias gradients of ``conv3_loops`` for the loss sum(out * dout):
+    dW[tap][co][ci] = sum_v dout[v][co] x[v + off(tap)][ci] (inside the grid), db[co] = sum_v dout[v][co]."""
+    nz, ny, nx, ci = x.shape
+    co = dout.shape[3]
+    dw = np.zeros((27, co, ci))
+    for z in range(nz):
+        for y in range(ny):
+            for xx in range(nx):
+                for tap in range(27):
+                    dz, dy, dx = tap // 9 - 1, (tap // 3) % 3 - 1, tap % 3 - 1
+                    zs, ys, xs = z + dz, y + dy, xx + dx
+                    if 0 <= zs < nz and 0 <= ys < ny and 0 <= xs < nx:
+                        dw[tap] += np.outer(dout[z, y, xx], x[zs, ys, xs])
+    return dw, dout.reshape(-1, co).sum(axis=0)
+
+
+def tconv_dgrad_loops(dout, w):
+    """Data gradient of ``tconv_loops``: din[V] = sum_k W[k]^T dout[child(V, k)], child(V, k) = 2V + (kx, ky, kz)."""
+    Z2, Y2, X2, co = dout.shape
+    ci = w.shape[2]
+    din = np.zeros((Z2 // 2, Y2 // 2, X2 // 2, ci))
+    for z in range(Z2):
+        for y in range(Y2):
+            for xx in range(X2):
+                k = (xx % 2) + 2 * (y % 2) + 4 * (z % 2)
+                din[z // 2, y // 2, xx // 2] += w[k].T @ dout[z, y, xx]
+    return din
+
+
+def tconv_wgrad_loops(x, dout):
+    """Weight and bias gradients of ``tconv_loops``: dW[k] = sum_V outer(dout[child(V, k)], x[V]), db = sum dout."""
+    Z2, Y2, X2, co = dout.shape
+    ci = x.shape[3]
+    dw = np.zeros((8, co, ci))
+    for z in range(Z2):
+        for y in range(Y2):
+            for xx in range(X2):
+                k = (xx % 2) + 2 * (y % 2) + 4 * (z % 2)
+                dw[k] += np.outer(dout[z, y, xx], x[z // 2, y // 2, xx // 2])
+    return dw, dout.reshape(-1, co).sum(axis=0)
+
+
+def head_fwd(x, w, b):
+    """1x1x1 head: out[v][o] = b[o] + sum_c x[v][c] W[o][c] (x [N, C] numpy)."""
+    return x @ w.T + b
+
+
+def head_bwd(x, dout, w):
+    """Gradients of ``head_fwd`` for the loss sum(out * dout): (din, dW, db)."""
+    return dout @ w, dout.T @ x, dout.sum(axis=0)
