@@ -22,6 +22,9 @@
  *  - Memory: vectors (x, y, rhs, solutions) are DEVICE pointers owned by the caller, on the
  *    device that was current at fit_grid_create.  Geometry and material inputs are HOST
  *    pointers, copied in before the call returns.  The handle owns every derived device array.
+ *  - Devices: every call that takes a grid makes the grid's device current (cudaSetDevice) before
+ *    its first device allocation or launch, and leaves it current on return; the caller's stream
+ *    must belong to that device.
  *  - Errors: every call returns a fit_status and never throws across the ABI.  Negative values
  *    are errors that leave outputs unspecified; FIT_NOT_CONVERGED / FIT_BREAKDOWN still fill
  *    the solution and the report.  fit_last_error() gives a message for the calling thread.
@@ -119,11 +122,37 @@ fit_status fit_apply_sym(fit_grid* g, int nbatch, const double* omega, const voi
  *   nbatch   1 .. 4096; larger batches return FIT_EINVAL
  *   other arguments as for fit_apply (host omega, device x and y, stream)
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before anything that must not see CUDA runtime set-up work.
+ * device current; make that first call before anything that must not see CUDA runtime set-up work,
+ * and before any stream capture.  The address is kept for the life of the process: it belongs to the
+ * device's primary context, so after a cudaDeviceReset of that device this call must not be used
+ * again in the process.
  * All calls share the one array and each overwrites the entries it uses, so calls whose work may
  * overlap on the GPU (different streams, or different host threads) race on it: serialise them. */
 fit_status fit_apply_noalloc(fit_grid* g, int nbatch, const double* omega, const void* x, void* y,
                              fit_prec prec, void* stream);
+
+/* fit_set_abort -- set (value 1) or clear (value 0) the grid's abort word (not in the paper: failure
+ * detection of the runtime).  The word lives in pinned host memory mapped into the device, so kernels
+ * that are already queued or running see the host's write:
+ *   - while it is set, every call on this grid that enqueues device work (fit_apply, fit_apply_sym,
+ *     fit_apply_noalloc, fit_solve) returns FIT_ETIMEOUT at once without enqueuing anything;
+ *   - a fused apply kernel that starts while it is set leaves at once, and one that is running gives up
+ *     at its next bounded wait; either writes no further output and records the abort in the grid's
+ *     error word, which fit_sync reports;
+ *   - a running fit_solve ends its Krylov loops at the next loop test (every outer step, every 64th inner
+ *     step) and returns FIT_ETIMEOUT with x holding the last iterate and the reports filled.
+ * The untiled generic kernel has no waits and does not poll the word.  Host only; thread-safe (an
+ * atomic store), so another host thread may call it while a solve runs.  FIT_EINVAL for value not 0/1. */
+fit_status fit_set_abort(fit_grid* g, int value);
+
+/* fit_sync -- synchronise stream (a cudaStream_t as void*, NULL = legacy default stream), then read and
+ * clear the grid's device error word and the learned preconditioner's convolution timeout word.
+ * Returns FIT_ETIMEOUT (with fit_last_error saying which) if, since the last check, a bounded wait in a
+ * kernel of this grid ran out (about 0.5 s for the fused apply's hand-offs between warps, 2^22 polls
+ * for a copy) or the abort word stopped a kernel: the output of that kernel is incomplete.  FIT_OK
+ * otherwise; FIT_ECUDA if the synchronisation itself fails.  fit_solve performs the same check before
+ * it returns. */
+fit_status fit_sync(fit_grid* g, void* stream);
 
 /* Krylov methods (Sec. IV lists the PETSc solvers tried; bcgs and the gmres family are kept, and
  * "cg" and "cr" on this complex symmetric system (A^T = A, Eq. e2) are read as CG and CR with the
@@ -163,6 +192,9 @@ typedef struct fit_solve_opts {
                         (h * nfreq + f) * n_e (used to harvest training pairs); NULL = off */
   int history_len;   /* slots in history (per system) */
   int history_every; /* outer steps between snapshots (>= 1) */
+  int pc_every;      /* FIT_PC_UNET: the network runs on the Arnoldi steps j of a cycle with j % pc_every == 0
+                        (the Jacobi term alone on the others); 2 (the default) alternates, a value >= restart
+                        runs it on the cycle's first vector only, which is the normalised true residual */
 } fit_solve_opts;
 
 typedef struct fit_solve_report {
@@ -192,7 +224,8 @@ void fit_solve_opts_default(fit_solve_opts* opts);
  * ends above its starting residual gives no step, and the next one (from the same residual, so
  * along the same iterates) stops where that one was smallest.
  * Returns FIT_OK if every system converged, else the first non-OK per-system status, or an
- * error.  Synchronous on opts->stream.  FIT_EBUDGET if the Krylov workspace for the batch does
+ * error; FIT_ETIMEOUT if the abort word (fit_set_abort) ended the solve or a bounded device wait ran
+ * out (the reports of the systems that ran are filled).  Synchronous on opts->stream.  FIT_EBUDGET if the Krylov workspace for the batch does
  * not fit the handle's HBM budget (checked before any allocation). */
 fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rhs, void* x,
                      double tol, const fit_solve_opts* opts, fit_solve_report* report);
@@ -279,6 +312,63 @@ fit_status fit_unet_pack(const fit_grid* g, const void* r, double scale, void* o
 fit_status fit_unet_pack_target(const fit_grid* g, const void* e, double scale, float* out6, void* stream);
 /* z = scale * (network output as complex64, n_e), zero on masked edges */
 fit_status fit_unet_unpack(const fit_grid* g, const float* y6, double scale, void* z, void* stream);
+/* Single layers of the network: the kernels fit_unet_forward and fit_unet_backward run, one call per
+ * layer, for per-layer checks and tools.  All tensors are DEVICE pointers in NDHWC layout (voxel
+ * x + nx*(y + ny*z), channels innermost); activations are bf16, weights, biases and weight gradients
+ * FP32.  Asynchronous on stream.  The convolution calls convert the FP32 weights to the layer's bf16
+ * copies in stream-ordered scratch (cudaMallocAsync / cudaFreeAsync) exactly as the network does.
+ * FIT_EINVAL for a (cin, cout) that is not a layer shape of the network. */
+/* fit_unet_conv3 -- 3x3x3 convolution, stride 1, zero padding 1, on the tensor cores (bf16 operands, FP32
+ * accumulation, bf16 result):  out[v][co] = act(bias[co] + sum_{tap, ci} in[v + off(tap)][ci] W[tap][co][ci])
+ * with tap = dz*9 + dy*3 + dx, off(tap) = (dx-1, dy-1, dz-1), act = ReLU if relu != 0.
+ *   nx, ny, nz >= 1 (any sizes); (cin, cout) in {(16,16), (16,32), (32,32), (32,64), (64,64), (64,32), (32,16)}
+ *   in [N][cin] bf16; w [27][cout][cin] FP32 (rounded to bf16 for the MMAs); bias [cout] FP32 or NULL;
+ *   out [N][cout] bf16 */
+fit_status fit_unet_conv3(int nx, int ny, int nz, int cin, int cout, const void* in, const float* w,
+                          const float* bias, int relu, void* out, void* stream);
+/* fit_unet_conv3_dgrad -- its data gradient (the same convolution kernel on flipped, transposed weights):
+ *   din[v][ci] = sum_{tap, co} dout[v - off(tap)][co] W[tap][co][ci];  dout [N][cout] bf16, din [N][cin] bf16 */
+fit_status fit_unet_conv3_dgrad(int nx, int ny, int nz, int cin, int cout, const void* dout, const float* w,
+                                void* din, void* stream);
+/* fit_unet_conv3_wgrad -- its weight gradient (FP32 on the CUDA cores), overwritten:
+ *   dw[tap][co][ci] = sum_v dout[v][co] in[v + off(tap)][ci],  db[co] = sum_v dout[v][co] (db may be NULL) */
+fit_status fit_unet_conv3_wgrad(int nx, int ny, int nz, int cin, int cout, const void* in, const void* dout,
+                                float* dw, float* db, void* stream);
+/* fit_unet_tconv -- 2x2x2 transposed convolution, stride 2, from an mx x my x mz grid to the 2x finer one:
+ *   out[X][co] = b[co] + sum_ci in[X / 2][ci] W[k][co][ci], k = X_x%2 + 2 (X_y%2) + 4 (X_z%2);
+ *   (cin, cout) = (64, 32) or (32, 16); in [mx*my*mz][cin] bf16, w [8][cout][cin] FP32, out bf16 */
+fit_status fit_unet_tconv(int mx, int my, int mz, int cin, int cout, const void* in, const float* w,
+                          const float* b, void* out, void* stream);
+/* fit_unet_tconv_backward -- din[V][ci] = sum_{k, co} dout[child(V, k)][co] W[k][co][ci] (bf16), and, overwritten,
+ * dw[k][co][ci] = sum_V in[V][ci] dout[child(V, k)][co], db[co] = sum dout[.][co] (FP32) */
+fit_status fit_unet_tconv_backward(int mx, int my, int mz, int cin, int cout, const void* in, const void* dout,
+                                   const float* w, void* din, float* dw, float* db, void* stream);
+/* fit_unet_head -- the 1x1x1 head, 16 -> 6 channels: out[v][o] = b[o] + sum_c in[v][c] W[o][c] (FP32 out) */
+fit_status fit_unet_head(long long nvox, const void* in, const float* w, const float* b, float* out, void* stream);
+/* fit_unet_head_backward -- din[v][c] = sum_o dout[v][o] W[o][c] (bf16); overwritten dw[o][c] = sum_v dout[v][o]
+ * in[v][c], db[o] = sum_v dout[v][o] (FP32) */
+fit_status fit_unet_head_backward(long long nvox, const void* in, const float* dout, const float* w, void* din,
+                                  float* dw, float* db, void* stream);
+
+/* fit_unet_training_pair -- one training pair of the learned preconditioner from an iterate x_k of a solve
+ * of A(omega) x = b whose solution is x* (the harvest step of the training data):
+ *     r = b - A(omega) x_k  (FP64 apply),   rms = ||r||_2 / sqrt(n_e),
+ *     pair[c][0..5]  = bf16 of r / rms                            (Re, Im of the x, y, z edges of cell c)
+ *     pair[c][6..11] = bf16 of ((x* - x_k) - D^-1 r) / (s rms)    (the correction the Jacobi term misses)
+ * with D = diag(A(omega)) (Eq. Precond construction) and s = fit_coef_scale (the units of the scaled
+ * complex64 operator the network preconditions); masked edges are zero in both halves.
+ *   x_k, x_star, b   DEVICE complex128 [n_e];  pair  DEVICE bf16 [ncell][12] (4-byte aligned)
+ *   rms_out          HOST, may be NULL: receives rms (the call synchronises on stream either way)
+ * Holds two temporary device vectors (counted against the HBM budget) while it runs. */
+fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, const void* xstar, const void* b,
+                                  void* pair, double* rms_out, void* stream);
+/* fit_unet_pair_sample -- network input and target of a stored pair: in16[c] = base16[c] with channels
+ * 0..5 replaced by pair[c][0..5]; target6[c] = FP32 of pair[c][6..11].  base16 is the geometry's packed
+ * input of a zero residual (fit_unet_pack), which carries its material channels.  DEVICE pointers,
+ * base16 and in16 16-byte aligned; asynchronous. */
+fit_status fit_unet_pair_sample(long long ncell, const void* pair, const void* base16, void* in16, float* target6,
+                                void* stream);
+
 /* attach a network to the grid; fit_solve with precond = FIT_PC_UNET (FGMRES, FIT_SOLVE_MIXED)
  * then applies M(v) = D^-1 v + rms(v) U(v / rms(v)) as the right preconditioner: the network learns
  * the part of the correction that the Jacobi term misses (its head starts at zero, so an untrained

@@ -81,7 +81,8 @@ struct FusedArgs {
   using V = typename cplx<T>::t;
   const V* x;
   const double* omega;
-  int* err;
+  int* err;                  // the grid's error word: 1 = a bounded wait ran out, 2 = aborted
+  const volatile int* abort; // the grid's abort word (pinned host memory), polled in every bounded wait
   int nx, ny, nz, tz, nzc, ntx, nty, ntiles;
   int nb;    // systems in the batch; tile t = (chunk, row, column) * nb + b, so that CTAs running at the
              // same time work on one column for several systems and share its coefficients in L2
@@ -156,14 +157,19 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false after ~2^22 polls (the copy engine never needs that long for a few KB)
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait: false after ~2^22 polls (the copy engine never needs that long for a few KB), or as
+// soon as the host sets the abort word (read every 4096 polls; abort = nullptr: no early exit, for the
+// waits that let a CTA's own copies land before it leaves)
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort) {
   for (int it = 0; it < (1 << 22); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(64);
+    if ((it & 4095) == 4095 && abort && *abort) return false;
   }
   return false;
 }
+// the error code a kernel records when a wait gives up: 2 if the host asked it to stop, else 1
+__device__ inline int wait_error(const volatile int* abort) { return *abort ? 2 : 1; }
 __device__ inline void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -223,9 +229,11 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
-    bad = 0;
+    bad = *a.abort ? 1 : 0;  // aborted before it started: no copy is issued, nothing is written
+    if (bad) atomicExch(a.err, 2);
   }
   __syncthreads();
+  if (bad) return;
 
   unsigned G = 0, O = 0;        // planes issued into the ring / output planes written, this CTA
   bool pend = false;            // an output plane is staged but not yet stored (thread 0's view)
@@ -264,8 +272,8 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
       if (kU) tma_prefetch_4d(&tm_u, L::CE * 3 * i0, j0, p, b);
     };
     auto wait = [&](int q) {
-      if (!mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1)) {
-        atomicExch(a.err, 1);
+      if (!mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1, a.abort)) {
+        atomicExch(a.err, wait_error(a.abort));
         bad = 1;
       }
     };
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
     }
     int issued = min(S, nplanes);
     auto drain = [&]() {  // bounded waits for every copy this tile issued
-      for (int q = 0; q < issued; ++q) (void)mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1);
+      for (int q = 0; q < issued; ++q) (void)mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1, nullptr);
     };
 
     // prologue: planes k0-1 (q = 0) and k0 (q = 1); h(k0-1) of the own column
@@ -387,6 +395,9 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
             acc[2] += out.x * out.x + out.y * out.y;
           } else if (EPI == FIT_EPI_RESID) {
             acc[2] += out.x * out.x + out.y * out.y;
+          } else if (EPI == FIT_EPI_DOT_XY) {
+            acc[0] += xv.x * out.x - xv.y * out.y;
+            acc[1] += xv.x * out.y + xv.y * out.x;
           }
         }
         ob[w] = out;
@@ -457,12 +468,14 @@ __device__ inline uint64_t global_ns() {
 // Wait for a handoff between warps of the CTA: spin on try_wait (which itself suspends the thread
 // until the phase completes or a short hardware limit passes) with no sleep in between, so the
 // waiting warp resumes as soon as the other side arrives; gives up after 0.5 s of wall time.
-__device__ inline bool mbar_wait_handoff(uint64_t* bar, uint32_t parity) {
+// The host's abort word ends the wait early (read every 256 polls, with the clock); abort = nullptr
+// for the waits that let the CTA's own copies land before it leaves.
+__device__ inline bool mbar_wait_handoff(uint64_t* bar, uint32_t parity, const volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1; it < (1u << 30); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0u && global_ns() - t0 > 500000000ull) return false;
+    if ((it & 255u) == 0u && (global_ns() - t0 > 500000000ull || (abort && *abort))) return false;
   }
   return false;
 }
@@ -506,12 +519,14 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       mbar_init(&ready[s], 1);
       mbar_init(&empty[s], TY);
     }
-    *abort_flag = 0;
+    *abort_flag = *a.abort ? 1 : 0;  // aborted before it started: every role leaves at once
+    if (*abort_flag) atomicExch(a.err, 2);
     fence_mbar_init();
   }
   __syncthreads();
+  if (*abort_flag) return;
   auto stage = [&](unsigned gq) -> unsigned char* { return smem + (gq % S) * L::STAGE; };
-  auto fail = [&]() { atomicExch(a.err, 1); };
+  auto fail = [&]() { atomicExch(a.err, wait_error(a.abort)); };
 
   // This CTA's work, one segment (bx, by, b, planes k0 .. k1-1) at a time; every role walks the
   // same sequence.  Tiled: tiles blockIdx.x, blockIdx.x + gridDim.x, ... of ntx*nty*nzc*nbatch
@@ -575,10 +590,10 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
         for (int p = k0 - 1; p < k0 - 1 + S + a.pf; ++p) prefetch(p);
       for (int p = k0 - 1; p <= k1; ++p, ++G) {
         const unsigned s = G % S, use = G / S;
-        if (use > 0 && !mbar_wait_handoff(&empty[s], (use - 1) & 1)) {
+        if (use > 0 && !mbar_wait_handoff(&empty[s], (use - 1) & 1, a.abort)) {
           // record; the copies still in flight are the last (at most S - 1) issued: let them land
           fail();
-          for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1);
+          for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1, nullptr);
           return;
         }
         unsigned char* st = stage(G);
@@ -592,7 +607,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       }
     }
     // every copy lands before the CTA retires
-    for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1);
+    for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1, nullptr);
     return;
   }
 
@@ -604,7 +619,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       if (epi.status && epi.status[b] != 0) continue;
       const int nplanes = k1 - k0 + 2;
       for (int q = 0; q < nplanes; ++q, ++G) {
-        if (!__all_sync(0xffffffffu, mbar_wait_handoff(&full[G % S], (G / S) & 1))) {  // warp-uniform
+        if (!__all_sync(0xffffffffu, mbar_wait_handoff(&full[G % S], (G / S) & 1, a.abort))) {  // warp-uniform
           if (lane == 0) fail();
           return;
         }
@@ -658,7 +673,8 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       const int er = (ty + 1) * L::EW + 3 * (tx + 2);
       const int nr = (ty + 1) * L::NW + 3 * (tx + 4);
       V* stg = stg_all + ty * 96;
-      dead = !mbar_wait_handoff(&ready[G0 % S], (G0 / S) & 1) || !mbar_wait_handoff(&ready[(G0 + 1) % S], ((G0 + 1) / S) & 1);
+      dead = !mbar_wait_handoff(&ready[G0 % S], (G0 / S) & 1, a.abort) ||
+             !mbar_wait_handoff(&ready[(G0 + 1) % S], ((G0 + 1) / S) & 1, a.abort);
       dead = __any_sync(0xffffffffu, dead);  // warp-uniform
       if (!dead) {
         V e0[3], em[3], ejm[3];
@@ -691,7 +707,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
 #pragma unroll 2
         for (int k = k0; k < k1; ++k) {
           const int qk = k - k0 + 1, qn = qk + 1;
-          if (__any_sync(0xffffffffu, !mbar_wait_handoff(&ready[(G0 + qn) % S], ((G0 + qn) / S) & 1))) {
+          if (__any_sync(0xffffffffu, !mbar_wait_handoff(&ready[(G0 + qn) % S], ((G0 + qn) / S) & 1, a.abort))) {
             dead = true;
             break;
           }
@@ -759,6 +775,9 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
                 acc[2] += out.x * out.x + out.y * out.y;
               } else if (EPI == FIT_EPI_RESID) {
                 acc[2] += out.x * out.x + out.y * out.y;
+              } else if (EPI == FIT_EPI_DOT_XY) {
+                acc[0] += xv.x * out.x - xv.y * out.y;
+                acc[1] += xv.x * out.y + xv.y * out.x;
               }
             }
             stg[3 * tx + w] = out;
@@ -838,10 +857,26 @@ const Variant kVariants64[] = {
     {8, 0, 3, 0, 2},  {8, 0, 3, 0, 4},  {8, 0, 3, 0, 8}, {4, 0, 4, 0, 4}, {8, 0, 4, 0, 4},
     {4, 0, 4, 1, 0},  {8, 0, 4, 1, 0},  {8, 32, 4, 1, 0}, {16, 0, 4, 1, 0},
     {4, 0, 4, 1, 4},  {8, 0, 3, 1, 4},  {8, 0, 4, 1, 2}, {8, 0, 4, 1, 4}, {8, 0, 4, 1, 8}, {8, 32, 4, 1, 4},
-    {8, -1, 4, 1, 0}, {4, -1, 4, 1, 0}, {8, -1, 4, 1, 2}};
+    {8, -1, 4, 1, 0}, {4, -1, 4, 1, 0}, {8, -1, 4, 1, 2},
+    // taller tiles and deeper rings on the even split: fewer y-halo rows per cell, longer z ranges per CTA
+    {16, -1, 4, 1, 0}, {16, -1, 5, 1, 0}, {16, -1, 4, 1, 2}, {8, -1, 5, 1, 0}, {8, -1, 3, 1, 0}};
 const Variant kVariants128[] = {{4, 16, 3, 0, 0}, {4, 32, 3, 0, 0}, {8, 16, 3, 0, 0}, {8, 32, 3, 0, 0},
                                 {4, 0, 3, 0, 0},  {8, 0, 3, 0, 0},  {4, 0, 4, 1, 0},  {8, 0, 4, 1, 0},
                                 {8, 0, 3, 0, 4},  {4, 0, 4, 1, 4},  {8, 0, 4, 1, 4},  {8, -1, 4, 1, 0}};
+
+// largest dynamic shared memory a CTA may opt in to on the current device
+int fused_smem_limit() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 0;
+  return v;
+}
+
+// dynamic shared memory of a variant with the largest epilogue staging (the vector u of DOT_U / RESID)
+template <typename T, int TY, int S, int WS>
+int variant_smem_max() {
+  return Layout<T, TY, true>::smem(S) + (WS ? 3 * 8 * S + 8 * 3 * TY + 16 : 0);
+}
 
 template <typename T, int TY, int S, int WS>
 fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y, const T* nu,
@@ -910,6 +945,7 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
   a.x = (const typename cplx<T>::t*)x;
   a.omega = omega_dev;
   a.err = g->err_dev;
+  a.abort = g->abort_dev;
   a.nx = g->nx;
   a.ny = g->ny;
   a.nz = g->nz;
@@ -925,6 +961,10 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
   int smem = ku ? Layout<T, TY, true>::smem(S) : Layout<T, TY, false>::smem(S);
   if (WS) smem += 3 * 8 * S + 8 * 3 * TY + 16;  // three barriers per stage, row partial sums, abort flag
   auto run = [&](auto kern) -> fit_status {
+    if (smem > fused_smem_limit()) {  // this ring depth and epilogue staging exceed an SM's shared memory
+      fit_set_error("fused apply: launch shape does not fit on an SM");
+      return FIT_EINVAL;
+    }
     FIT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -972,6 +1012,7 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
       case FIT_EPI_DOT_U: return run(ws_apply_kernel<T, TY, FIT_EPI_DOT_U, S>);
       case FIT_EPI_DOT_TS: return run(ws_apply_kernel<T, TY, FIT_EPI_DOT_TS, S>);
       case FIT_EPI_RESID: return run(ws_apply_kernel<T, TY, FIT_EPI_RESID, S>);
+      case FIT_EPI_DOT_XY: return run(ws_apply_kernel<T, TY, FIT_EPI_DOT_XY, S>);
     }
   } else {
     switch (e.mode) {
@@ -979,6 +1020,7 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
       case FIT_EPI_DOT_U: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_U, S>);
       case FIT_EPI_DOT_TS: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_TS, S>);
       case FIT_EPI_RESID: return run(fused_apply_kernel<T, TY, FIT_EPI_RESID, S>);
+      case FIT_EPI_DOT_XY: return run(fused_apply_kernel<T, TY, FIT_EPI_DOT_XY, S>);
     }
   }
   fit_set_error("fused apply: unknown epilogue");
@@ -1001,6 +1043,8 @@ fit_status launch_fused(fit_grid* g, int nbatch, const double* omega_dev, const 
   if constexpr (sizeof(T) == 4) {  // complex64 only
     FIT_LV(8, 3, 1);
     FIT_LV(16, 4, 1);
+    FIT_LV(16, 5, 1);
+    FIT_LV(8, 5, 1);
   }
 #undef FIT_LV
   fit_set_error("fused apply: no such variant");
@@ -1037,6 +1081,34 @@ bool fused_supported(const fit_grid* g, fit_prec prec) {
   return encoder() != nullptr;
 }
 
+// dynamic shared memory of variant v with the epilogue vector staged (ku) or not
+template <typename T>
+int variant_smem(const Variant& v, bool ku) {
+#define FIT_SM(TY_, S_, WS_)                                                                              \
+  if (v.ty == TY_ && v.stages == S_ && v.ws == WS_)                                                       \
+    return (ku ? Layout<T, TY_, true>::smem(S_) : Layout<T, TY_, false>::smem(S_)) +                      \
+           (WS_ ? 3 * 8 * S_ + 8 * 3 * TY_ + 16 : 0)
+  FIT_SM(4, 4, 0);
+  FIT_SM(8, 4, 0);
+  FIT_SM(16, 3, 0);
+  FIT_SM(4, 3, 0);
+  FIT_SM(8, 3, 0);
+  FIT_SM(4, 4, 1);
+  FIT_SM(8, 4, 1);
+  FIT_SM(8, 3, 1);
+  FIT_SM(16, 4, 1);
+  FIT_SM(16, 5, 1);
+  FIT_SM(8, 5, 1);
+#undef FIT_SM
+  return 1 << 30;
+}
+
+// the variant's shared memory fits one CTA with every epilogue (so an autotuned choice serves them all)
+bool fused_smem_ok(fit_prec prec, const Variant& v) {
+  const int need = prec == FIT_C64 ? variant_smem<float>(v, true) : variant_smem<double>(v, true);
+  return need <= fused_smem_limit();
+}
+
 bool fused_fits(const fit_grid* g, int nbatch, const Variant& v) {
   // the persistent loop indexes tiles with int
   const int tz = v.tz > 0 ? v.tz : 2;
@@ -1067,7 +1139,7 @@ static fit_status launch_choice(fit_grid* g, int choice, int nbatch, const doubl
   if (choice < 0) return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, &e);
   int n = 0;
   const Variant* v = variants(prec, &n);
-  if (choice >= n || !fused_fits(g, nbatch, v[choice]))
+  if (choice >= n || !fused_fits(g, nbatch, v[choice]) || !fused_smem_ok(prec, v[choice]))
     return fit_launch_apply_generic(g, nbatch, omega_dev, x, y, prec, out_scale, s, &e);
   if (prec == FIT_C64) return launch_fused<float>(g, nbatch, omega_dev, x, y, g->nu32, g->ek32, out_scale, s, e, v[choice]);
   return launch_fused<double>(g, nbatch, omega_dev, x, y, g->nu64, g->ek64, out_scale, s, e, v[choice]);
@@ -1111,7 +1183,7 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
     }
   }
   int n = 0;
-  variants(prec, &n);
+  const Variant* vars = variants(prec, &n);
   // Candidates are timed from a cold L2, as an apply inside a solve or a sweep mostly runs: before
   // each timed launch half of a scratch buffer of twice the L2 size is written and the other half
   // read, which evicts the operands and leaves only clean lines behind.  Without room for the
@@ -1142,6 +1214,7 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
   std::vector<float> t(n + 1, 1e30f);
   for (int pass = 0; pass < 3; ++pass) {
     for (int c = -1; c < n; ++c) {
+      if (c >= 0 && (!fused_smem_ok(prec, vars[c]) || !fused_fits(g, nbatch, vars[c]))) continue;
       fit_status st = launch_choice(g, c, nbatch, omega_dev, x, y, prec, 1.0, s, none);  // warm-up
       if (st != FIT_OK) continue;
       float ms[7];
@@ -1165,6 +1238,13 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
       best_ms = t[c + 1];
       best = c;
     }
+  // FIT_TUNE_LOG=1: every candidate's time on stderr (for studying the launch shapes)
+  const char* lg = getenv("FIT_TUNE_LOG");
+  if (lg && lg[0] == '1') {
+    for (int c = -1; c < n; ++c)
+      fprintf(stderr, "[fit tune] %dx%dx%d prec %d batch %d: candidate %d %.2f us%s\n", g->nx, g->ny, g->nz, (int)prec,
+              nbatch, c, t[c + 1] < 1e29f ? 1e3f * t[c + 1] : -1.f, c == best ? " (chosen)" : "");
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (scratch) {
@@ -1172,6 +1252,8 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
     fit_dev_free(g, scratch, 2 * half);
   }
   FIT_CHECK_CUDA(cudaGetLastError());
+  // kernels that saw the abort word left at once: their times mean nothing, so nothing is cached
+  if (fit_check_abort(g, "fit_tune_apply") != FIT_OK) return FIT_ETIMEOUT;
   g->tuned[key] = best;
   if (use_cache)  // a cache that cannot be written leaves the in-memory choice in force
     (void)fit_tuning_record(cache, dev_name.c_str(), sms, g->nx, g->ny, g->nz, prec, nbatch, best);

@@ -197,6 +197,24 @@ static fit_status finish_coefficients(fit_grid* g) {
 // ------------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------------
+fit_status fit_check_abort(const fit_grid* g, const char* what) {
+  if (g->abort_host && __atomic_load_n(g->abort_host, __ATOMIC_SEQ_CST)) {
+    fit_set_error(std::string(what) + ": the grid's abort word is set (fit_set_abort)");
+    return FIT_ETIMEOUT;
+  }
+  return FIT_OK;
+}
+
+fit_status fit_take_device_error(fit_grid* g) {
+  int code = 0;
+  FIT_CHECK_CUDA(cudaMemcpy(&code, g->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code == 0) return FIT_OK;
+  FIT_CHECK_CUDA(cudaMemset(g->err_dev, 0, sizeof(int)));
+  fit_set_error(code == 2 ? "a kernel of this grid stopped early: the abort word was set"
+                          : "a bounded wait in a kernel of this grid ran out; its output is incomplete");
+  return FIT_ETIMEOUT;
+}
+
 extern "C" {
 
 const char* fit_status_str(fit_status s) {
@@ -224,6 +242,7 @@ void fit_grid_destroy(fit_grid* g) {
   void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev, g->err_dev, g->mat16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (g->abort_host) cudaFreeHost(g->abort_host);
   cudaSetDevice(cur);
   delete g;
 }
@@ -262,6 +281,24 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
       (st = fit_dev_alloc(g, (void**)&g->mat16, (size_t)g->ncell * 4 * 2))) {
     fit_grid_destroy(g);
     return st;
+  }
+  // the abort word: pinned host memory mapped into the device's address space, so that a kernel that
+  // is already running sees the host's write
+  {
+    void* hp = nullptr;
+    void* dp = nullptr;
+    cudaError_t e = cudaHostAlloc(&hp, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess) {
+      g->abort_host = (int*)hp;
+      *g->abort_host = 0;
+      e = cudaHostGetDevicePointer(&dp, hp, 0);
+    }
+    if (e != cudaSuccess) {
+      fit_set_error(std::string("fit_grid_create: abort word: ") + cudaGetErrorString(e));
+      fit_grid_destroy(g);
+      return FIT_ECUDA;
+    }
+    g->abort_dev = (const int*)dp;
   }
   cudaMemcpy(g->dx, dx, nx * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(g->dy, dy, ny * sizeof(double), cudaMemcpyHostToDevice);
@@ -398,12 +435,32 @@ fit_status fit_apply(fit_grid* g, int nbatch, const double* omega, const void* x
   const char* xb = (const char*)x;
   const char* yb = (const char*)y;
   FIT_REQUIRE(xb + vbytes <= yb || yb + vbytes <= xb, "fit_apply: x and y overlap");
+  if (fit_check_abort(g, "fit_apply") != FIT_OK) return FIT_ETIMEOUT;
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
   fit_status st = stage_omega(g, nbatch, omega, s);
   if (st != FIT_OK) return st;
   double out_scale = prec == FIT_C64 ? 1.0 / g->coef_scale : 1.0;
   return fit_launch_apply(g, nbatch, g->omega_dev, x, y, prec, out_scale, s);
+}
+
+fit_status fit_set_abort(fit_grid* g, int value) {
+  FIT_REQUIRE(g && g->abort_host, "fit_set_abort: null grid");
+  FIT_REQUIRE(value == 0 || value == 1, "fit_set_abort: value must be 0 or 1");
+  __atomic_store_n(g->abort_host, value, __ATOMIC_SEQ_CST);
+  return FIT_OK;
+}
+
+fit_status fit_sync(fit_grid* g, void* stream) {
+  FIT_REQUIRE(g, "fit_sync: null grid");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  FIT_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  fit_status st = fit_take_device_error(g);
+  if (fit_unet_take_timeout() && st == FIT_OK) {
+    fit_set_error("fit_sync: a bounded wait in a learned-preconditioner convolution ran out");
+    st = FIT_ETIMEOUT;
+  }
+  return st;
 }
 
 fit_status fit_apply_sym(fit_grid* g, int nbatch, const double* omega, const void* x, void* y, fit_prec prec,
@@ -419,6 +476,7 @@ fit_status fit_apply_sym(fit_grid* g, int nbatch, const double* omega, const voi
   const char* xb = (const char*)x;
   const char* yb = (const char*)y;
   FIT_REQUIRE(xb + vbytes <= yb || yb + vbytes <= xb, "fit_apply_sym: x and y overlap");
+  if (fit_check_abort(g, "fit_apply_sym") != FIT_OK) return FIT_ETIMEOUT;
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
   fit_status st = stage_omega(g, nbatch, omega, s);

@@ -45,7 +45,9 @@ struct fit_grid {
   size_t budget = 0;       // 0 = unlimited
   // autotuned apply kernel per (batch, precision): -1 = generic kernel, k >= 0 = fused variant k
   std::map<long long, int> tuned;
-  int* err_dev = nullptr;  // device error word: a bounded wait in a kernel ran out
+  int* err_dev = nullptr;  // device error word: 1 = a bounded wait in a kernel ran out, 2 = aborted
+  int* abort_host = nullptr;       // abort word in pinned, mapped host memory (fit_set_abort)
+  const int* abort_dev = nullptr;  // its device alias, polled by the persistent kernels and the solver
   void* mat16 = nullptr;   // [ncell][4] bf16 material channels of the learned preconditioner
   struct fit_unet* unet = nullptr;  // attached learned preconditioner (not owned)
 };
@@ -57,6 +59,16 @@ fit_status fit_unet_apply_vec(fit_unet* u, const fit_grid* g, const void* v, voi
                               void* x16, const void* dinv, cudaStream_t s);
 // size the network's activations for the grid and refresh its bf16 weights (call before capture)
 fit_status fit_unet_prepare(fit_unet* u, const fit_grid* g, cudaStream_t s);
+
+// Reads and clears the grid's device error word (synchronous); FIT_ETIMEOUT with a message if a bounded
+// wait ran out or the abort word stopped a kernel since the last check, else FIT_OK.
+fit_status fit_take_device_error(fit_grid* g);
+// Reads and clears the network kernels' timeout word on the current device (synchronous): 1 if a bounded
+// wait of a tensor-core convolution ran out since the last call.
+int fit_unet_take_timeout();
+// FIT_ETIMEOUT (with a message) if the grid's abort word is set, else FIT_OK: checked on the host before
+// a call enqueues any work.
+fit_status fit_check_abort(const fit_grid* g, const char* what);
 
 // Thread-local last-error message.
 void fit_set_error(const std::string& msg);
@@ -114,8 +126,9 @@ struct FitDevTmp {
 //   FIT_EPI_DOT_U   y = A x;  q0,q1 = sum conj(u) * y           (BiCGStab <r^, v>)
 //   FIT_EPI_DOT_TS  y = A x;  q0,q1 = sum conj(y) * x, q2 = sum |y|^2   (<t, s>, <t, t>)
 //   FIT_EPI_RESID   y = u - A x (u = b);  q2 = sum |y|^2        (true residual and its norm)
+//   FIT_EPI_DOT_XY  y = A x;  q0,q1 = sum x * y (unconjugated)  (COCG (p, A p))
 // Systems whose status[b] != 0 are skipped entirely (no write, no partial).
-enum { FIT_EPI_NONE = 0, FIT_EPI_DOT_U = 1, FIT_EPI_DOT_TS = 2, FIT_EPI_RESID = 3 };
+enum { FIT_EPI_NONE = 0, FIT_EPI_DOT_U = 1, FIT_EPI_DOT_TS = 2, FIT_EPI_RESID = 3, FIT_EPI_DOT_XY = 4 };
 struct fit_epi {
   int mode = FIT_EPI_NONE;
   const void* u = nullptr;
@@ -160,6 +173,24 @@ __host__ __device__ inline double2 operator*(double s, double2 a) { return make_
 template <typename V> __host__ __device__ inline V czero();
 template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+// diag(A(w)) of one unmasked edge w of cell (i, j, k) (Eq. Precond construction on the unsymmetrised
+// operator): the sum of M_nu over the four facets that contain the edge (zero beyond the low walls),
+// minus w^2 M_eps, plus j w M_kappa; coefficients in the padded per-cell layout (row pitch nxp).
+template <typename T>
+__device__ inline double2 fit_jacobi_diag(const T* __restrict__ nu, const T* __restrict__ ek, int i, int j, int k,
+                                          int w, int nxp, int ny, double omega) {
+  auto NU = [&](int a, int bb, int cc, int q) -> double {
+    if (a < 0 || bb < 0 || cc < 0) return 0.0;
+    return (double)nu[3 * (a + (long long)nxp * (bb + (long long)ny * cc)) + q];
+  };
+  double ns;
+  if (w == 0) ns = NU(i, j, k, 1) + NU(i, j, k - 1, 1) + NU(i, j, k, 2) + NU(i, j - 1, k, 2);
+  else if (w == 1) ns = NU(i, j, k, 0) + NU(i, j, k - 1, 0) + NU(i, j, k, 2) + NU(i - 1, j, k, 2);
+  else ns = NU(i, j, k, 0) + NU(i, j - 1, k, 0) + NU(i, j, k, 1) + NU(i - 1, j, k, 1);
+  const long long cp = i + (long long)nxp * (j + (long long)ny * k);
+  return make_double2(ns - omega * omega * (double)ek[6 * cp + w], omega * (double)ek[6 * cp + 3 + w]);
+}
 
 // ------------------------------------------------------------------------------------------------
 // Block sum of NQ per-thread values.  Each thread's value is in T (float for the complex64 path,

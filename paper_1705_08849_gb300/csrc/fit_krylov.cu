@@ -81,6 +81,9 @@ struct P {
   double tiny;       // breakdown threshold for the inner precision
   int stall;         // inner solve stops after this many iterations without a new minimum
   int precond;       // right preconditioner of the inner solve (FIT_PC_*)
+  int pc_every;      // FIT_PC_UNET: Arnoldi steps j with j % pc_every == 0 go through the network
+  const volatile int* abort;  // the grid's abort word (pinned host memory), polled by the loop conditions
+  int* err;                   // the grid's error word: set to 2 when the abort word ends the loops
 };
 
 __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -101,19 +104,18 @@ template <> __device__ inline double2 mkc<double>(double re, double im) { return
 // ------------------------------------------------------------------------------------------------
 // Fixed-order reduction of the per-block partials of one system, then a scalar operation.
 // ------------------------------------------------------------------------------------------------
-template <int NQ, class Op>
-__global__ void __launch_bounds__(256) fin_kernel(const double* __restrict__ part, long long nslots, int stride,
-                                                  Sys* sys, P p, Op op) {
-  const int b = blockIdx.x;
-  if (!op.active(sys[b])) return;
+// All 256 threads of the block call it; thread 0 receives out[0..NQ-1] = sum over the nslots
+// partials pb[s * stride + q] in a fixed order (threads take slots t, t + 256, ..., then a tree).
+// The partials are read through L2 (another block of the same kernel may just have written them).
+template <int NQ>
+__device__ inline void reduce_slots(const double* pb, long long nslots, int stride, double* out) {
   __shared__ double red[256][NQ];
   double acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-  const double* pb = part + (long long)b * nslots * stride;
   for (long long s = threadIdx.x; s < nslots; s += 256)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] += pb[s * stride + q];
+    for (int q = 0; q < NQ; ++q) acc[q] += __ldcg(pb + s * stride + q);
 #pragma unroll
   for (int q = 0; q < NQ; ++q) red[threadIdx.x][q] = acc[q];
   __syncthreads();
@@ -123,11 +125,40 @@ __global__ void __launch_bounds__(256) fin_kernel(const double* __restrict__ par
       for (int q = 0; q < NQ; ++q) red[threadIdx.x][q] += red[threadIdx.x + h][q];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double s[NQ];
+  if (threadIdx.x == 0)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) s[q] = red[0][q];
+    for (int q = 0; q < NQ; ++q) out[q] = red[0][q];
+}
+
+template <int NQ, class Op>
+__global__ void __launch_bounds__(256) fin_kernel(const double* __restrict__ part, long long nslots, int stride,
+                                                  Sys* sys, P p, Op op) {
+  const int b = blockIdx.x;
+  if (!op.active(sys[b])) return;
+  double s[NQ];
+  reduce_slots<NQ>(part + (long long)b * nslots * stride, nslots, stride, s);
+  if (threadIdx.x == 0) op.apply(sys[b], s, p, b);
+}
+
+// The last block of a vector kernel to finish (per system) reduces the partial sums of all blocks and
+// applies the scalar operation, in place of a separate fin_kernel launch.  Every block calls it after
+// fit_block_sum has written its partials; cnt[b] counts the finished blocks of system b and is reset by
+// the last one, so it is zero again for the next launch.
+template <int NQ, class Op>
+__device__ inline void last_block_fin(const double* part, unsigned* cnt, Sys* sys, const P& p, int b, Op op) {
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partials are visible before its arrival is counted
+    last = atomicAdd(&cnt[b], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s[NQ];
+  reduce_slots<NQ>(part + (long long)b * p.nblk * p.pstride, p.nblk, p.pstride, s);
+  if (threadIdx.x == 0) {
     op.apply(sys[b], s, p, b);
+    cnt[b] = 0u;
   }
 }
 
@@ -706,30 +737,12 @@ __global__ void __launch_bounds__(256) k_cocg_start(const double2* __restrict__ 
   fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
 }
 
-// COCG: partials of (p, q) with q = A p (unconjugated)
-template <typename T>
-__global__ void __launch_bounds__(256) k_cocg_pq(const typename cplx<T>::t* __restrict__ pv,
-                                                 const typename cplx<T>::t* __restrict__ q, const Sys* __restrict__ sys,
-                                                 double* part, P p) {
-  using V = typename cplx<T>::t;
-  const int b = blockIdx.y;
-  if (sys[b].inner_status != SYS_RUN) return;
-  const long long off = (long long)b * p.ne;
-  T acc[3] = {T(0), T(0), T(0)};
-  VEC_LOOP(p) {
-    const V a = pv[off + e], c = q[off + e];
-    acc[0] += a.x * c.x - a.y * c.y;
-    acc[1] += a.x * c.y + a.y * c.x;
-  }
-  fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
-}
-
-// COCG: d += alpha p, r -= alpha q; partials (r, D^-1 r), ||r||^2
+// COCG: d += alpha p, r -= alpha q; partials (r, D^-1 r), ||r||^2; the last block applies OpCocgRho
 template <typename T>
 __global__ void __launch_bounds__(256) k_cocg_xr(typename cplx<T>::t* d, const typename cplx<T>::t* __restrict__ pv,
                                                  typename cplx<T>::t* r, const typename cplx<T>::t* __restrict__ q,
-                                                 const typename cplx<T>::t* __restrict__ dinv, const Sys* __restrict__ sys,
-                                                 double* part, P p) {
+                                                 const typename cplx<T>::t* __restrict__ dinv, Sys* sys,
+                                                 double* part, unsigned* cnt, P p) {
   using V = typename cplx<T>::t;
   const int b = blockIdx.y;
   if (sys[b].inner_status != SYS_RUN) return;
@@ -751,6 +764,7 @@ __global__ void __launch_bounds__(256) k_cocg_xr(typename cplx<T>::t* d, const t
     acc[2] += rr.x * rr.x + rr.y * rr.y;
   }
   fit_block_sum<T, 3>(acc, part + PSLOT(p, b));
+  last_block_fin<3>(part, cnt, sys, p, b, OpCocgRho{});
 }
 
 // COCG: p = D^-1 r + beta p
@@ -1196,20 +1210,30 @@ __global__ void k_nusum(const T* __restrict__ nu, int nx, int ny, int nz, int nx
 }
 
 // ---- loop conditions -------------------------------------------------------------------------
+// (it also refreshes the mirrored per-system status words the apply's predicate reads)
 __global__ void k_cond(const Sys* __restrict__ sys, Ctl* ctl, P p, int which, int guard_max,
-                       cudaGraphConditionalHandle h, int use_handle) {
+                       cudaGraphConditionalHandle h, int use_handle, int* mirror_inner, int* mirror_outer) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
-    int st = which == 0 ? sys[b].inner_status : sys[b].outer_status;
-    if (st == SYS_RUN) any = 1;
+    const int si = sys[b].inner_status, so = sys[b].outer_status;
+    mirror_inner[b] = si;
+    mirror_outer[b] = so;
+    if ((which == 0 ? si : so) == SYS_RUN) any = 1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int* guard = which == 0 ? &ctl->inner_guard : &ctl->outer_guard;
     *guard += 1;
-    int v = (any && *guard < guard_max) ? 1 : 0;
+    // the host's abort word ends both loops: read at every outer step and every 64th inner step (a
+    // read of pinned host memory costs about a microsecond)
+    bool stop = false;
+    if (p.abort && (which == 1 || (*guard & 63) == 1) && *p.abort) {
+      stop = true;
+      atomicExch(p.err, 2);
+    }
+    int v = (!stop && any && *guard < guard_max) ? 1 : 0;
     ctl->cond = v;
     if (use_handle) cudaGraphSetConditional(h, v);
   }
@@ -1253,6 +1277,7 @@ struct Work {
   double *h1 = nullptr, *h2 = nullptr, *hn2 = nullptr, *H = nullptr, *G = nullptr, *CS = nullptr, *SN = nullptr, *Y = nullptr;
   Sys* sys = nullptr;
   Ctl* ctl = nullptr;
+  unsigned* cnt = nullptr;  // per system: blocks of a vector kernel finished (last-block reductions)
   std::vector<std::pair<void*, size_t>> allocs;
   ~Work() {
     for (auto& a : allocs) fit_dev_free(g, a.first, a.second);
@@ -1279,7 +1304,7 @@ size_t workspace_bytes(const fit_grid* g, int B, int method, int m, int mixed, i
   bytes += (size_t)B * napply * 4 * 8;
   bytes += (size_t)B * 1216 * 2 * FG_MAXV * 8;
   bytes += (size_t)B * (3 * 2 * FG_MAXV + 2 * (m + 1) * m * 2 + 2 * (m + 1) * 2 + 2 * 2 * m + 2 * FG_MAXV) * 8;
-  return bytes + (size_t)B * sizeof(Sys) + 4096;
+  return bytes + (size_t)B * (sizeof(Sys) + sizeof(unsigned)) + 4096;
 }
 
 fit_status setup(Work& w, int B) {
@@ -1357,9 +1382,11 @@ fit_status setup(Work& w, int B) {
   }
   ALLOC(w.sys, (size_t)B * sizeof(Sys));
   ALLOC(w.ctl, sizeof(Ctl));
+  ALLOC(w.cnt, (size_t)B * sizeof(unsigned));
 #undef ALLOC
   FIT_CHECK_CUDA(cudaMemset(w.sys, 0, (size_t)B * sizeof(Sys)));
   FIT_CHECK_CUDA(cudaMemset(w.ctl, 0, sizeof(Ctl)));
+  FIT_CHECK_CUDA(cudaMemset(w.cnt, 0, (size_t)B * sizeof(unsigned)));
   w.p.B = B;
   w.p.ne = g->ne;
   w.p.nblk = nblk;
@@ -1373,6 +1400,8 @@ fit_status setup(Work& w, int B) {
   // minimum for thousands of iterations before it falls again, so it gets a far longer window
   w.p.stall = (w.method == FIT_COCG || w.method == FIT_COCR) ? 20000 : 1000;
   w.p.precond = w.pc;
+  w.p.abort = g->abort_dev;
+  w.p.err = g->err_dev;
   if (w.pc == FIT_PC_JACOBI || w.pc == FIT_PC_UNET) {
     long long nc = g->ncell;
     if (w.mixed)
@@ -1463,18 +1492,16 @@ struct Seq {
     }
   }
 
-  // one COCG iteration (predicated on inner status): q = A p, then alpha, the x/r update, beta, p
+  // one COCG iteration (predicated on inner status): q = A p with (p, q) from the apply's epilogue,
+  // alpha, the x/r update (its last block computes rho and beta), then p
   template <typename T>
   void cocg_iter(const int* st_inner) {
     using V = typename cplx<T>::t;
-    apply(w.pv, w.v, FIT_EPI_NONE, nullptr, w.inner, st_inner);
-    k_cocg_pq<T><<<vgrid(), 256, 0, s>>>((const V*)w.pv, (const V*)w.v, w.sys, w.part_vec, w.p);
-    check();
-    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocgAlpha{});
+    long long n1 = apply(w.pv, w.v, FIT_EPI_DOT_XY, nullptr, w.inner, st_inner);
+    fin<3>(w.part_apply, n1, 4, OpCocgAlpha{});
     k_cocg_xr<T><<<vgrid(), 256, 0, s>>>((V*)w.d, (const V*)w.pv, (V*)w.rin, (const V*)w.v, (const V*)w.dinv, w.sys,
-                                         w.part_vec, w.p);
+                                         w.part_vec, w.cnt, w.p);
     check();
-    fin<3>(w.part_vec, w.p.nblk, w.p.pstride, OpCocgRho{});
     k_cocg_p<T><<<vgrid(), 256, 0, s>>>((const V*)w.rin, (V*)w.pv, (const V*)w.dinv, w.sys, w.p);
     check();
   }
@@ -1565,10 +1592,10 @@ struct Seq {
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
-    } else if (w.pc == FIT_PC_UNET && (j & 1)) {
-      // odd Arnoldi steps use the Jacobi term alone: the flexible method may vary the preconditioner
-      // per step, and with plain-Jacobi directions in the basis the residual minimisation never
-      // depends only on the network's directions
+    } else if (w.pc == FIT_PC_UNET && (j % w.p.pc_every) != 0) {
+      // the other Arnoldi steps use the Jacobi term alone: the flexible method may vary the
+      // preconditioner per step, and with plain-Jacobi directions in the basis the residual
+      // minimisation never depends only on the network's directions
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
@@ -1633,8 +1660,10 @@ struct Seq {
     }
   }
 
+  int* mirror_inner = nullptr;  // per-system status words for the apply's predicate
+  int* mirror_outer = nullptr;
   void cond(int which, int guard_max, cudaGraphConditionalHandle h, int use_handle) {
-    k_cond<<<1, 256, 0, s>>>(w.sys, w.ctl, w.p, which, guard_max, h, use_handle);
+    k_cond<<<1, 256, 0, s>>>(w.sys, w.ctl, w.p, which, guard_max, h, use_handle, mirror_inner, mirror_outer);
     check();
   }
 };
@@ -1658,6 +1687,8 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
   if ((st = w.alloc((void**)&st_inner, w.p.B * sizeof(int))) != FIT_OK) return st;
   if ((st = w.alloc((void**)&st_outer, w.p.B * sizeof(int))) != FIT_OK) return st;
   Seq q{w, rhs, x, s};
+  q.mirror_inner = st_inner;
+  q.mirror_outer = st_outer;
   q.hist = hist;
   q.hist_len = hist_len;
   q.hist_every = hist_every;
@@ -1705,7 +1736,6 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
       if (bicg) {
         for (int it = 0; it < max_inner_guard; ++it) {
           q.loop_iter<T>(st_inner);
-          mirror(s);
           if (it % 100 == 99) dump("bicg it", it + 1);
           q.cond(0, max_inner_guard, 0, 0);
           FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -1716,7 +1746,6 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
       } else {
         for (int j = 0; j < w.m; ++j) {
           q.fg_step<T>(j, st_inner);
-          mirror(s);
           dump("fg step", j);
           q.cond(0, max_inner_guard, 0, 0);
           FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -1727,7 +1756,6 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
         q.fg_finish<T>();
       }
       q.outer_tail<T>(st_outer);
-      mirror(s);
       dump("outer", outer);
       q.cond(1, max_outer_guard, 0, 0);
       FIT_CHECK_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -1810,7 +1838,6 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
       if (result != FIT_OK) break;
       q.s = s_inner;
       q.loop_iter<T>(st_inner);
-      mirror(s_inner);
       q.cond(0, max_inner_guard, h_inner, 1);
       cudaGraph_t tmp;
       fail(cudaStreamEndCapture(s_inner, &tmp), "end inner");
@@ -1823,7 +1850,6 @@ fit_status run_batch(Work& w, const double2* rhs, double2* x, cudaStream_t s, in
       q.fg_finish<T>();
     }
     q.outer_tail<T>(st_outer);
-    mirror(s_outer);
     q.cond(1, max_outer_guard, h_outer, 1);
     cudaGraph_t tmp2;
     fail(cudaStreamEndCapture(s_outer, &tmp2), "end outer");
@@ -1860,22 +1886,14 @@ __global__ void k_jacobi_apply(const typename cplx<T>::t* __restrict__ x, typena
     const long long c = e / 3;
     const int q = (int)(e - 3 * c);
     const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
-    auto NU = [&](int a, int bb, int cc, int w) -> double {
-      if (a < 0 || bb < 0 || cc < 0) return 0.0;
-      return (double)nu[3 * (a + (long long)nxp * (bb + (long long)ny * cc)) + w];
-    };
     const long long cp = i + (long long)nxp * (j + (long long)ny * k);
     const auto xv = x[t];
     typename cplx<T>::t o;
     if ((mask[cp] >> q) & 1) {
       o = xv;
     } else {
-      double ns;
-      if (q == 0) ns = NU(i, j, k, 1) + NU(i, j, k - 1, 1) + NU(i, j, k, 2) + NU(i, j - 1, k, 2);
-      else if (q == 1) ns = NU(i, j, k, 0) + NU(i, j, k - 1, 0) + NU(i, j, k, 2) + NU(i - 1, j, k, 2);
-      else ns = NU(i, j, k, 0) + NU(i, j - 1, k, 0) + NU(i, j, k, 1) + NU(i - 1, j, k, 1);
-      const double w = omega[b];
-      const double dr = ns - w * w * (double)ek[6 * cp + q], di = w * (double)ek[6 * cp + 3 + q];
+      const double2 dg = fit_jacobi_diag<T>(nu, ek, i, j, k, q, nxp, ny, omega[b]);
+      const double dr = dg.x, di = dg.y;
       const double den = (dr * dr + di * di) / out_scale;
       o.x = (T)((xv.x * dr + xv.y * di) / den);
       o.y = (T)((xv.y * dr - xv.x * di) / den);
@@ -1891,6 +1909,7 @@ fit_status fit_jacobi(fit_grid* g, int nbatch, const double* omega, const void* 
                       void* stream) {
   FIT_REQUIRE(g && omega && x && y && nbatch >= 1, "fit_jacobi: bad argument");
   FIT_REQUIRE(g->has_materials, "fit_jacobi: materials not set");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
   double* om = nullptr;
   FIT_CHECK_CUDA(cudaMallocAsync((void**)&om, nbatch * sizeof(double), s));
@@ -1923,6 +1942,7 @@ void fit_solve_opts_default(fit_solve_opts* o) {
   o->history = nullptr;
   o->history_len = 0;
   o->history_every = 1;
+  o->pc_every = 2;
 }
 
 fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rhs, void* x, double tol,
@@ -1951,8 +1971,10 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
   FIT_REQUIRE(o.max_iter >= 1 && o.max_outer >= 1, "fit_solve: iteration caps must be >= 1");
   FIT_REQUIRE(o.inner_tol > 0 && o.inner_tol < 1, "fit_solve: inner_tol must be in (0, 1)");
   FIT_REQUIRE(!o.history || (o.history_len >= 1 && o.history_every >= 1), "fit_solve: bad history options");
+  FIT_REQUIRE(o.pc_every >= 1, "fit_solve: pc_every must be >= 1");
   FIT_REQUIRE(!o.history || o.batch == 0 || o.batch >= nfreq, "fit_solve: history needs all systems in one batch");
   for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(isfinite(omega[f]), "fit_solve: omega must be finite");
+  if (fit_check_abort(g, "fit_solve") != FIT_OK) return FIT_ETIMEOUT;
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)o.stream;
   const int mixed = o.precision == FIT_SOLVE_MIXED;
@@ -1983,6 +2005,7 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
     w.p.inner_tol = o.inner_tol;
     w.p.max_iter = o.max_iter;
     w.p.max_outer = o.max_outer;
+    w.p.pc_every = o.pc_every;
     FIT_CHECK_CUDA(cudaMemcpyAsync(w.omega, omega + f0, nb * sizeof(double), cudaMemcpyHostToDevice, s));
     const double2* rb = (const double2*)rhs + (size_t)f0 * g->ne;
     double2* xb = (double2*)x + (size_t)f0 * g->ne;
@@ -2002,6 +2025,13 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
     if (st != FIT_OK) return st;
     FIT_CHECK_CUDA(cudaStreamSynchronize(s));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    // a bounded wait that ran out (apply or network kernels) or the abort word ends the solve: the
+    // reports of this batch are still filled, later batches are not run
+    fit_status dev_err = fit_take_device_error(g);
+    if (dev_err == FIT_OK && w.pc == FIT_PC_UNET && fit_unet_take_timeout()) {
+      fit_set_error("fit_solve: a bounded wait in a learned-preconditioner convolution ran out");
+      dev_err = FIT_ETIMEOUT;
+    }
     hs.resize(nb);
     FIT_CHECK_CUDA(cudaMemcpy(hs.data(), w.sys, nb * sizeof(Sys), cudaMemcpyDeviceToHost));
     for (int b = 0; b < nb; ++b) {
@@ -2024,6 +2054,7 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
         r.snapshots = y.hist;
       }
     }
+    if (dev_err != FIT_OK) return dev_err;
   }
   return overall;
 }

@@ -21,7 +21,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kMaxDevices] = {};
 
-// once per device, with that device current: look up the array's device address
+// once per device, with that device current: look up the array's device address.  The cached address
+// belongs to the device's primary context; a cudaDeviceReset of the device would make it stale, which is
+// why the header rules out calls after such a reset.
 fit_status noalloc_scratch(int device, double** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (device < 0 || device >= kMaxDevices) {
@@ -55,6 +57,7 @@ extern "C" fit_status fit_apply_noalloc(fit_grid* g, int nbatch, const double* o
   FIT_REQUIRE(prec == FIT_C64 || prec == FIT_C128, "fit_apply_noalloc: unknown precision");
   FIT_REQUIRE(g->has_materials, "fit_apply_noalloc: materials not set");
   for (int b = 0; b < nbatch; ++b) FIT_REQUIRE(isfinite(omega[b]), "fit_apply_noalloc: omega must be finite");
+  if (fit_check_abort(g, "fit_apply_noalloc") != FIT_OK) return FIT_ETIMEOUT;
   const size_t vbytes = (size_t)g->ne * (prec == FIT_C64 ? sizeof(float2) : sizeof(double2)) * nbatch;
   const char* xb = (const char*)x;
   const char* yb = (const char*)y;

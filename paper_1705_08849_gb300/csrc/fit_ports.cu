@@ -69,6 +69,7 @@ fit_status fit_port_rhs(fit_grid* g, int nfreq, const double* omega, int nedge, 
   FIT_REQUIRE(std::isfinite(current), "fit_port_rhs: current must be finite");
   for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(std::isfinite(omega[f]), "fit_port_rhs: omega must be finite");
   for (int q = 0; q < nedge; ++q) FIT_REQUIRE(edges[q] >= 0 && edges[q] < g->ne, "fit_port_rhs: edge out of range");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));  // temporaries and kernels on the grid's device
   cudaStream_t s = (cudaStream_t)stream;
   FIT_CHECK_CUDA(cudaMemsetAsync(b, 0, (size_t)nfreq * g->ne * sizeof(double2), s));
   if (nedge == 0) {
@@ -100,6 +101,7 @@ fit_status fit_probe_voltages(fit_grid* g, int nfreq, const void* x, int nprobe,
   FIT_REQUIRE(nedge == 0 || (edges && signs), "fit_probe_voltages: null edge list");
   for (int k = 0; k < nedge; ++k)
     FIT_REQUIRE(edges[k] >= 0 && edges[k] < g->ne, "fit_probe_voltages: edge out of range");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));  // temporaries and kernels on the grid's device
   cudaStream_t s = (cudaStream_t)stream;
   FitDevTmp tmp(g);
   void *d_off, *d_e, *d_s, *d_v;
@@ -200,6 +202,7 @@ fit_status fit_z_parameters(fit_grid* g, int nfreq, const double* omega, int npo
     o = *opts;
   else
     fit_solve_opts_default(&o);
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
   // one batch of nport * nfreq systems: system (j, f) at j * nfreq + f is port j excited alone at omega_f
   const size_t vbytes = (size_t)nsys * g->ne * sizeof(double2);
   FitDevTmp tmp(g);

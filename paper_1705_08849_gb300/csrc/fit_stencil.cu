@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(256) apply_generic_kernel(ApplyArgs<T> a, fit_
           V u = ((const V*)epi.u)[(long long)b * a.ne + 3 * c + q];
           out = u - out;
           acc[2] += out.x * out.x + out.y * out.y;
+        } else if (EPI == FIT_EPI_DOT_XY) {
+          acc[0] += xv.x * out.x - xv.y * out.y;  // x * y, unconjugated
+          acc[1] += xv.x * out.y + xv.y * out.x;
         }
         y[3 * c + q] = out;
       }
@@ -167,6 +170,7 @@ static fit_status launch_generic(fit_grid* g, int nbatch, const double* omega_de
     case FIT_EPI_DOT_U: apply_generic_kernel<T, FIT_EPI_DOT_U><<<grid, block, 0, s>>>(a, e); break;
     case FIT_EPI_DOT_TS: apply_generic_kernel<T, FIT_EPI_DOT_TS><<<grid, block, 0, s>>>(a, e); break;
     case FIT_EPI_RESID: apply_generic_kernel<T, FIT_EPI_RESID><<<grid, block, 0, s>>>(a, e); break;
+    case FIT_EPI_DOT_XY: apply_generic_kernel<T, FIT_EPI_DOT_XY><<<grid, block, 0, s>>>(a, e); break;
     default: fit_set_error("unknown apply epilogue"); return FIT_EINVAL;
   }
   FIT_CHECK_CUDA(cudaGetLastError());

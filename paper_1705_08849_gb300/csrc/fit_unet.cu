@@ -451,6 +451,75 @@ __global__ void pack_target_kernel(const double2* __restrict__ e, double scale, 
   }
 }
 
+// ---- training pairs ------------------------------------------------------------------------------
+// The partial sums of ||r||^2 written by the apply's residual epilogue (slot q2), summed in a fixed
+// order by one block: out[0] = ||r||^2.
+__global__ void __launch_bounds__(256) pair_norm_kernel(const double* __restrict__ part, long long nslots, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long q = threadIdx.x; q < nslots; q += 256) acc += part[4 * q + 2];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// pair[c][0..5] = r / rms, pair[c][6..11] = ((x* - x_k) - D^-1 r) / (s rms), both bf16 and zero on masked
+// edges; rms = sqrt(||r||^2 / n_e), D the SI Jacobi diagonal (Eq. Precond)
+__global__ void pair_pack_kernel(const double2* __restrict__ r, const double2* __restrict__ xk,
+                                 const double2* __restrict__ xs, const double* __restrict__ nrm2, const double* nu,
+                                 const double* ek, const uint8_t* __restrict__ mask, double omega, int nx, int ny, int nxp,
+                                 long long ncell, double s, bf16* pair) {
+  const double rms = sqrt(nrm2[0] / (3.0 * (double)ncell));
+  const double ir = rms > 0.0 ? 1.0 / rms : 0.0, it = rms > 0.0 ? 1.0 / (s * rms) : 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
+    __align__(16) bf16 v[12];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      double2 in = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+      if (!((m >> w) & 1)) {
+        const double2 rr = r[3 * c + w], a = xk[3 * c + w], b = xs[3 * c + w];
+        const double2 d = fit_jacobi_diag<double>(nu, ek, i, j, k, w, nxp, ny, omega);
+        const double den = d.x * d.x + d.y * d.y;
+        const double2 dr = make_double2((rr.x * d.x + rr.y * d.y) / den, (rr.y * d.x - rr.x * d.y) / den);
+        in = make_double2(rr.x * ir, rr.y * ir);
+        t = make_double2((b.x - a.x - dr.x) * it, (b.y - a.y - dr.y) * it);
+      }
+      v[2 * w] = __float2bfloat16((float)in.x);
+      v[2 * w + 1] = __float2bfloat16((float)in.y);
+      v[6 + 2 * w] = __float2bfloat16((float)t.x);
+      v[6 + 2 * w + 1] = __float2bfloat16((float)t.y);
+    }
+    uint32_t* dst = reinterpret_cast<uint32_t*>(pair + 12 * c);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(v);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) dst[q] = src[q];
+  }
+}
+
+// in16[c] = base16[c] with channels 0..5 replaced by the pair's residual channels; target6 = FP32 of the
+// pair's target channels
+__global__ void pair_sample_kernel(const bf16* __restrict__ pair, const bf16* __restrict__ base16, bf16* in16,
+                                   float* target6, long long ncell) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    __align__(16) bf16 v[16];
+    *reinterpret_cast<uint4*>(v) = reinterpret_cast<const uint4*>(base16 + 16 * c)[0];
+    *reinterpret_cast<uint4*>(v + 8) = reinterpret_cast<const uint4*>(base16 + 16 * c)[1];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      v[q] = pair[12 * c + q];
+      target6[6 * c + q] = __bfloat162float(pair[12 * c + 6 + q]);
+    }
+    reinterpret_cast<uint4*>(in16 + 16 * c)[0] = *reinterpret_cast<uint4*>(v);
+    reinterpret_cast<uint4*>(in16 + 16 * c)[1] = *reinterpret_cast<uint4*>(v + 8);
+  }
+}
+
 }  // namespace
 
 // Used by the solver: z = scale_out * U(scale_in * v) for one complex64 vector (pack, forward,
@@ -465,6 +534,16 @@ fit_status fit_unet_apply_vec(fit_unet* u, const fit_grid* g, const void* v, voi
                                                   (const float2*)dinv, (const float2*)v);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
+}
+
+int fit_unet_take_timeout() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, unet::g_conv_timeout, sizeof(int)) != cudaSuccess) return 0;
+  if (v) {
+    const int zero = 0;
+    (void)cudaMemcpyToSymbol(unet::g_conv_timeout, &zero, sizeof(int));
+  }
+  return v;
 }
 
 fit_status fit_unet_prepare(fit_unet* u, const fit_grid* g, cudaStream_t s) {
@@ -560,6 +639,10 @@ fit_status fit_unet_backward(fit_unet* u, int nx, int ny, int nz, const void* in
   UCK(alloc_acts(u, nx, ny, nz));
   UCK(forward(u, (const bf16*)in16, s));
   UCK(loss_and_grad(u, target6, loss, s));
+  if (loss && fit_unet_take_timeout()) {  // the loss read-back synchronised the forward pass
+    fit_set_error("fit_unet_backward: a bounded wait in a tensor-core convolution ran out");
+    return FIT_ETIMEOUT;
+  }
   UCK(backward(u, (const bf16*)in16, s));
   if (grad) FIT_CHECK_CUDA(cudaMemcpyAsync(grad, u->g, u->nparams * sizeof(float), cudaMemcpyDeviceToDevice, s));
   return FIT_OK;
@@ -581,6 +664,7 @@ fit_status fit_unet_train_step(fit_unet* u, int nx, int ny, int nz, const void* 
 
 fit_status fit_unet_pack(const fit_grid* g, const void* r, double scale, void* out16, void* stream) {
   FIT_REQUIRE(g && r && out16, "fit_unet_pack: null argument");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
   pack_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>((const float2*)r, (float)scale,
                                                                     (const bf16*)g->mat16, (bf16*)out16, g->ncell);
   FIT_CHECK_CUDA(cudaGetLastError());
@@ -589,6 +673,7 @@ fit_status fit_unet_pack(const fit_grid* g, const void* r, double scale, void* o
 
 fit_status fit_unet_pack_target(const fit_grid* g, const void* e, double scale, float* out6, void* stream) {
   FIT_REQUIRE(g && e && out6, "fit_unet_pack_target: null argument");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
   pack_target_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>((const double2*)e, scale, g->mask, g->nx,
                                                                            g->ny, g->nxp, out6, g->ncell);
   FIT_CHECK_CUDA(cudaGetLastError());
@@ -597,8 +682,181 @@ fit_status fit_unet_pack_target(const fit_grid* g, const void* e, double scale, 
 
 fit_status fit_unet_unpack(const fit_grid* g, const float* y6, double scale, void* z, void* stream) {
   FIT_REQUIRE(g && y6 && z, "fit_unet_unpack: null argument");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
   unpack_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>(y6, (float)scale, g->mask, g->nx, g->ny, g->nxp,
                                                                       (float2*)z, g->ncell, nullptr, nullptr);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+// ---- single layers (the kernels the network runs, one at a time) ---------------------------------
+namespace {
+bool conv_shape_ok(int cin, int cout) {  // the 3x3x3 layer shapes of the network
+  static const int ok[][2] = {{16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64}, {64, 32}, {32, 16}};
+  for (auto& p : ok)
+    if (p[0] == cin && p[1] == cout) return true;
+  return false;
+}
+// bf16 forward copy W[tap][co][ci] and dgrad copy W[26 - tap][ci][co] of FP32 weights, in stream-ordered
+// scratch that the caller frees with cudaFreeAsync
+fit_status layer_weights(const float* w, int cin, int cout, bf16** wf, bf16** wt, cudaStream_t s) {
+  const size_t wb = (size_t)27 * cin * cout * sizeof(bf16);
+  FIT_CHECK_CUDA(cudaMallocAsync((void**)wf, wb, s));
+  FIT_CHECK_CUDA(cudaMallocAsync((void**)wt, wb, s));
+  unet::conv_weights_bf16_kernel<<<nblocks(27LL * cin * cout), 256, 0, s>>>(w, *wf, *wt, cout, cin);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+}  // namespace
+
+fit_status fit_unet_conv3(int nx, int ny, int nz, int cin, int cout, const void* in, const float* w, const float* bias,
+                          int relu, void* out, void* stream) {
+  FIT_REQUIRE(in && w && out && nx >= 1 && ny >= 1 && nz >= 1, "fit_unet_conv3: bad argument");
+  FIT_REQUIRE(conv_shape_ok(cin, cout), "fit_unet_conv3: (cin, cout) is not a layer shape of the network");
+  cudaStream_t s = (cudaStream_t)stream;
+  bf16 *wf = nullptr, *wt = nullptr;
+  UCK(layer_weights(w, cin, cout, &wf, &wt, s));
+  fit_status st = conv3((const bf16*)in, cin, nullptr, 0, wf, bias, (bf16*)out, cout, nullptr, 0, nx, ny, nz,
+                        relu ? 1 : 0, s);
+  cudaFreeAsync(wf, s);
+  cudaFreeAsync(wt, s);
+  return st;
+}
+
+fit_status fit_unet_conv3_dgrad(int nx, int ny, int nz, int cin, int cout, const void* dout, const float* w, void* din,
+                                void* stream) {
+  FIT_REQUIRE(dout && w && din && nx >= 1 && ny >= 1 && nz >= 1, "fit_unet_conv3_dgrad: bad argument");
+  FIT_REQUIRE(conv_shape_ok(cin, cout), "fit_unet_conv3_dgrad: (cin, cout) is not a layer shape of the network");
+  cudaStream_t s = (cudaStream_t)stream;
+  bf16 *wf = nullptr, *wt = nullptr;
+  UCK(layer_weights(w, cin, cout, &wf, &wt, s));
+  fit_status st = conv3((const bf16*)dout, cout, nullptr, 0, wt, nullptr, (bf16*)din, cin, nullptr, 0, nx, ny, nz, 0, s);
+  cudaFreeAsync(wf, s);
+  cudaFreeAsync(wt, s);
+  return st;
+}
+
+fit_status fit_unet_conv3_wgrad(int nx, int ny, int nz, int cin, int cout, const void* in, const void* dout, float* dw,
+                                float* db, void* stream) {
+  FIT_REQUIRE(in && dout && dw && nx >= 1 && ny >= 1 && nz >= 1, "fit_unet_conv3_wgrad: bad argument");
+  FIT_REQUIRE(conv_shape_ok(cin, cout), "fit_unet_conv3_wgrad: (cin, cout) is not a layer shape of the network");
+  cudaStream_t s = (cudaStream_t)stream;
+  FIT_CHECK_CUDA(cudaMemsetAsync(dw, 0, (size_t)27 * cin * cout * sizeof(float), s));
+  if (db) FIT_CHECK_CUDA(cudaMemsetAsync(db, 0, (size_t)cout * sizeof(float), s));
+  unet::WgradArgs a;
+  a.dy = (const bf16*)dout;
+  a.x1 = (const bf16*)in;
+  a.x2 = nullptr;
+  a.c1 = cin;
+  a.c2 = 0;
+  a.cout = cout;
+  a.dw = dw;
+  a.db = db;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.chunk = 4096;
+  const long long nv = (long long)nx * ny * nz;
+  unet::conv3_wgrad_kernel<<<dim3((unsigned)((nv + 4095) / 4096), 27), 256, 0, s>>>(a);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_tconv(int mx, int my, int mz, int cin, int cout, const void* in, const float* w, const float* b,
+                          void* out, void* stream) {
+  FIT_REQUIRE(in && w && b && out && mx >= 1 && my >= 1 && mz >= 1, "fit_unet_tconv: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cin == 64 && cout == 32) return tconv_fwd<64, 32>((const bf16*)in, w, b, (bf16*)out, mx, my, mz, s);
+  if (cin == 32 && cout == 16) return tconv_fwd<32, 16>((const bf16*)in, w, b, (bf16*)out, mx, my, mz, s);
+  fit_set_error("fit_unet_tconv: (cin, cout) must be (64, 32) or (32, 16)");
+  return FIT_EINVAL;
+}
+
+fit_status fit_unet_tconv_backward(int mx, int my, int mz, int cin, int cout, const void* in, const void* dout,
+                                   const float* w, void* din, float* dw, float* db, void* stream) {
+  FIT_REQUIRE(in && dout && w && din && dw && db && mx >= 1 && my >= 1 && mz >= 1,
+              "fit_unet_tconv_backward: bad argument");
+  FIT_REQUIRE((cin == 64 && cout == 32) || (cin == 32 && cout == 16),
+              "fit_unet_tconv_backward: (cin, cout) must be (64, 32) or (32, 16)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nx = 2 * mx, ny = 2 * my, nz = 2 * mz;
+  const long long nc = (long long)mx * my * mz;
+  FIT_CHECK_CUDA(cudaMemsetAsync(dw, 0, (size_t)8 * cin * cout * sizeof(float), s));
+  FIT_CHECK_CUDA(cudaMemsetAsync(db, 0, (size_t)cout * sizeof(float), s));
+  unet::tconv_bwd_data_kernel<<<nblocks(nc * cin), 256, 0, s>>>((const bf16*)dout, w, (bf16*)din, cin, cout, nx, ny, nz);
+  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((nc + 1023) / 1024), 8), 256, 0, s>>>(
+      (const bf16*)in, (const bf16*)dout, dw, db, cin, cout, nx, ny, nz, 1024);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_head(long long nvox, const void* in, const float* w, const float* b, float* out, void* stream) {
+  FIT_REQUIRE(in && w && b && out && nvox >= 1 && nvox < (1LL << 31), "fit_unet_head: bad argument");
+  unet::head_fwd_kernel<16, 6><<<(unsigned)((nvox + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      (const bf16*)in, w, b, out, (int)nvox);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_head_backward(long long nvox, const void* in, const float* dout, const float* w, void* din,
+                                  float* dw, float* db, void* stream) {
+  FIT_REQUIRE(in && dout && w && din && dw && db && nvox >= 1, "fit_unet_head_backward: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  FIT_CHECK_CUDA(cudaMemsetAsync(dw, 0, 6 * 16 * sizeof(float), s));
+  FIT_CHECK_CUDA(cudaMemsetAsync(db, 0, 6 * sizeof(float), s));
+  unet::head_bwd_weight_kernel<<<(unsigned)((nvox + 4095) / 4096), 256, 0, s>>>((const bf16*)in, dout, dw, db, 16, 6,
+                                                                                nvox);
+  unet::head_bwd_data_kernel<<<nblocks(nvox * 16), 256, 0, s>>>(dout, w, (bf16*)din, 16, 6, nvox);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, const void* xstar, const void* b,
+                                  void* pair, double* rms_out, void* stream) {
+  FIT_REQUIRE(g && xk && xstar && b && pair, "fit_unet_training_pair: null argument");
+  FIT_REQUIRE(g->has_materials, "fit_unet_training_pair: materials not set");
+  FIT_REQUIRE(isfinite(omega), "fit_unet_training_pair: omega must be finite");
+  FIT_REQUIRE((((uintptr_t)pair) & 3) == 0, "fit_unet_training_pair: pair must be 4-byte aligned");
+  if (fit_check_abort(g, "fit_unet_training_pair") != FIT_OK) return FIT_ETIMEOUT;
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  FitDevTmp tmp(g);
+  void *d_om = nullptr, *r = nullptr, *part = nullptr, *nrm = nullptr;
+  const long long nslots = fit_apply_partials(g, FIT_C128);
+  fit_status st;
+  if ((st = tmp.copy(&d_om, &omega, sizeof(double), s)) != FIT_OK) return st;
+  if ((st = tmp.alloc(&r, (size_t)g->ne * sizeof(double2))) != FIT_OK) return st;
+  if ((st = tmp.alloc(&part, (size_t)nslots * 4 * sizeof(double))) != FIT_OK) return st;
+  if ((st = tmp.alloc(&nrm, sizeof(double))) != FIT_OK) return st;
+  // r = b - A x_k in FP64 with its squared norm from the residual epilogue
+  fit_epi e;
+  e.mode = FIT_EPI_RESID;
+  e.u = b;
+  e.part = (double*)part;
+  if ((st = fit_launch_apply(g, 1, (const double*)d_om, xk, r, FIT_C128, 1.0, s, &e)) != FIT_OK) return st;
+  if (e.nslots > nslots) {
+    fit_set_error("fit_unet_training_pair: the apply wrote more partial slots than were allocated");
+    return FIT_ECUDA;
+  }
+  pair_norm_kernel<<<1, 256, 0, s>>>((const double*)part, e.nslots, (double*)nrm);
+  pair_pack_kernel<<<nblocks(g->ncell), 256, 0, s>>>((const double2*)r, (const double2*)xk, (const double2*)xstar,
+                                                     (const double*)nrm, g->nu64, g->ek64, g->mask, omega, g->nx,
+                                                     g->ny, g->nxp, g->ncell, g->coef_scale, (bf16*)pair);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  double n2 = 0.0;
+  FIT_CHECK_CUDA(cudaMemcpyAsync(&n2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FIT_CHECK_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed on return
+  if (rms_out) *rms_out = sqrt(n2 / (double)g->ne);
+  return fit_take_device_error(g);
+}
+
+fit_status fit_unet_pair_sample(long long ncell, const void* pair, const void* base16, void* in16, float* target6,
+                                void* stream) {
+  FIT_REQUIRE(pair && base16 && in16 && target6 && ncell >= 1, "fit_unet_pair_sample: bad argument");
+  FIT_REQUIRE(((((uintptr_t)base16) | ((uintptr_t)in16)) & 15) == 0,
+              "fit_unet_pair_sample: base16 and in16 must be 16-byte aligned");
+  pair_sample_kernel<<<nblocks(ncell), 256, 0, (cudaStream_t)stream>>>((const bf16*)pair, (const bf16*)base16,
+                                                                        (bf16*)in16, target6, ncell);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }

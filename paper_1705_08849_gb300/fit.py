@@ -36,7 +36,8 @@ class fit_solve_opts(ct.Structure):
     _fields_ = [("method", ct.c_int), ("restart", ct.c_int), ("precision", ct.c_int), ("max_iter", ct.c_int),
                 ("max_outer", ct.c_int), ("inner_tol", ct.c_double), ("batch", ct.c_int),
                 ("use_graph", ct.c_int), ("precond", ct.c_int), ("stream", ct.c_void_p),
-                ("history", ct.c_void_p), ("history_len", ct.c_int), ("history_every", ct.c_int)]
+                ("history", ct.c_void_p), ("history_len", ct.c_int), ("history_every", ct.c_int),
+                ("pc_every", ct.c_int)]
 
 
 class fit_solve_report(ct.Structure):
@@ -112,6 +113,25 @@ def lib():
                                        pd, ct.POINTER(fit_solve_report)]
         for name in ("fit_port_rhs", "fit_probe_voltages", "fit_z_to_s", "fit_z_parameters"):
             getattr(L, name).restype = ct.c_int
+        ll = ct.c_longlong
+        L.fit_unet_conv3.argtypes = [i, i, i, i, i, vp, vp, vp, i, vp, vp]
+        L.fit_unet_conv3_dgrad.argtypes = [i, i, i, i, i, vp, vp, vp, vp]
+        L.fit_unet_conv3_wgrad.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
+        L.fit_unet_tconv.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
+        L.fit_unet_tconv_backward.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.fit_unet_head.argtypes = [ll, vp, vp, vp, vp, vp]
+        L.fit_unet_head_backward.argtypes = [ll, vp, vp, vp, vp, vp, vp, vp]
+        for name in ("fit_unet_conv3", "fit_unet_conv3_dgrad", "fit_unet_conv3_wgrad", "fit_unet_tconv",
+                     "fit_unet_tconv_backward", "fit_unet_head", "fit_unet_head_backward"):
+            getattr(L, name).restype = ct.c_int
+        L.fit_unet_training_pair.argtypes = [vp, d, vp, vp, vp, vp, ct.POINTER(ct.c_double), vp]
+        L.fit_unet_training_pair.restype = ct.c_int
+        L.fit_unet_pair_sample.argtypes = [ll, vp, vp, vp, vp, vp]
+        L.fit_unet_pair_sample.restype = ct.c_int
+        L.fit_set_abort.argtypes = [vp, i]
+        L.fit_set_abort.restype = ct.c_int
+        L.fit_sync.argtypes = [vp, vp]
+        L.fit_sync.restype = ct.c_int
         L.fit_last_error.argtypes = []
         L.fit_last_error.restype = ct.c_char_p
         for name in ("fit_grid_create", "fit_set_materials", "fit_set_material_matrices", "fit_apply", "fit_solve",
@@ -246,7 +266,8 @@ def fit_solve(g, omega, rhs, x, tol, opts=None, **kw):
     reps = (fit_solve_report * nf)()
     st = lib().fit_solve(g, nf, pom, ct.c_void_p(rhs.data_ptr()), ct.c_void_p(x.data_ptr()), float(tol),
                          ct.byref(o), reps)
-    if st not in (FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN, FIT_ENAN):  # per-system outcomes are returned
+    # per-system outcomes, and an abort or a device timeout (the reports are filled), are returned
+    if st not in (FIT_OK, FIT_NOT_CONVERGED, FIT_BREAKDOWN, FIT_ENAN, FIT_ETIMEOUT):
         _check(st, "fit_solve")
     return st, [dict(status=r.status, iterations=r.iterations, outer=r.outer, relres=r.relres, seconds=r.seconds,
                      snapshots=r.snapshots) for r in reps]
@@ -440,9 +461,77 @@ def fit_unet_unpack(g, y6, scale, z, stream=None):
     _check(lib().fit_unet_unpack(g, _ptr(y6), float(scale), _ptr(z), _stream_ptr(stream)), "fit_unet_unpack")
 
 
+def _p(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def fit_unet_conv3(nx, ny, nz, cin, cout, x, w, bias, relu, out, stream=None):
+    """One 3x3x3 conv layer: x bf16 [N, cin], w float32 [27, cout, cin], bias float32 [cout] or None."""
+    _check(lib().fit_unet_conv3(nx, ny, nz, cin, cout, _p(x), _p(w), _p(bias), int(relu), _p(out),
+                                _stream_ptr(stream)), "fit_unet_conv3")
+
+
+def fit_unet_conv3_dgrad(nx, ny, nz, cin, cout, dout, w, din, stream=None):
+    _check(lib().fit_unet_conv3_dgrad(nx, ny, nz, cin, cout, _p(dout), _p(w), _p(din), _stream_ptr(stream)),
+           "fit_unet_conv3_dgrad")
+
+
+def fit_unet_conv3_wgrad(nx, ny, nz, cin, cout, x, dout, dw, db=None, stream=None):
+    _check(lib().fit_unet_conv3_wgrad(nx, ny, nz, cin, cout, _p(x), _p(dout), _p(dw), _p(db), _stream_ptr(stream)),
+           "fit_unet_conv3_wgrad")
+
+
+def fit_unet_tconv(mx, my, mz, cin, cout, x, w, b, out, stream=None):
+    _check(lib().fit_unet_tconv(mx, my, mz, cin, cout, _p(x), _p(w), _p(b), _p(out), _stream_ptr(stream)),
+           "fit_unet_tconv")
+
+
+def fit_unet_tconv_backward(mx, my, mz, cin, cout, x, dout, w, din, dw, db, stream=None):
+    _check(lib().fit_unet_tconv_backward(mx, my, mz, cin, cout, _p(x), _p(dout), _p(w), _p(din), _p(dw), _p(db),
+                                         _stream_ptr(stream)), "fit_unet_tconv_backward")
+
+
+def fit_unet_head(nvox, x, w, b, out, stream=None):
+    _check(lib().fit_unet_head(int(nvox), _p(x), _p(w), _p(b), _p(out), _stream_ptr(stream)), "fit_unet_head")
+
+
+def fit_unet_head_backward(nvox, x, dout, w, din, dw, db, stream=None):
+    _check(lib().fit_unet_head_backward(int(nvox), _p(x), _p(dout), _p(w), _p(din), _p(dw), _p(db),
+                                        _stream_ptr(stream)), "fit_unet_head_backward")
+
+
+def fit_unet_training_pair(g, omega, xk, xstar, b, pair, stream=None):
+    """Build one 12-channel bf16 training pair (residual / rms, Jacobi-missed correction) on the device from
+    the iterate xk of a solve with solution xstar; returns rms(b - A xk)."""
+    rms = ct.c_double()
+    _check(lib().fit_unet_training_pair(g, float(omega), _p(xk), _p(xstar), _p(b), _p(pair), ct.byref(rms),
+                                        _stream_ptr(stream)), "fit_unet_training_pair")
+    return rms.value
+
+
+def fit_unet_pair_sample(ncell, pair, base16, in16, target6, stream=None):
+    _check(lib().fit_unet_pair_sample(int(ncell), _p(pair), _p(base16), _p(in16), _p(target6), _stream_ptr(stream)),
+           "fit_unet_pair_sample")
+
+
 def fit_set_preconditioner(g, net):
     _check(lib().fit_set_preconditioner(g, FIT_PC_UNET, net.h if net is not None else None),
            "fit_set_preconditioner")
+
+
+def fit_set_abort(g, value):
+    """Set (1) or clear (0) the grid's abort word: queued and running fused applies and solves on the
+    grid stop at their next bounded wait or loop test and report FIT_ETIMEOUT."""
+    _check(lib().fit_set_abort(g, int(value)), "fit_set_abort")
+
+
+def fit_sync(g, stream=None):
+    """Synchronise the stream and report (and clear) a device-side failure of this grid's kernels since
+    the last check: returns the status (FIT_OK or FIT_ETIMEOUT) instead of raising for FIT_ETIMEOUT."""
+    st = lib().fit_sync(g, _stream_ptr(stream))
+    if st not in (FIT_OK, FIT_ETIMEOUT):
+        _check(st, "fit_sync")
+    return st
 
 
 def fit_set_hbm_budget(g, nbytes):

@@ -1,16 +1,28 @@
-"""Training of the learned right preconditioner (3D U-Net) on residual -> correction pairs.
+"""Training and evaluation of the learned right preconditioner (3D U-Net) on residual -> correction pairs.
 
-    python -m paper_1705_08849_gb300.train_unet --out weights.bin [--geometries 12] [--steps 3000]
+    python -m paper_1705_08849_gb300.train_unet --out weights.fitw [--geometries 75] [--pairs 20000]
+                                                [--epochs 3] [--eval-n 64]
 
-Pairs come from plain solves: for seeded 64^3 geometries of the layered / conductor-block family
-(fitgen.layered_blocks) at frequencies drawn in 1-10 GHz, fit_solve (complex64 FGMRES(30) + Jacobi
-inside FP64 refinement, tol 1e-7) records the iterate x_k every few refinement steps.  With x* the
-converged solution:
-    r_k = b - A x_k,   e_k = x* - x_k,   input = r_k / rms(r_k) (+ material channels),
-    target = (e_k - D^-1 r_k) / (s rms(r_k))
-so the network learns the part of A^-1 r that the Jacobi term D^-1 r misses, in the units of the
-scaled complex64 operator (s = fit_coef_scale).  Training minimises ||U(in) - target||^2 / ||target||^2
-with Adam on the GPU (the library's own forward and backward kernels).
+Harvest.  For seeded n^3 geometries of the layered / conductor-block family (fitgen.layered_blocks, the
+benchmark workload's material law) at frequencies drawn uniformly in 1-10 GHz, fit_solve (complex64
+FGMRES(30) + Jacobi inside FP64 refinement, tol 1e-7) records the iterate x_k after every refinement step
+(one FGMRES cycle each).  With x* the converged solution, evenly spaced snapshots become pairs built on
+the device by fit_unet_training_pair:
+    r_k = b - A x_k,   input = r_k / rms(r_k) (+ the geometry's material channels),
+    target = ((x* - x_k) - D^-1 r_k) / (s rms(r_k))
+so the network learns the part of A^-1 r that the Jacobi term D^-1 r misses, in the units of the scaled
+complex64 operator (s = fit_coef_scale).  Pairs stay on the GPU as one bf16 shard per geometry
+([pairs, cells, 12], 24 bytes per cell and pair: 6.3 MB per 64^3 pair, about 126 GB for 20 000 pairs,
+inside the 288 GB of HBM), so training never waits on storage.
+
+Training.  Adam (cosine learning rate) on ||U(in) - target||^2 / ||target||^2 with the library's own
+forward and backward kernels, one pair per step in a shuffled order, the parameters with the lowest
+validation loss (held-out geometries) kept.
+
+Evaluation (``evaluate``).  FGMRES(30) with the network (M(v) = D^-1 v + rms(v) U(v / rms(v)) on even
+Arnoldi steps and Jacobi on odd ones, or the network on each cycle's first vector only, the normalised
+true residual the pairs are made of) against FGMRES(30) + Jacobi, plain FGMRES(30) and plain BiCGStab on
+unseen geometries, each to a 1e-8 true residual: iterations, wall time, status.
 
 Checkpoint format: one JSON header line (format, parameter count, training record), then the
 parameters as little-endian float32.
@@ -31,10 +43,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FORMAT = "fit-unet-v1"
+# the checkpoint the benchmark's learned solve loads (trained by this module, see its record)
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_layered64.fitw")
 
 
 def save(net, path, record):
     p = net.get_params()
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
     with open(path, "wb") as fh:
         fh.write((json.dumps({"format": FORMAT, "nparams": int(p.size), "record": record}) + "\n").encode())
         fh.write(p.astype("<f4").tobytes())
@@ -50,16 +65,20 @@ def load(net, path):
     return head
 
 
-def harvest(seeds, n=64, every=6, slots=24, tol=1e-7, fmin=1e9, fmax=10e9, log=print):
-    """Returns a list of (in16, target6) device tensors."""
+def _freq(seed, fmin, fmax):
+    return float(np.random.default_rng(int(seed)).uniform(fmin, fmax))
+
+
+def harvest(seeds, n=64, pairs_per_geometry=270, slots=2400, tol=1e-7, fmin=1e9, fmax=10e9, log=print):
+    """One shard per geometry: dict(seed, f, base16 [cells, 16] bf16, pairs [k, cells, 12] bf16) on the GPU."""
     import torch
 
     import fitgen as G
     from . import fit
-    samples = []
+    shards = []
     for s in seeds:
         case = G.layered_blocks(n=n, seed=int(s))
-        f = float(np.random.default_rng(int(s)).uniform(fmin, fmax))
+        f = _freq(s, fmin, fmax)
         w = 2 * math.pi * f
         t0 = time.time()
         with fit.Grid.from_case(case) as g:
@@ -68,45 +87,56 @@ def harvest(seeds, n=64, every=6, slots=24, tol=1e-7, fmin=1e9, fmax=10e9, log=p
             x = torch.zeros_like(b)
             hist = torch.zeros(slots, ne, dtype=torch.complex128, device="cuda")
             st, rep = g.solve([w], b, x, tol, method=fit.FIT_FGMRES, restart=30, precond=fit.FIT_PC_JACOBI,
-                              max_iter=200000, max_outer=20000, history=hist.data_ptr(), history_len=slots,
-                              history_every=every)
-            sc = fit.fit_coef_scale(g.h)
-            ns = rep[0]["snapshots"]
-            for k in range(ns):
-                xk = hist[k]
-                ax = torch.empty_like(xk)
-                fit.fit_apply(g.h, [w], xk, ax, fit.FIT_C128)
-                r = b - ax
-                dr = torch.empty_like(r)
-                fit.fit_jacobi(g.h, [w], r, dr, fit.FIT_C128)
-                rms = float(torch.linalg.vector_norm(r)) / math.sqrt(ne)
-                if not rms > 0:
-                    continue
-                in16 = torch.empty(ncell, 16, dtype=torch.bfloat16, device="cuda")
-                t6 = torch.empty(ncell, 6, dtype=torch.float32, device="cuda")
-                fit.fit_unet_pack(g.h, r.to(torch.complex64), 1.0 / rms, in16)
-                fit.fit_unet_pack_target(g.h, (x - xk) - dr, 1.0 / (sc * rms), t6)
-                samples.append((in16, t6))
+                              max_iter=30 * slots, max_outer=slots, history=hist.data_ptr(), history_len=slots,
+                              history_every=1)
+            # x* must be the solution: a geometry whose solve did not converge gives no pairs
+            ns = rep[0]["snapshots"] if st == fit.FIT_OK else 0
+            pick = np.unique(np.linspace(0, ns - 1, min(ns, pairs_per_geometry)).round().astype(int)) if ns else []
+            pairs = torch.empty(len(pick), ncell, 12, dtype=torch.bfloat16, device="cuda")
+            for q, k in enumerate(pick):
+                fit.fit_unet_training_pair(g.h, w, hist[int(k)], x, b, pairs[q])
+            del hist
+            base16 = torch.empty(ncell, 16, dtype=torch.bfloat16, device="cuda")
+            fit.fit_unet_pack(g.h, torch.zeros(ne, dtype=torch.complex64, device="cuda"), 1.0, base16)
             torch.cuda.synchronize()
-        log(f"harvest seed {s}: f = {f / 1e9:.2f} GHz, {rep[0]['iterations']} iterations, relres "
-            f"{rep[0]['relres']:.2e}, {ns} snapshots, {time.time() - t0:.1f} s")
-    return samples
+        if len(pick):
+            shards.append(dict(seed=int(s), f=f, base16=base16, pairs=pairs))
+        log(f"harvest seed {s}: f = {f / 1e9:.2f} GHz, {fit.status_str(st)}, {rep[0]['iterations']} iterations, "
+            f"relres {rep[0]['relres']:.2e}, {rep[0]['snapshots']} snapshots -> {len(pick)} pairs, "
+            f"{time.time() - t0:.1f} s")
+    return shards
 
 
-def train(net, samples, n, steps, lr=1e-3, lr_min=1e-4, seed=0, val=None, log=print):
-    """Adam with a cosine learning rate; with validation pairs the parameters with the lowest
-    validation loss seen at the checkpoints (every steps/10) are kept (early stopping)."""
+def _sample(fit, shard, k, in16, t6):
+    fit.fit_unet_pair_sample(in16.shape[0], shard["pairs"][k], shard["base16"], in16, t6)
+
+
+def train(net, shards, n, epochs, lr=1e-3, lr_min=1e-4, seed=0, val=None, checks=10, log=print):
+    """Adam with a cosine learning rate over ``epochs`` passes of the pairs in a shuffled order; with
+    validation shards the parameters with the lowest validation loss at the checkpoints are kept."""
+    import torch
+
+    from . import fit
     rng = np.random.default_rng(seed)
+    index = [(si, k) for si, sh in enumerate(shards) for k in range(sh["pairs"].shape[0])]
+    steps = max(1, int(epochs * len(index)))
+    ncell = n * n * n
+    in16 = torch.empty(ncell, 16, dtype=torch.bfloat16, device="cuda")
+    t6 = torch.empty(ncell, 6, dtype=torch.float32, device="cuda")
     hist = []
     best = (validate(net, val, n), net.get_params()) if val else None
     t0 = time.time()
+    order = []
+    every = max(1, steps // checks)
     for it in range(steps):
-        lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / max(1, steps)))
-        x, t = samples[int(rng.integers(len(samples)))]
-        loss = net.train_step(n, n, n, x, t, lr_t)
-        hist.append(loss)
-        if (it + 1) % max(1, steps // 10) == 0:
-            msg = f"step {it + 1}: train loss (mean of last {steps // 10}) {np.mean(hist[-(steps // 10):]):.4f}"
+        if not order:
+            order = list(rng.permutation(len(index)))
+        si, k = index[order.pop()]
+        lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / steps))
+        _sample(fit, shards[si], k, in16, t6)
+        hist.append(net.train_step(n, n, n, in16, t6, lr_t))
+        if (it + 1) % every == 0:
+            msg = f"step {it + 1}/{steps}: train loss (mean of last {every}) {np.mean(hist[-every:]):.4f}"
             if val:
                 v = validate(net, val, n)
                 msg += f", validation {v:.4f}"
@@ -115,48 +145,113 @@ def train(net, samples, n, steps, lr=1e-3, lr_min=1e-4, seed=0, val=None, log=pr
             log(msg + f", {time.time() - t0:.1f} s")
     if best is not None:
         net.set_params(best[1])
-    return hist
+    return hist, steps
 
 
-def validate(net, samples, n):
+def validate(net, shards, n, per_shard=16):
+    """Mean loss over up to ``per_shard`` evenly spaced pairs of every validation shard."""
     import torch
+
+    from . import fit
+    ncell = n * n * n
+    in16 = torch.empty(ncell, 16, dtype=torch.bfloat16, device="cuda")
+    t6 = torch.empty(ncell, 6, dtype=torch.float32, device="cuda")
     losses = []
-    for x, t in samples:
-        losses.append(net.backward(n, n, n, x, t))
+    for sh in shards:
+        m = sh["pairs"].shape[0]
+        for k in np.unique(np.linspace(0, m - 1, min(m, per_shard)).round().astype(int)):
+            _sample(fit, sh, int(k), in16, t6)
+            losses.append(net.backward(n, n, n, in16, t6))
     torch.cuda.synchronize()
     return float(np.mean(losses))
+
+
+METHODS = {  # label: (fit_solve method, precision, preconditioner[, pc_every])
+    "fgmres30+unet": ("FIT_FGMRES", "FIT_SOLVE_MIXED", "FIT_PC_UNET"),
+    "fgmres30+unet@0": ("FIT_FGMRES", "FIT_SOLVE_MIXED", "FIT_PC_UNET", 30),
+    "fgmres30+jacobi": ("FIT_FGMRES", "FIT_SOLVE_MIXED", "FIT_PC_JACOBI"),
+    "fgmres30": ("FIT_FGMRES", "FIT_SOLVE_MIXED", "FIT_PC_NONE"),
+    "bicgstab": ("FIT_BICGSTAB", "FIT_SOLVE_MIXED", "FIT_PC_NONE"),
+}
+
+
+def evaluate(net, seeds, freqs, n=128, methods=tuple(METHODS), tol=1e-8, max_iter=60000, log=print):
+    """Solve b = -j w j on each unseen geometry and frequency with each method; returns a list of records
+    (seed, f, method, iterations, seconds, relres, status)."""
+    import torch
+
+    import fitgen as G
+    from . import fit
+    out = []
+    for s in seeds:
+        case = G.layered_blocks(n=n, seed=int(s))
+        with fit.Grid.from_case(case) as g:
+            fit.fit_set_preconditioner(g.h, net)
+            j = torch.from_numpy(G.source_vector(case)).cuda()
+            for f in freqs:
+                w = 2 * math.pi * f
+                b = (-1j * w) * j
+                for mname in methods:
+                    spec = METHODS[mname]
+                    meth, prec, pc = (getattr(fit, a) for a in spec[:3])
+                    every = spec[3] if len(spec) > 3 else 2
+                    x = torch.zeros_like(b)
+                    torch.cuda.synchronize()
+                    t0 = time.time()
+                    st, rep = g.solve([w], b, x, tol, method=meth, precision=prec, restart=30, precond=pc,
+                                      max_iter=max_iter, max_outer=max_iter, pc_every=every)
+                    torch.cuda.synchronize()
+                    r = dict(seed=int(s), f=f, method=mname, iterations=rep[0]["iterations"],
+                             seconds=time.time() - t0, relres=rep[0]["relres"], status=fit.status_str(rep[0]["status"]))
+                    out.append(r)
+                    log(json.dumps(r))
+    return out
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--out", required=True)
-    ap.add_argument("--geometries", type=int, default=12)
-    ap.add_argument("--validation", type=int, default=2)
+    ap.add_argument("--geometries", type=int, default=75)
+    ap.add_argument("--validation", type=int, default=3)
+    ap.add_argument("--pairs", type=int, default=20000, help="training pairs in all (spread over the geometries)")
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--epochs", type=float, default=3.0)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1000)
+    ap.add_argument("--eval-n", type=int, default=0, help="grid of an evaluation on unseen geometries (0: none)")
+    ap.add_argument("--eval-seeds", default="5000")
+    ap.add_argument("--eval-freqs", default="1e9,4e9,7e9,10e9")
+    ap.add_argument("--eval-methods", default=",".join(METHODS))
+    ap.add_argument("--eval-max-iter", type=int, default=60000)
     args = ap.parse_args(argv)
     from . import build, fit
     build.build()
     fit.lib()
     t0 = time.time()
     seeds = list(range(args.seed, args.seed + args.geometries + args.validation))
-    samples = harvest(seeds[:args.geometries], n=args.n)
-    val = harvest(seeds[args.geometries:], n=args.n) if args.validation else None
+    per = max(1, args.pairs // max(1, args.geometries))
+    shards = harvest(seeds[:args.geometries], n=args.n, pairs_per_geometry=per)
+    val = harvest(seeds[args.geometries:], n=args.n, pairs_per_geometry=32) if args.validation else None
     t_h = time.time() - t0
+    npairs = sum(sh["pairs"].shape[0] for sh in shards)
     net = fit.UNet(seed=args.seed)
     v0 = validate(net, val, args.n) if val else None
     t1 = time.time()
-    hist = train(net, samples, args.n, args.steps, lr=args.lr, val=val)
+    hist, steps = train(net, shards, args.n, args.epochs, lr=args.lr, val=val)
     t_t = time.time() - t1
     v1 = validate(net, val, args.n) if val else None
-    record = {"geometries": seeds[:args.geometries], "validation_geometries": seeds[args.geometries:], "n": args.n,
-              "pairs": len(samples), "validation_pairs": len(val) if val else 0, "steps": args.steps, "lr": args.lr,
-              "harvest_s": t_h, "train_s": t_t, "final_train_loss": float(np.mean(hist[-max(1, args.steps // 10):])),
+    record = {"geometries": [seeds[0], seeds[args.geometries - 1]], "validation_geometries": seeds[args.geometries:],
+              "n": args.n, "pairs": npairs, "pairs_per_geometry": per, "epochs": args.epochs, "steps": steps,
+              "lr": args.lr, "harvest_s": t_h, "train_s": t_t,
+              "final_train_loss": float(np.mean(hist[-max(1, steps // 10):])),
               "validation_loss_initial": v0, "validation_loss_final": v1}
     save(net, args.out, record)
     print(json.dumps(record), flush=True)
+    del shards, val
+    if args.eval_n:
+        res = evaluate(net, [int(v) for v in args.eval_seeds.split(",")], [float(v) for v in args.eval_freqs.split(",")],
+                       n=args.eval_n, methods=args.eval_methods.split(","), max_iter=args.eval_max_iter)
+        print(json.dumps({"evaluation": res}), flush=True)
 
 
 if __name__ == "__main__":
