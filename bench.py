@@ -183,25 +183,30 @@ def run_reference(args, rank):
 def parse_kind(fit, kind):
     """"[method-]precision[+pc]": method fgmres (FGMRES(30), the default), cocg, cocr or bicgstab; precision
     "mixed" (complex64 inner solve inside FP64 refinement) or "c128"; pc jacobi (the Eq. Precond
-    diagonal, the default), eps (M_eps^-1: the symmetrised form's change of variable, Eq. e2s) or none.
-    Returns (method, precision, precond, label)."""
+    diagonal, the default), eps (M_eps^-1: the symmetrised form's change of variable, Eq. e2s), none, or
+    unet (the learned preconditioner, committed checkpoint, network on every other Arnoldi step; FGMRES
+    mixed only) / unet@0 (the network on each cycle's first vector only).
+    Returns (method, precision, precond, label, pc_every)."""
     base, _, pcname = kind.partition("+")
     pcname = pcname or "jacobi"
     mname, _, pname = base.rpartition("-")
     mname = mname or "fgmres"
     method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "cocr": fit.FIT_COCR, "bicgstab": fit.FIT_BICGSTAB}[mname]
-    pc = {"jacobi": fit.FIT_PC_JACOBI, "eps": fit.FIT_PC_EPS, "none": fit.FIT_PC_NONE}[pcname]
+    pc = {"jacobi": fit.FIT_PC_JACOBI, "eps": fit.FIT_PC_EPS, "none": fit.FIT_PC_NONE, "unet": fit.FIT_PC_UNET,
+          "unet@0": fit.FIT_PC_UNET}[pcname]
     prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
     label = {"fgmres": "FGMRES(30)", "cocg": "COCG", "cocr": "COCR", "bicgstab": "BiCGStab"}[mname] + \
-        {"jacobi": "+Jacobi", "eps": "+M_eps^-1", "none": ""}[pcname]
-    return method, prec, pc, label
+        {"jacobi": "+Jacobi", "eps": "+M_eps^-1", "none": "", "unet": "+U-Net", "unet@0": "+U-Net(cycle start)"}[pcname] + \
+        (" complex64+FP64 refinement" if pname == "mixed" else " complex128")
+    return method, prec, pc, label, (30 if pcname == "unet@0" else 2)
 
 
 def valid_kind(kind):
     base, _, pcname = kind.partition("+")
     mname, _, pname = base.rpartition("-")
-    return pname in ("mixed", "c128") and mname in ("", "fgmres", "cocg", "cocr", "bicgstab") and \
-        pcname in ("", "jacobi", "eps", "none")
+    ok = pname in ("mixed", "c128") and mname in ("", "fgmres", "cocg", "cocr", "bicgstab") and \
+        pcname in ("", "jacobi", "eps", "none", "unet", "unet@0")
+    return ok and (not pcname.startswith("unet") or (mname in ("", "fgmres") and pname == "mixed"))
 
 
 def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
@@ -212,27 +217,41 @@ def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
     w = 2 * np.pi * float(case["freqs"][0])
     j = torch.from_numpy(G.source_vector(case)).cuda()
     out = {}
+    net = None
     with fit.Grid.from_case(case) as g:
         b = (-1j * w) * j  # b = -j w j (masked source edges carry no current in these workloads)
         for kind in kinds:
-            method, prec, pc, label = parse_kind(fit, kind)
+            method, prec, pc, label, every = parse_kind(fit, kind)
+            extra = {}
+            if pc == fit.FIT_PC_UNET and net is None:
+                from paper_1705_08849_gb300 import train_unet
+                net = fit.UNet(seed=0)
+                head = train_unet.load(net, train_unet.DEFAULT_WEIGHTS)
+                fit.fit_set_preconditioner(g.h, net)
+                extra["weights"] = os.path.relpath(train_unet.DEFAULT_WEIGHTS, ROOT)
+                extra["trained_on"] = {k: head["record"].get(k) for k in ("n", "pairs", "geometries", "epochs")}
             x = torch.zeros_like(b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, rep = g.solve([w], b, x, 1e-8, precision=prec, method=method, restart=30,
-                              precond=pc, max_iter=max_iter, max_outer=max_iter, use_graph=use_graph)
+                              precond=pc, max_iter=max_iter, max_outer=max_iter, use_graph=use_graph, pc_every=every)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             out[kind] = {"s_per_freq": dt, "iterations": rep[0]["iterations"], "outer": rep[0]["outer"],
                          "relres": rep[0]["relres"], "status": fit.status_str(rep[0]["status"]),
-                         "method": label, "tol": 1e-8}
+                         "method": label, "tol": 1e-8, **extra}
+    if net is not None:
+        net.close()
     return out
 
 
-def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None):
-    """A wide-band sweep: nfreq of the workload's frequencies (evenly picked), b_f = -j w_f j, solved
-    to a 1e-8 true residual with the Jacobi preconditioner, once as one batch (one graph launch for
-    all systems) and once as nfreq sequential single-frequency solves.  Wall time of fit_solve."""
+def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None, seq_kind=None, budget_gb=0.0, restart=30,
+               seq_max_iter=None):
+    """A wide-band sweep: nfreq of the workload's frequencies (evenly picked, or evenly spaced over
+    ``band``), b_f = -j w_f j, solved to a 1e-8 true residual, once as one batch (one graph launch per
+    admitted batch: with an HBM budget, fit_solve halves the batch until its workspace fits) with
+    ``kind``, and once as nfreq sequential single-frequency solves with ``seq_kind`` (default: the same
+    kind).  Wall time of fit_solve; per-frequency status, iterations and true relative residual."""
     import fitgen as G
     if band:  # nfreq frequencies evenly spaced over [fmin, fmax]
         sel = np.linspace(band[0], band[1], max(1, nfreq))
@@ -240,32 +259,57 @@ def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None):
         fr = np.asarray(case["freqs"], dtype=np.float64)
         sel = fr[np.unique(np.linspace(0, len(fr) - 1, max(1, min(nfreq, len(fr)))).round().astype(int))]
     ws = 2 * np.pi * sel
-    method, prec, pc, _ = parse_kind(fit, kind)
+    seq_kind = seq_kind or kind
     j = torch.from_numpy(G.source_vector(case)).cuda()
     ne = j.numel()
     b = torch.stack([(-1j * w) * j for w in ws]).reshape(-1)
-    opts = dict(precision=prec, method=method, restart=30, precond=pc, max_iter=max_iter, max_outer=max_iter)
-    out = {"frequencies_hz": sel.tolist(), "method": kind}
+
+    def opts_of(k, cap):
+        method, prec, pc, _, every = parse_kind(fit, k)
+        return dict(precision=prec, method=method, restart=restart, precond=pc, max_iter=cap, max_outer=cap,
+                    pc_every=every), pc
+
+    out = {"frequencies_hz": sel.tolist(), "method": kind, "sequential_method": seq_kind, "restart": restart,
+           "max_iter": max_iter}
+    net = None
     with fit.Grid.from_case(case) as g:
+        if budget_gb > 0:
+            fit.fit_set_hbm_budget(g.h, int(budget_gb * 1e9))
+            out["hbm_budget_gb"] = budget_gb
+        for k in {kind, seq_kind}:
+            if parse_kind(fit, k)[2] == fit.FIT_PC_UNET and net is None:
+                from paper_1705_08849_gb300 import train_unet
+                net = fit.UNet(seed=0)
+                train_unet.load(net, train_unet.DEFAULT_WEIGHTS)
+                fit.fit_set_preconditioner(g.h, net)
+        o, _ = opts_of(kind, max_iter)
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, rep = g.solve(ws, b, x, 1e-8, batch=0, **opts)
+        st, rep = g.solve(ws, b, x, 1e-8, batch=0, **o)
         torch.cuda.synchronize()
+        # systems solved in the same admitted batch share their batch's wall time
+        groups = sorted({round(r["seconds"], 6) for r in rep})
         out["batched"] = {"s": time.perf_counter() - t0, "statuses": [fit.status_str(r["status"]) for r in rep],
-                          "iterations": [r["iterations"] for r in rep], "relres": [r["relres"] for r in rep]}
+                          "iterations": [r["iterations"] for r in rep], "relres": [r["relres"] for r in rep],
+                          "admitted_batches": len(groups), "converged": sum(r["status"] == 0 for r in rep)}
+        del x
+        o, _ = opts_of(seq_kind, seq_max_iter or max_iter)
         seq_t, seq_rep = 0.0, []
         for f, w in enumerate(ws):
             xf = torch.zeros(ne, dtype=b.dtype, device="cuda")
             bf = b[f * ne:(f + 1) * ne].contiguous()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st, rep1 = g.solve([w], bf, xf, 1e-8, **opts)
+            st, rep1 = g.solve([w], bf, xf, 1e-8, **o)
             torch.cuda.synchronize()
             seq_t += time.perf_counter() - t0
             seq_rep.append(rep1[0])
         out["sequential"] = {"s": seq_t, "statuses": [fit.status_str(r["status"]) for r in seq_rep],
-                             "iterations": [r["iterations"] for r in seq_rep]}
+                             "iterations": [r["iterations"] for r in seq_rep], "relres": [r["relres"] for r in seq_rep],
+                             "converged": sum(r["status"] == 0 for r in seq_rep)}
+    if net is not None:
+        net.close()
     return out
 
 
@@ -289,7 +333,7 @@ def time_ports(fit, torch, case, nport, nfreq, kind, max_iter, batch):
     fr = np.asarray(case["freqs"], dtype=np.float64)
     sel = fr[np.unique(np.linspace(0, len(fr) - 1, max(1, min(nfreq, len(fr)))).round().astype(int))]
     ws = 2 * np.pi * sel
-    method, prec, pc, _ = parse_kind(fit, kind)
+    method, prec, pc, _, _ = parse_kind(fit, kind)
     ports = port_columns(case, nport)
     with fit.Grid.from_case(case) as g:
         torch.cuda.synchronize()
@@ -361,6 +405,12 @@ def main():
                          "cocg, cocr or bicgstab, precision mixed or c128, pc jacobi (default), eps or none; "
                          "none for no solve")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
+    ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="sweep mode: the handle's HBM budget (0: none)")
+    ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length of the sweep mode")
+    ap.add_argument("--seq-max-iter", type=int, default=0, help="sweep mode: iteration cap of the sequential solves "
+                    "(0: --max-iter)")
+    ap.add_argument("--e2e-chunks", type=int, default=4, help="end-to-end leg: each host<->device copy is split into "
+                    "this many pieces on as many streams (several copy engines per direction)")
     ap.add_argument("--graph", type=int, default=1, help="1: the solve runs as one CUDA graph; 0: host-driven loop "
                     "(for per-kernel profiling)")
     args = ap.parse_args()
@@ -391,9 +441,12 @@ def main():
     if args.mode == "sweep":
         if rank == 0:
             kind = kinds[0] if kinds else "cocg-mixed"
+            seq = kinds[1] if len(kinds) > 1 else None
             print(json.dumps({"metric": "wide-band sweep s to 1e-8", "unit": "s", "workload": args.workload,
                               "sweep": time_sweep(fit, torch, case, args.nfreq, kind, args.max_iter,
-                                                  [float(v) for v in args.band.split(",")] if args.band else None)}),
+                                                  [float(v) for v in args.band.split(",")] if args.band else None,
+                                                  seq_kind=seq, budget_gb=args.hbm_budget_gb, restart=args.restart,
+                                                  seq_max_iter=args.seq_max_iter or None)}),
                   flush=True)
         return
     if args.mode == "ports":
@@ -487,6 +540,12 @@ def main():
     xd = [torch.empty_like(x) for _ in range(2)]
     yd = [torch.empty_like(x) for _ in range(2)]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    nch = max(1, args.e2e_chunks)
+    c_in = [torch.cuda.Stream() for _ in range(nch)]   # copy-in pieces, one stream each
+    c_out = [torch.cuda.Stream() for _ in range(nch)]  # copy-out pieces
+    bounds = [(B * ne * q) // nch for q in range(nch + 1)]
+    ev_ci = [torch.cuda.Event() for _ in range(nch)]
+    ev_co = [torch.cuda.Event() for _ in range(nch)]
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_ap = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
@@ -498,8 +557,12 @@ def main():
             q = k % 2
             if k >= 2:
                 s_in.wait_event(ev_ap[q])    # the apply of step k-2 has read xd[q]
-            with torch.cuda.stream(s_in):
-                xd[q].copy_(xh, non_blocking=True)
+            for c in range(nch):             # the input copy in pieces on parallel streams
+                c_in[c].wait_stream(s_in)
+                with torch.cuda.stream(c_in[c]):
+                    xd[q][bounds[c]:bounds[c + 1]].copy_(xh[bounds[c]:bounds[c + 1]], non_blocking=True)
+                ev_ci[c].record(c_in[c])
+                s_in.wait_event(ev_ci[c])
             ev_in[q].record(s_in)
             stream.wait_event(ev_in[q])
             if k >= 2:
@@ -509,8 +572,12 @@ def main():
                 raise fit.FitError(st, "fit_apply: " + L.fit_last_error().decode())
             ev_ap[q].record(stream)
             s_out.wait_event(ev_ap[q])
-            with torch.cuda.stream(s_out):
-                yh[q].copy_(yd[q], non_blocking=True)
+            for c in range(nch):
+                c_out[c].wait_stream(s_out)
+                with torch.cuda.stream(c_out[c]):
+                    yh[q][bounds[c]:bounds[c + 1]].copy_(yd[q][bounds[c]:bounds[c + 1]], non_blocking=True)
+                ev_co[c].record(c_out[c])
+                s_out.wait_event(ev_co[c])
             ev_out[q].record(s_out)
 
     k_e2e = max(10, min(args.steps, 200))
@@ -549,7 +616,8 @@ def main():
                        "l2_prefetch_planes": tuned["pf"],
                        "kernel_choice": tuned["choice"]},
             "roofline": roof, "clocks": clk.summary(), "step_stats": step_stats,
-            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * B * ne, "d2h_bytes_per_step": 8 * B * ne},
+            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * B * ne, "d2h_bytes_per_step": 8 * B * ne,
+                    "copy_pieces": nch, "pipelined": "copy in / apply / copy out on separate streams, 2 buffers"},
             "gpu_launches": args.steps}
 
     g.close()

@@ -910,6 +910,87 @@ __device__ inline void warp_accum(T re, T im, double* slot_re, double* slot_im) 
 
 #define FG_MAXV 65  // m + 1 <= 65
 
+// The last block of an orthogonalisation kernel to finish (per system b; cnt counts the finished blocks
+// and is reset by the last one) sums the nq per-block partials in a fixed order:
+// one warp per coefficient q, its lanes taking blocks lane, lane + 32, ..., then a shuffle tree.
+// Returns true in the last block (all of its threads), with hout[b][0 .. nq-1] written.
+__device__ inline bool fg_last_block_fin(const double* part, int nq, double* hout, unsigned* cnt, int b, const P& p) {
+  __shared__ int last;
+  __threadfence();  // every thread's partials are visible before the block's arrival is counted
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&cnt[b], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const double* pb = part + (long long)b * p.nblk * p.pstride;
+  for (int q = warp; q < nq; q += nw) {
+    double sum = 0.0;
+    for (int k = lane; k < p.nblk; k += 32) sum += __ldcg(pb + (long long)k * p.pstride + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) hout[(long long)b * 2 * FG_MAXV + q] = sum;
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (threadIdx.x == 0) cnt[b] = 0u;
+  return true;
+}
+
+// Hessenberg column j = h + h2, h_{j+1,j} = ||w||; Givens rotations; residual estimate |g_{j+1}|
+__device__ inline void fg_givens(int b, const double* __restrict__ hn2, int j, const double* __restrict__ h1,
+                                 const double* __restrict__ h2, double* H, double* G, double* CS, double* SN, Sys* sys,
+                                 const P& p) {
+  Sys& s = sys[b];
+  if (s.inner_status != SYS_RUN) return;
+  const double nrm2 = hn2[(long long)b * 2 * FG_MAXV];  // ||w||^2, reduced by the last block
+  const int m = p.m;
+  double2* Hc = (double2*)(H + (long long)b * 2 * (m + 1) * m) + (long long)j * (m + 1);  // column j
+  double2* g = (double2*)(G + (long long)b * 2 * (m + 1));
+  double2* cs = (double2*)(CS + (long long)b * 2 * m);
+  double2* sn = (double2*)(SN + (long long)b * 2 * m);
+  const double2* a1 = (const double2*)(h1 + (long long)b * 2 * FG_MAXV);
+  const double2* a2 = (const double2*)(h2 + (long long)b * 2 * FG_MAXV);
+  for (int i = 0; i <= j; ++i) Hc[i] = cadd(a1[i], a2[i]);
+  const double hn = sqrt(nrm2);
+  Hc[j + 1] = make_double2(hn, 0.0);
+  if (!isfinite(hn) || !cfinite(Hc[j])) { s.inner_status = SYS_NAN; return; }
+  for (int i = 0; i < j; ++i) {
+    double2 hi = Hc[i], hi1 = Hc[i + 1];
+    Hc[i] = cadd(cmul(cconj(cs[i]), hi), cmul(cconj(sn[i]), hi1));
+    Hc[i + 1] = csub(cmul(cs[i], hi1), cmul(sn[i], hi));
+  }
+  double2 a = Hc[j], c = Hc[j + 1];
+  double den = sqrt(cabs2(a) + cabs2(c));
+  if (den > 0.0) {
+    cs[j] = make_double2(a.x / den, a.y / den);
+    sn[j] = make_double2(c.x / den, c.y / den);
+  } else {
+    cs[j] = make_double2(1.0, 0.0);
+    sn[j] = make_double2(0.0, 0.0);
+  }
+  Hc[j] = make_double2(den, 0.0);
+  Hc[j + 1] = make_double2(0.0, 0.0);
+  double2 gj = g[j];
+  g[j + 1] = make_double2(-(sn[j].x * gj.x - sn[j].y * gj.y), -(sn[j].x * gj.y + sn[j].y * gj.x));
+  g[j] = cmul(cconj(cs[j]), gj);
+  s.jlast = j + 1;
+  s.inner_it += 1;
+  s.inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+  double res2 = cabs2(g[j + 1]);
+  s.rin2 = res2;
+  if (res2 <= s.inner_tol2) s.inner_status = SYS_CONV;
+  else if (hn == 0.0 || den == 0.0) s.inner_status = SYS_CONV;  // exact invariant subspace
+  else if (j + 1 >= m || s.inner_it >= s.max_inner) s.inner_status = SYS_MAXIT;
+}
+
+// Arnoldi coefficient vectors of the orthogonalisation passes and the Hessenberg workspace, for the
+// last block's reduction and Givens step
+struct FgOut {
+  double *h1, *h2, *hn2, *H, *G, *CS, *SN;
+  unsigned* cnt;
+};
+
 // The three CGS2 passes.  They work on chunks of CH elements (one per thread, CH = 256 for complex64
 // and 128 for complex128) and keep only a few values per thread in registers:
 //   k_fg_dots:         h_i = <V_i, w>                   (2(j+1) partials per block)
@@ -955,7 +1036,7 @@ __device__ inline void fg_chunk_dots(const typename cplx<T>::t* vchunk, long lon
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fg_dots(const typename cplx<T>::t* __restrict__ Vb, int j,
-                                                 const Sys* __restrict__ sys, double* part, P p) {
+                                                 const Sys* __restrict__ sys, double* part, FgOut fo, P p) {
   using V = typename cplx<T>::t;
   constexpr int CH = FgChunk<T>::CH;
   const int b = blockIdx.y;
@@ -976,12 +1057,13 @@ __global__ void __launch_bounds__(256) k_fg_dots(const typename cplx<T>::t* __re
   __syncthreads();
   double* out = part + PSLOT(p, b);
   for (int q = tid; q < 2 * nv; q += CH) out[q] = acc[q];
+  fg_last_block_fin(part, 2 * nv, fo.h1, fo.cnt, b, p);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fg_update_dots(const typename cplx<T>::t* __restrict__ Vb, int j,
                                                         const double* __restrict__ hcoef,
-                                                        const Sys* __restrict__ sys, double* part, P p) {
+                                                        const Sys* __restrict__ sys, double* part, FgOut fo, P p) {
   using V = typename cplx<T>::t;
   constexpr int CH = FgChunk<T>::CH;
   const int b = blockIdx.y;
@@ -1021,12 +1103,13 @@ __global__ void __launch_bounds__(256) k_fg_update_dots(const typename cplx<T>::
   __syncthreads();
   double* out = part + PSLOT(p, b);
   for (int q = tid; q < 2 * nv; q += CH) out[q] = acc[q];
+  fg_last_block_fin(part, 2 * nv, fo.h2, fo.cnt, b, p);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fg_update_norm(const typename cplx<T>::t* __restrict__ Vb, int j,
                                                         const double* __restrict__ hcoef,
-                                                        const Sys* __restrict__ sys, double* part, P p) {
+                                                        Sys* sys, double* part, FgOut fo, P p) {
   using V = typename cplx<T>::t;
   constexpr int CH = FgChunk<T>::CH;
   const int b = blockIdx.y;
@@ -1053,71 +1136,175 @@ __global__ void __launch_bounds__(256) k_fg_update_norm(const typename cplx<T>::
     nrm[0] += wv.x * wv.x + wv.y * wv.y;
   }
   fit_block_sum<T, 1>(nrm, part + PSLOT(p, b));
+  // the last block reduces ||w||^2 and takes the Givens step of this system
+  if (fg_last_block_fin(part, 1, fo.hn2, fo.cnt, b, p) && threadIdx.x == 0) {
+    __threadfence_block();
+    fg_givens(b, fo.hn2, j, fo.h1, fo.h2, fo.H, fo.G, fo.CS, fo.SN, sys, p);
+  }
 }
 
-// hout[b][q] = sum over the blocks k of part[b][k][q], q < nq: one warp per q, its lanes summing
-// blocks k = lane, lane + 32, ... and then a fixed shuffle tree (the same order on every run)
-__global__ void __launch_bounds__(256) k_fg_fin_dots(const double* __restrict__ part, int nq, double* hout,
-                                                     const Sys* __restrict__ sys, P p) {
-  const int b = blockIdx.x;
+
+// ---- the three CGS2 passes with bulk copies -----------------------------------------------------
+// The same passes and per-block partial layout as k_fg_dots / k_fg_update_dots / k_fg_update_norm, but
+// the block's chunk of every basis vector and of w arrives in shared memory by a bulk copy engine
+// transfer (cp.async.bulk, one 2 KB copy per vector and chunk), S chunks in flight, completed on one
+// mbarrier per stage.  The copy engine keeps the loads streaming while the threads update w and take
+// the dot products from shared memory, so V is read from HBM once per pass at close to copy speed.
+// Dot products: warp q of NW owns the basis vectors i = q, q + NW, ...; each lane accumulates its share over
+// all of the block's chunks in the vector precision, and the warp's shuffle sum goes to the block's
+// partial slot in FP64.  Needs 16-byte aligned chunks: complex128, or complex64 with an even n_e.
+// Every wait on a stage is bounded (2^22 polls, the grid's abort word read every 4096): on a timeout the
+// block records it in the grid's error word, lets its own copies land and leaves.
+__device__ inline uint32_t kr_smem(const void* q) { return (uint32_t)__cvta_generic_to_shared(q); }
+__device__ inline bool kr_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(kr_smem(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline bool kr_wait(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (kr_try_wait(bar, parity)) return true;
+    if (it > 32) __nanosleep(32);
+    if ((it & 4095) == 4095 && abort && *abort) return false;
+  }
+  return false;
+}
+
+template <typename T, int MODE, int S>
+__global__ void __launch_bounds__(256) k_fg_cgs_bulk(const typename cplx<T>::t* __restrict__ Vb, int j,
+                                                     const double* __restrict__ hcoef, Sys* sys, double* part,
+                                                     FgOut fo, P p) {
+  using V = typename cplx<T>::t;
+  constexpr int CH = FgChunk<T>::CH;
+  constexpr int NW = CH / 32;       // warps per block (one thread per chunk element)
+  constexpr int SLOTS = 64 / NW;    // basis vectors per warp: nv <= 64
+  const int b = blockIdx.y;
   if (sys[b].inner_status != SYS_RUN) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double* pb = part + (long long)b * p.nblk * p.pstride;
-  for (int q = warp; q < nq; q += 8) {
-    double s = 0.0;
-    for (int k = lane; k < p.nblk; k += 32) s += pb[(long long)k * p.pstride + q];
+  extern __shared__ __align__(128) unsigned char fg_bulk_smem[];
+  const int nv = j + 1, nrow = nv + 1, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t stage_vals = (size_t)nrow * CH;
+  V* stg = (V*)fg_bulk_smem;
+  uint64_t* bar = (uint64_t*)(stg + S * stage_vals);
+  T* hs = (T*)(bar + S);                 // [2 nv]
+  double* red = (double*)(hs + 2 * FG_MAXV);  // [2 nv] per-vector block sums
+  __shared__ int bad;
+  const long long vs = (long long)p.B * p.ne, off = (long long)b * p.ne;
+  V* w = (V*)(Vb + (long long)(j + 1) * vs + off);
+  const long long first = (long long)blockIdx.x * CH, step = (long long)gridDim.x * CH;
+  const int nch = first < p.ne ? (int)((p.ne - first + step - 1) / step) : 0;
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(kr_smem(&bar[q])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bad = 0;
+  }
+  if (MODE >= 1) {
+    const double* hc = hcoef + (long long)b * 2 * FG_MAXV;
+    for (int q = tid; q < 2 * nv; q += blockDim.x) hs[q] = (T)hc[q];
+  }
+  __syncthreads();
+  auto issue = [&](int n) {  // thread 0: every row of chunk n into stage n % S
+    const long long c0 = first + (long long)n * step;
+    const uint32_t bytes = (uint32_t)(min((long long)CH, p.ne - c0) * (long long)sizeof(V));
+    V* dst = stg + (size_t)(n % S) * stage_vals;
+    uint64_t* br = &bar[n % S];
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(kr_smem(br)), "r"(bytes * nrow)
+                 : "memory");
+    for (int r = 0; r < nrow; ++r) {
+      const V* src = (r < nv ? Vb + (long long)r * vs + off : w) + c0;
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       kr_smem(dst + (size_t)r * CH)),
+                   "l"(src), "r"(bytes), "r"(kr_smem(br))
+                   : "memory");
+    }
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(S, nch); ++issued) issue(issued);
+  T ar[SLOTS], ai[SLOTS], nrm = T(0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) hout[(long long)b * 2 * FG_MAXV + q] = s;
+  for (int q = 0; q < SLOTS; ++q) ar[q] = ai[q] = T(0);
+  int n = 0;
+  for (; n < nch; ++n) {
+    const bool ok = kr_wait(&bar[n % S], (uint32_t)((n / S) & 1), p.abort);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        bad = 1;
+        atomicExch(p.err, (p.abort && *p.abort) ? 2 : 1);
+      }
+      break;
+    }
+    V* sv = stg + (size_t)(n % S) * stage_vals;
+    const long long c0 = first + (long long)n * step;
+    const int nvalid = (int)min((long long)CH, p.ne - c0);
+    if (MODE >= 1 && tid < nvalid) {  // w -= sum_i h_i V_i for this thread's element
+      V wv = sv[(size_t)nv * CH + tid];
+      for (int i = 0; i < nv; ++i) {
+        const V a = sv[(size_t)i * CH + tid];
+        const T hr = hs[2 * i], hi = hs[2 * i + 1];
+        wv.x -= hr * a.x - hi * a.y;
+        wv.y -= hr * a.y + hi * a.x;
+      }
+      w[c0 + tid] = wv;
+      if (MODE == 1) sv[(size_t)nv * CH + tid] = wv;
+      else nrm += wv.x * wv.x + wv.y * wv.y;
+    }
+    if (MODE <= 1) {
+      if (MODE == 1) __syncthreads();  // the updated w of the chunk is in shared memory
+      const V* wsm = sv + (size_t)nv * CH;
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        const int i = warp + NW * q;
+        if (i < nv) {
+          const V* vi = sv + (size_t)i * CH;
+          for (int e = lane; e < nvalid; e += 32) {
+            const V a = vi[e], c = wsm[e];
+            ar[q] += a.x * c.x + a.y * c.y;  // conj(V_i) w
+            ai[q] += a.x * c.y - a.y * c.x;
+          }
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes before the stage's refill
+    __syncthreads();  // the stage is consumed
+    if (tid == 0 && issued < nch) issue(issued++);
   }
-}
-
-// Hessenberg column j = h + h2, h_{j+1,j} = ||w||; Givens rotations; residual estimate |g_{j+1}|
-__global__ void k_fg_givens(const double* __restrict__ hn2, int j, const double* __restrict__ h1,
-                            const double* __restrict__ h2, double* H, double* G, double* CS, double* SN, Sys* sys, P p) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= p.B) return;
-  Sys& s = sys[b];
-  if (s.inner_status != SYS_RUN) return;
-  const double nrm2 = hn2[(long long)b * 2 * FG_MAXV];  // ||w||^2, reduced by k_fg_fin_dots
-  const int m = p.m;
-  double2* Hc = (double2*)(H + (long long)b * 2 * (m + 1) * m) + (long long)j * (m + 1);  // column j
-  double2* g = (double2*)(G + (long long)b * 2 * (m + 1));
-  double2* cs = (double2*)(CS + (long long)b * 2 * m);
-  double2* sn = (double2*)(SN + (long long)b * 2 * m);
-  const double2* a1 = (const double2*)(h1 + (long long)b * 2 * FG_MAXV);
-  const double2* a2 = (const double2*)(h2 + (long long)b * 2 * FG_MAXV);
-  for (int i = 0; i <= j; ++i) Hc[i] = cadd(a1[i], a2[i]);
-  const double hn = sqrt(nrm2);
-  Hc[j + 1] = make_double2(hn, 0.0);
-  if (!isfinite(hn) || !cfinite(Hc[j])) { s.inner_status = SYS_NAN; return; }
-  for (int i = 0; i < j; ++i) {
-    double2 hi = Hc[i], hi1 = Hc[i + 1];
-    Hc[i] = cadd(cmul(cconj(cs[i]), hi), cmul(cconj(sn[i]), hi1));
-    Hc[i + 1] = csub(cmul(cs[i], hi1), cmul(sn[i], hi));
+  if (bad) {  // let this block's copies land before it leaves (bounded; no early exit on abort)
+    if (tid == 0)
+      for (int q = n; q < issued; ++q) (void)kr_wait(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
+    __syncthreads();
+    return;
   }
-  double2 a = Hc[j], c = Hc[j + 1];
-  double den = sqrt(cabs2(a) + cabs2(c));
-  if (den > 0.0) {
-    cs[j] = make_double2(a.x / den, a.y / den);
-    sn[j] = make_double2(c.x / den, c.y / den);
-  } else {
-    cs[j] = make_double2(1.0, 0.0);
-    sn[j] = make_double2(0.0, 0.0);
+  double* out = part + PSLOT(p, b);
+  if (MODE == 2) {
+    T v1[1] = {nrm};
+    fit_block_sum<T, 1>(v1, out);
+    if (fg_last_block_fin(part, 1, fo.hn2, fo.cnt, b, p) && tid == 0) {
+      __threadfence_block();
+      fg_givens(b, fo.hn2, j, fo.h1, fo.h2, fo.H, fo.G, fo.CS, fo.SN, sys, p);
+    }
+    return;
   }
-  Hc[j] = make_double2(den, 0.0);
-  Hc[j + 1] = make_double2(0.0, 0.0);
-  double2 gj = g[j];
-  g[j + 1] = make_double2(-(sn[j].x * gj.x - sn[j].y * gj.y), -(sn[j].x * gj.y + sn[j].y * gj.x));
-  g[j] = cmul(cconj(cs[j]), gj);
-  s.jlast = j + 1;
-  s.inner_it += 1;
-  s.inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
-  double res2 = cabs2(g[j + 1]);
-  s.rin2 = res2;
-  if (res2 <= s.inner_tol2) s.inner_status = SYS_CONV;
-  else if (hn == 0.0 || den == 0.0) s.inner_status = SYS_CONV;  // exact invariant subspace
-  else if (j + 1 >= m || s.inner_it >= s.max_inner) s.inner_status = SYS_MAXIT;
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    const int i = warp + NW * q;
+    T r = ar[q], m = ai[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      r += __shfl_xor_sync(0xffffffffu, r, o);
+      m += __shfl_xor_sync(0xffffffffu, m, o);
+    }
+    if (lane == 0 && i < nv) {
+      red[2 * i] = (double)r;
+      red[2 * i + 1] = (double)m;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < 2 * nv; q += blockDim.x) out[q] = red[q];
+  fg_last_block_fin(part, 2 * nv, MODE == 0 ? fo.h1 : fo.h2, fo.cnt, b, p);
 }
 
 // v_{j+1} = w / h_{j+1,j}
@@ -1561,21 +1748,40 @@ struct Seq {
   }
 
   // the three CGS2 passes over V[0..j] (mode 0: dots; 1: update with h, dots; 2: update with h2, norm)
+  FgOut fg_out() const { return FgOut{w.h1, w.h2, w.hn2, w.H, w.G, w.CS, w.SN, w.cnt}; }
+  template <typename T, int MODE, int S>
+  void ortho_bulk(int j, const double* h) {
+    using V = typename cplx<T>::t;
+    constexpr int CH = FgChunk<T>::CH;
+    const size_t smem = (size_t)S * (j + 2) * CH * sizeof(V) + S * 8 + 2 * FG_MAXV * sizeof(T) +
+                        2 * FG_MAXV * sizeof(double);
+    auto kern = k_fg_cgs_bulk<T, MODE, S>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<vgrid(), CH, smem, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, fg_out(), w.p);
+    check();
+  }
+  // the bulk-copy passes need 16-byte aligned chunks of every vector
+  bool bulk_ok() const { return w.esz == 16 || (w.p.ne % 2) == 0; }
   template <typename T, int MODE>
   void ortho(int j, const double* h) {
     using V = typename cplx<T>::t;
     constexpr int CH = FgChunk<T>::CH;
     const int nv = j + 1;
+    if (bulk_ok()) {  // three stages while they fit two blocks per SM, else two
+      if ((size_t)3 * (j + 2) * CH * sizeof(V) <= 100 * 1024) ortho_bulk<T, MODE, 3>(j, h);
+      else ortho_bulk<T, MODE, 2>(j, h);
+      return;
+    }
     if (MODE == 0) {
-      k_fg_dots<T><<<vgrid(), CH, 0, s>>>((const V*)w.Vb, j, w.sys, w.part_vec, w.p);
+      k_fg_dots<T><<<vgrid(), CH, 0, s>>>((const V*)w.Vb, j, w.sys, w.part_vec, fg_out(), w.p);
     } else if (MODE == 1) {
       const size_t smem = (size_t)(nv + 1) * CH * sizeof(V) + (size_t)2 * nv * sizeof(double) +
                           (size_t)2 * nv * sizeof(T);
       auto kern = k_fg_update_dots<T>;
       if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<vgrid(), CH, smem, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+      kern<<<vgrid(), CH, smem, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, fg_out(), w.p);
     } else {
-      k_fg_update_norm<T><<<vgrid(), CH, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, w.p);
+      k_fg_update_norm<T><<<vgrid(), CH, 0, s>>>((const V*)w.Vb, j, h, w.sys, w.part_vec, fg_out(), w.p);
     }
     check();
   }
@@ -1612,16 +1818,10 @@ struct Seq {
       zin = (const char*)w.Zb + (size_t)j * vecb;
     }
     apply(zin, wj1, FIT_EPI_NONE, nullptr, w.inner, st_inner);
+    // CGS2: each pass's last block reduces its partial sums (h, h2, then ||w||^2 and the Givens step)
     ortho<T, 0>(j, nullptr);
-    k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h1, w.sys, w.p);
-    check();
     ortho<T, 1>(j, w.h1);
-    k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 2 * (j + 1), w.h2, w.sys, w.p);
-    check();
     ortho<T, 2>(j, w.h2);
-    k_fg_fin_dots<<<w.p.B, 256, 0, s>>>(w.part_vec, 1, w.hn2, w.sys, w.p);
-    k_fg_givens<<<(w.p.B + 127) / 128, 128, 0, s>>>(w.hn2, j, w.h1, w.h2, w.H, w.G, w.CS, w.SN, w.sys, w.p);
-    check();
     k_fg_scale<T><<<vgrid(), 256, 0, s>>>((V*)w.Vb, j, w.sys, w.p);
     check();
   }

@@ -7,7 +7,7 @@ import bench
 
 class _Consts:
     FIT_BICGSTAB, FIT_FGMRES, FIT_COCG, FIT_COCR = 0, 1, 2, 3
-    FIT_PC_NONE, FIT_PC_JACOBI, FIT_PC_EPS = 0, 1, 3
+    FIT_PC_NONE, FIT_PC_JACOBI, FIT_PC_UNET, FIT_PC_EPS = 0, 1, 2, 3
     FIT_SOLVE_C128, FIT_SOLVE_MIXED = 0, 1
 
 
@@ -18,13 +18,21 @@ class _Consts:
     ("cocr-c128+none", (3, 0, 0)),
     ("bicgstab-mixed+eps", (0, 1, 3)),
     ("fgmres-c128+jacobi", (1, 0, 1)),
+    ("fgmres-mixed+unet", (1, 1, 2)),
+    ("mixed+unet@0", (1, 1, 2)),
 ])
 def test_parse_kind(kind, want):
     assert bench.valid_kind(kind)
     assert bench.parse_kind(_Consts, kind)[:3] == want
 
 
-@pytest.mark.parametrize("kind", ["cocg", "cocg-fp32", "gmres-mixed", "cocg-mixed+ilu", "none", ""])
+def test_learned_kinds_place_the_network():
+    assert bench.parse_kind(_Consts, "fgmres-mixed+unet")[4] == 2  # every other Arnoldi step
+    assert bench.parse_kind(_Consts, "fgmres-mixed+unet@0")[4] == 30  # each cycle's first vector
+
+
+@pytest.mark.parametrize("kind", ["cocg", "cocg-fp32", "gmres-mixed", "cocg-mixed+ilu", "none", "",
+                                  "cocg-mixed+unet", "fgmres-c128+unet"])
 def test_invalid_kinds_are_dropped(kind):
     assert not bench.valid_kind(kind)
 

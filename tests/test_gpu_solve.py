@@ -223,3 +223,22 @@ def test_zero_rhs_and_nan_rhs_and_caps():
         with pytest.raises(fit.FitError) as ei:
             g.solve([1e10], b, x, 1e-8)
         assert ei.value.status == fit.FIT_EBUDGET
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nx,ny,nz", [(9, 7, 5), (12, 10, 8)])
+def test_fgmres_orthogonalisation_paths(precision, nx, ny, nz):
+    """FGMRES(12) on a grid with an odd number of unknowns (complex64 chunks are not 16-byte aligned, so
+    the orthogonalisation runs the per-thread kernels) and on one with an even number (the bulk-copy
+    kernels), a batch of two lossy systems, judged by the oracle's residual."""
+    from oracle import fit as F
+    case = G.small_random(nx, ny, nz, seed=61, pec_frac=0.05)
+    n = 3 * nx * ny * nz
+    mask = F.edge_mask(nx, ny, nz, case["pec"])
+    rhs = np.stack([G.random_vector(n, s) * (1 - mask) for s in (7, 8)])
+    st, rep, xs, bs, ws = _solve(case, [2e9, 7e9], 1e-9, rhs=rhs, method=1, precond=1, restart=12,
+                                 precision=precision, max_outer=2000, max_iter=20000)
+    assert st == 0, rep
+    for i in range(2):
+        rr, _ = _oracle_relres(case, ws[i], xs[i], bs[i])
+        assert rr <= 1e-9, (i, rr, rep[i])
