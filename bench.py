@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -184,28 +185,33 @@ def parse_kind(fit, kind):
     """"[method-]precision[+pc]": method fgmres (FGMRES(30), the default), cocg, cocr or bicgstab; precision
     "mixed" (complex64 inner solve inside FP64 refinement) or "c128"; pc jacobi (the Eq. Precond
     diagonal, the default), eps (M_eps^-1: the symmetrised form's change of variable, Eq. e2s), none, or
-    unet (the learned preconditioner, committed checkpoint, network on every other Arnoldi step; FGMRES
-    mixed only) / unet@0 (the network on each cycle's first vector only).
+    unet (the learned preconditioner from the committed checkpoint: one direction from the network per
+    restart cycle, the Jacobi term on the other steps; FGMRES mixed only) / unet/K (the network's direction
+    on the steps j = 1 mod K).
     Returns (method, precision, precond, label, pc_every)."""
     base, _, pcname = kind.partition("+")
     pcname = pcname or "jacobi"
     mname, _, pname = base.rpartition("-")
     mname = mname or "fgmres"
     method = {"fgmres": fit.FIT_FGMRES, "cocg": fit.FIT_COCG, "cocr": fit.FIT_COCR, "bicgstab": fit.FIT_BICGSTAB}[mname]
-    pc = {"jacobi": fit.FIT_PC_JACOBI, "eps": fit.FIT_PC_EPS, "none": fit.FIT_PC_NONE, "unet": fit.FIT_PC_UNET,
-          "unet@0": fit.FIT_PC_UNET}[pcname]
+    every = 0
+    if pcname.startswith("unet/"):
+        pcname, every = "unet", int(pcname[5:])
+    pc = {"jacobi": fit.FIT_PC_JACOBI, "eps": fit.FIT_PC_EPS, "none": fit.FIT_PC_NONE, "unet": fit.FIT_PC_UNET}[pcname]
     prec = fit.FIT_SOLVE_MIXED if pname == "mixed" else fit.FIT_SOLVE_C128
     label = {"fgmres": "FGMRES(30)", "cocg": "COCG", "cocr": "COCR", "bicgstab": "BiCGStab"}[mname] + \
-        {"jacobi": "+Jacobi", "eps": "+M_eps^-1", "none": "", "unet": "+U-Net", "unet@0": "+U-Net(cycle start)"}[pcname] + \
+        {"jacobi": "+Jacobi", "eps": "+M_eps^-1", "none": "", "unet": "+U-Net+Jacobi"}[pcname] + \
+        (f"(network every {every} steps)" if every else "") + \
         (" complex64+FP64 refinement" if pname == "mixed" else " complex128")
-    return method, prec, pc, label, (30 if pcname == "unet@0" else 2)
+    return method, prec, pc, label, every
 
 
 def valid_kind(kind):
     base, _, pcname = kind.partition("+")
     mname, _, pname = base.rpartition("-")
+    unet_k = re.fullmatch(r"unet/([2-9]|[1-9][0-9]+)", pcname) is not None
     ok = pname in ("mixed", "c128") and mname in ("", "fgmres", "cocg", "cocr", "bicgstab") and \
-        pcname in ("", "jacobi", "eps", "none", "unet", "unet@0")
+        (pcname in ("", "jacobi", "eps", "none", "unet") or unet_k)
     return ok and (not pcname.startswith("unet") or (mname in ("", "fgmres") and pname == "mixed"))
 
 

@@ -192,9 +192,10 @@ typedef struct fit_solve_opts {
                         (h * nfreq + f) * n_e (used to harvest training pairs); NULL = off */
   int history_len;   /* slots in history (per system) */
   int history_every; /* outer steps between snapshots (>= 1) */
-  int pc_every;      /* FIT_PC_UNET: the network runs on the Arnoldi steps j of a cycle with j % pc_every == 0
-                        (the Jacobi term alone on the others); 2 (the default) alternates, a value >= restart
-                        runs it on the cycle's first vector only, which is the normalised true residual */
+  int pc_every;      /* FIT_PC_UNET: the Arnoldi steps j of a cycle with j % pc_every == 1 take the network's
+                        direction z_j = U(v_{j-1}), all others the Jacobi term z_j = D^-1 v_j; 0 (the default)
+                        means once per cycle, at j = 1, where the network's input is the cycle's first vector:
+                        the normalised true residual it was trained on.  0 or >= 2 */
 } fit_solve_opts;
 
 typedef struct fit_solve_report {
@@ -352,14 +353,14 @@ fit_status fit_unet_head_backward(long long nvox, const void* in, const float* d
 
 /* fit_unet_training_pair -- one training pair of the learned preconditioner from an iterate x_k of a solve
  * of A(omega) x = b whose solution is x* (the harvest step of the training data):
- *     r = b - A(omega) x_k  (FP64 apply),   rms = ||r||_2 / sqrt(n_e),
- *     pair[c][0..5]  = bf16 of r / rms                            (Re, Im of the x, y, z edges of cell c)
- *     pair[c][6..11] = bf16 of ((x* - x_k) - D^-1 r) / (s rms)    (the correction the Jacobi term misses)
- * with D = diag(A(omega)) (Eq. Precond construction) and s = fit_coef_scale (the units of the scaled
- * complex64 operator the network preconditions); masked edges are zero in both halves.
- *   x_k, x_star, b   DEVICE complex128 [n_e];  pair  DEVICE bf16 [ncell][12] (4-byte aligned)
- *   rms_out          HOST, may be NULL: receives rms (the call synchronises on stream either way)
- * Holds two temporary device vectors (counted against the HBM budget) while it runs. */
+ *     r = b - A(omega) x_k  (FP64 apply),   e = x* - x_k  (the error of the iterate, A e = r),
+ *     pair[c][0..5]  = bf16 of r / rms(r)     (Re, Im of the x, y, z edges of cell c)
+ *     pair[c][6..11] = bf16 of e / rms(e)     (the direction of the error)
+ * with rms(v) = ||v||_2 / sqrt(n_e) over the unmasked edges; masked edges are zero in both halves.  Both
+ * halves have unit rms whatever the iterate, so pairs from early and late iterates weigh alike in the
+ * loss.  x_k, x_star, b: DEVICE complex128 [n_e];  pair: DEVICE bf16 [ncell][12] (4-byte aligned);
+ * rms_out: HOST, may be NULL: receives rms(r) (the call synchronises on stream either way).  Holds two
+ * temporary device vectors (counted against the HBM budget) while it runs. */
 fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, const void* xstar, const void* b,
                                   void* pair, double* rms_out, void* stream);
 /* fit_unet_pair_sample -- network input and target of a stored pair: in16[c] = base16[c] with channels
@@ -369,10 +370,14 @@ fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, con
 fit_status fit_unet_pair_sample(long long ncell, const void* pair, const void* base16, void* in16, float* target6,
                                 void* stream);
 
-/* attach a network to the grid; fit_solve with precond = FIT_PC_UNET (FGMRES, FIT_SOLVE_MIXED)
- * then applies M(v) = D^-1 v + rms(v) U(v / rms(v)) as the right preconditioner: the network learns
- * the part of the correction that the Jacobi term misses (its head starts at zero, so an untrained
- * network gives plain Jacobi).  The grid does not own the network. */
+/* attach a network to the grid; fit_solve with precond = FIT_PC_UNET (FGMRES, FIT_SOLVE_MIXED) then
+ * gives flexible GMRES one direction from the network per restart cycle (see fit_solve_opts.pc_every):
+ * z_1 = U(v_0) / sqrt(n_e) + 1e-3 D^-1 v_1, v_0 the normalised residual of the cycle, which the network
+ * maps to the direction of the current error (fit_unet_training_pair); every other step takes the Jacobi
+ * direction D^-1 v_j.  The small Jacobi term keeps z_1 usable if the network outputs zero (an untrained
+ * network, whose head starts at zero, gives exactly Jacobi FGMRES).  The residual minimisation decides how much of the network's direction to use, so a poor
+ * network costs its application time but cannot stop the Jacobi directions from converging.  The grid
+ * does not own the network. */
 fit_status fit_set_preconditioner(fit_grid* g, int kind, fit_unet* net);
 
 /* fit_jacobi -- y_b = D(omega_b)^-1 x_b with D = diag(A(omega)): for an unmasked edge the sum of M_nu

@@ -151,8 +151,9 @@ def bicgstab(A, b, tol=1e-10, maxiter=10000):
 def fgmres(A, b, tol=1e-10, restart=30, maxiter=10000, precond=None, precond_step=False, history=None):
     """Restarted right-preconditioned FGMRES(m) with modified Gram-Schmidt and Givens rotations.
     ``precond`` maps a vector v_j to z_j = M(v_j) (identity when None, which is plain GMRES); with
-    ``precond_step`` it is called as M(v_j, j) with the Arnoldi step j of the current cycle (the
-    flexible method allows the preconditioner to change from step to step).  ``history``, if a list,
+    ``precond_step`` it is called as M(V, j) with the cycle's basis V (rows 0 .. j filled) and the
+    Arnoldi step j, and returns z_j: the flexible method minimises the residual over x0 + span(z_0 ..
+    z_j) whatever the z_j are, so the preconditioner may change from step to step.  ``history``, if a list,
     receives the true relative residual after every restart cycle.
     Returns (x, iterations, true relative residual, status)."""
     b = np.asarray(b, dtype=np.complex128)
@@ -179,7 +180,7 @@ def fgmres(A, b, tol=1e-10, restart=30, maxiter=10000, precond=None, precond_ste
         V[0] = r / beta
         jlast = 0
         for jj in range(m):
-            Z[jj] = M(V[jj], jj) if precond_step else M(V[jj])
+            Z[jj] = M(V, jj) if precond_step else M(V[jj])
             w = A @ Z[jj]
             for i in range(jj + 1):  # modified Gram-Schmidt
                 H[i, jj] = np.vdot(V[i], w)

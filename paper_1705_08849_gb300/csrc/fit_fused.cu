@@ -229,11 +229,10 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
-    bad = *a.abort ? 1 : 0;  // aborted before it started: no copy is issued, nothing is written
-    if (bad) atomicExch(a.err, 2);
+    bad = 0;
   }
   __syncthreads();
-  if (bad) return;
+  bool first_tile = true;
 
   unsigned G = 0, O = 0;        // planes issued into the ring / output planes written, this CTA
   bool pend = false;            // an output plane is staged but not yet stored (thread 0's view)
@@ -285,7 +284,15 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
     if (tid == 0) {
       for (int q = 0; q < min(S, nplanes); ++q) issue(q);
       for (int q = S; q < S + a.pf; ++q) prefetch(q);  // the planes after the first ring fill
+      // The abort word (pinned host memory) is read once, after the first copies are on their way, so
+      // that its latency hides under theirs; the barrier below publishes the answer before anything
+      // is written.
+      if (first_tile && *a.abort) {
+        bad = 1;
+        atomicExch(a.err, 2);
+      }
     }
+    first_tile = false;
     int issued = min(S, nplanes);
     auto drain = [&]() {  // bounded waits for every copy this tile issued
       for (int q = 0; q < issued; ++q) (void)mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1, nullptr);
@@ -509,8 +516,10 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
   uint64_t* full = (uint64_t*)(smem + S * L::STAGE + L::O_BYTES);   // O_BYTES >= TY*96*sizeof(V)
   uint64_t* ready = full + S;
   uint64_t* empty = ready + S;
-  double* red = (double*)(empty + S);                                // [TY][3] tile partial sums
+  uint64_t* checked = empty + S;                                     // the abort word has been read
+  double* red = (double*)(checked + 1);                              // [TY][3] tile partial sums
   volatile int* abort_flag = (volatile int*)(red + 3 * TY);
+  volatile int* quit = abort_flag + 1;                               // the abort word was set at start
 
   const int lane = threadIdx.x, warp = threadIdx.y;
   if (warp == 0 && lane == 0) {
@@ -519,12 +528,12 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       mbar_init(&ready[s], 1);
       mbar_init(&empty[s], TY);
     }
-    *abort_flag = *a.abort ? 1 : 0;  // aborted before it started: every role leaves at once
-    if (*abort_flag) atomicExch(a.err, 2);
+    mbar_init(checked, 1);
+    *abort_flag = 0;
+    *quit = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  if (*abort_flag) return;
   auto stage = [&](unsigned gq) -> unsigned char* { return smem + (gq % S) * L::STAGE; };
   auto fail = [&]() { atomicExch(a.err, wait_error(a.abort)); };
 
@@ -574,6 +583,23 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
     if (lane != 0) return;
     unsigned G = 0;
     int bx, by, b, k0, k1, slot;
+    bool checked_abort = false;
+    // Read the abort word once, with the first copies already in flight (its latency hides under
+    // theirs); the masking warp waits for this before it releases any plane to the consumers, so a
+    // kernel that starts aborted writes nothing.  Returns true if the CTA must stop.
+    auto check_abort = [&]() -> bool {
+      checked_abort = true;
+      const bool stop = *a.abort != 0;
+      if (stop) {
+        *quit = 1;
+        atomicExch(a.err, 2);
+      }
+      mbar_arrive(checked);
+      return stop;
+    };
+    auto drain_all = [&]() {  // every copy this warp issued lands before the CTA retires
+      for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1, nullptr);
+    };
     while (next(bx, by, b, k0, k1, slot)) {
       if (epi.status && epi.status[b] != 0) continue;  // the same skip in every role
       const int i0 = bx * TX, j0 = by * TY;
@@ -590,6 +616,10 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
         for (int p = k0 - 1; p < k0 - 1 + S + a.pf; ++p) prefetch(p);
       for (int p = k0 - 1; p <= k1; ++p, ++G) {
         const unsigned s = G % S, use = G / S;
+        if (use > 0 && !checked_abort && check_abort()) {
+          drain_all();
+          return;
+        }
         if (use > 0 && !mbar_wait_handoff(&empty[s], (use - 1) & 1, a.abort)) {
           // record; the copies still in flight are the last (at most S - 1) issued: let them land
           fail();
@@ -605,9 +635,13 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
         if (kU) tma_load_4d(st + L::U_OFF, &tm_u, L::CE * 3 * i0, j0, p, b, &full[s]);
         if (a.pf && p - (k0 - 1) >= S) prefetch(p + a.pf);
       }
+      if (!checked_abort && check_abort()) {  // a first segment shorter than the ring
+        drain_all();
+        return;
+      }
     }
-    // every copy lands before the CTA retires
-    for (unsigned d = 1; d <= S && d <= G; ++d) (void)mbar_wait_handoff(&full[(G - d) % S], ((G - d) / S) & 1, nullptr);
+    if (!checked_abort) mbar_arrive(checked);  // no work: nobody waits, but keep the protocol whole
+    drain_all();
     return;
   }
 
@@ -615,9 +649,17 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
     // ---------------- masking warp: zero the masked edges of each landed plane ----------------
     unsigned G = 0;
     int bx, by, b, k0, k1, slot;
+    bool released = false;
     while (next(bx, by, b, k0, k1, slot)) {
       if (epi.status && epi.status[b] != 0) continue;
       const int nplanes = k1 - k0 + 2;
+      if (!released) {  // nothing reaches the consumers before the issuing warp has read the abort word
+        if (!__all_sync(0xffffffffu, mbar_wait_handoff(checked, 0, a.abort)) || *quit) {
+          if (lane == 0) fail();
+          return;
+        }
+        released = true;
+      }
       for (int q = 0; q < nplanes; ++q, ++G) {
         if (!__all_sync(0xffffffffu, mbar_wait_handoff(&full[G % S], (G / S) & 1, a.abort))) {  // warp-uniform
           if (lane == 0) fail();
@@ -959,7 +1001,7 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
   dim3 block(TX, WS ? TY + 2 : TY, 1);
   const bool ku = e.mode == FIT_EPI_DOT_U || e.mode == FIT_EPI_RESID;
   int smem = ku ? Layout<T, TY, true>::smem(S) : Layout<T, TY, false>::smem(S);
-  if (WS) smem += 3 * 8 * S + 8 * 3 * TY + 16;  // three barriers per stage, row partial sums, abort flag
+  if (WS) smem += 3 * 8 * S + 8 + 8 * 3 * TY + 16;  // three barriers per stage, the abort check, row sums, flags
   auto run = [&](auto kern) -> fit_status {
     if (smem > fused_smem_limit()) {  // this ring depth and epilogue staging exceed an SM's shared memory
       fit_set_error("fused apply: launch shape does not fit on an SM");
@@ -1087,7 +1129,7 @@ int variant_smem(const Variant& v, bool ku) {
 #define FIT_SM(TY_, S_, WS_)                                                                              \
   if (v.ty == TY_ && v.stages == S_ && v.ws == WS_)                                                       \
     return (ku ? Layout<T, TY_, true>::smem(S_) : Layout<T, TY_, false>::smem(S_)) +                      \
-           (WS_ ? 3 * 8 * S_ + 8 * 3 * TY_ + 16 : 0)
+           (WS_ ? 3 * 8 * S_ + 8 + 8 * 3 * TY_ + 16 : 0)
   FIT_SM(4, 4, 0);
   FIT_SM(8, 4, 0);
   FIT_SM(16, 3, 0);

@@ -53,10 +53,10 @@ struct fit_grid {
 };
 
 struct fit_unet;
-// z = scale_out * U(scale_in * v) for one complex64 vector of the grid (x16: [ncell][16] bf16 scratch)
-// (plus dinv (.) v when dinv is given: the Jacobi term of the preconditioner)
+// z = scale_out * U(scale_in * v) for one complex64 vector of the grid (x16: [ncell][16] bf16 scratch),
+// plus jac_scale * dinv (.) jac_v when dinv is given (a multiple of a Jacobi direction)
 fit_status fit_unet_apply_vec(fit_unet* u, const fit_grid* g, const void* v, void* z, float scale_in, float scale_out,
-                              void* x16, const void* dinv, cudaStream_t s);
+                              void* x16, const void* dinv, const void* jac_v, float jac_scale, cudaStream_t s);
 // size the network's activations for the grid and refresh its bf16 weights (call before capture)
 fit_status fit_unet_prepare(fit_unet* u, const fit_grid* g, cudaStream_t s);
 

@@ -81,7 +81,7 @@ struct P {
   double tiny;       // breakdown threshold for the inner precision
   int stall;         // inner solve stops after this many iterations without a new minimum
   int precond;       // right preconditioner of the inner solve (FIT_PC_*)
-  int pc_every;      // FIT_PC_UNET: Arnoldi steps j with j % pc_every == 0 go through the network
+  int pc_every;      // FIT_PC_UNET: Arnoldi steps j with (j + 1) % pc_every == 0 take the network's direction
   const volatile int* abort;  // the grid's abort word (pinned host memory), polled by the loop conditions
   int* err;                   // the grid's error word: set to 2 when the abort word ends the loops
 };
@@ -1798,21 +1798,28 @@ struct Seq {
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
-    } else if (w.pc == FIT_PC_UNET && (j % w.p.pc_every) != 0) {
-      // the other Arnoldi steps use the Jacobi term alone: the flexible method may vary the
-      // preconditioner per step, and with plain-Jacobi directions in the basis the residual
-      // minimisation never depends only on the network's directions
+    } else if (w.pc == FIT_PC_UNET && ((j + 1) % w.p.pc_every) != 0) {
+      // every other step of the cycle: the Jacobi term
       k_fg_precond_diag<T><<<vgrid(), 256, 0, s>>>((const V*)w.Vb, (V*)w.Zb, j, (const V*)w.dinv, w.sys, w.p);
       check();
       zin = (const char*)w.Zb + (size_t)j * vecb;
     } else if (w.pc == FIT_PC_UNET) {
-      // z = D^-1 v + U(v) with v of unit norm: the network sees v / rms(v) = sqrt(n_e) v
+      // The network's direction: z_j = U(v_i) / sqrt(n_e) + 1e-3 D^-1 v_j with i = j + 1 - pc_every and
+      // v_i of unit norm (the network sees v / rms(v) = sqrt(n_e) v).  By default pc_every = m: the last
+      // step of the cycle takes the network's answer for the cycle's first vector, the normalised true
+      // residual, which U (trained on residual -> error-direction pairs) maps to the direction of the
+      // current error.  Every earlier step is a Jacobi step, so the cycle's subspace is the Jacobi
+      // Krylov subspace of m - 1 steps plus the network's direction: flexible GMRES minimises the
+      // residual over whatever directions z_j it is given (their scale is immaterial), and a poor
+      // network costs one direction, not the cycle.  The small Jacobi term keeps z_j a usable direction
+      // when the network outputs zero (an untrained network, whose head starts at zero, then gives
+      // exactly Jacobi FGMRES).
       const float sin = (float)sqrt((double)w.p.ne), sout = 1.0f / sin;
+      const char* vin = (const char*)w.Vb + (size_t)(j + 1 - w.p.pc_every) * vecb;
       for (int b = 0; b < w.p.B; ++b) {
         const size_t off = (size_t)b * w.p.ne * w.esz;
-        fit_status r = fit_unet_apply_vec(w.g->unet, w.g, (const char*)w.Vb + (size_t)j * vecb + off,
-                                          (char*)w.Zb + (size_t)j * vecb + off, sin, sout, w.x16,
-                                          (const char*)w.dinv + off, s);
+        fit_status r = fit_unet_apply_vec(w.g->unet, w.g, vin + off, (char*)w.Zb + (size_t)j * vecb + off, sin,
+                                          sout, w.x16, (const char*)w.dinv + off, vj + off, 1e-3f, s);
         if (r != FIT_OK && st == FIT_OK) st = r;
       }
       zin = (const char*)w.Zb + (size_t)j * vecb;
@@ -2142,7 +2149,7 @@ void fit_solve_opts_default(fit_solve_opts* o) {
   o->history = nullptr;
   o->history_len = 0;
   o->history_every = 1;
-  o->pc_every = 2;
+  o->pc_every = 0;
 }
 
 fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rhs, void* x, double tol,
@@ -2171,7 +2178,7 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
   FIT_REQUIRE(o.max_iter >= 1 && o.max_outer >= 1, "fit_solve: iteration caps must be >= 1");
   FIT_REQUIRE(o.inner_tol > 0 && o.inner_tol < 1, "fit_solve: inner_tol must be in (0, 1)");
   FIT_REQUIRE(!o.history || (o.history_len >= 1 && o.history_every >= 1), "fit_solve: bad history options");
-  FIT_REQUIRE(o.pc_every >= 1, "fit_solve: pc_every must be >= 1");
+  FIT_REQUIRE(o.pc_every >= 0, "fit_solve: pc_every must be >= 0");
   FIT_REQUIRE(!o.history || o.batch == 0 || o.batch >= nfreq, "fit_solve: history needs all systems in one batch");
   for (int f = 0; f < nfreq; ++f) FIT_REQUIRE(isfinite(omega[f]), "fit_solve: omega must be finite");
   if (fit_check_abort(g, "fit_solve") != FIT_OK) return FIT_ETIMEOUT;
@@ -2205,7 +2212,7 @@ fit_status fit_solve(fit_grid* g, int nfreq, const double* omega, const void* rh
     w.p.inner_tol = o.inner_tol;
     w.p.max_iter = o.max_iter;
     w.p.max_outer = o.max_outer;
-    w.p.pc_every = o.pc_every;
+    w.p.pc_every = o.pc_every > 0 ? o.pc_every : w.m;  // 0: once per cycle, at its last step
     FIT_CHECK_CUDA(cudaMemcpyAsync(w.omega, omega + f0, nb * sizeof(double), cudaMemcpyHostToDevice, s));
     const double2* rb = (const double2*)rhs + (size_t)f0 * g->ne;
     double2* xb = (double2*)x + (size_t)f0 * g->ne;

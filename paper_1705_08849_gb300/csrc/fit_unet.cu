@@ -415,11 +415,11 @@ __global__ void pack_kernel(const float2* __restrict__ r, float scale, const bf1
   }
 }
 
-// z[3c + w] = scale * (y[c][2w] + j y[c][2w+1]) (zero on masked edges) + dinv[3c + w] * v[3c + w]
+// z[3c + w] = scale * (y[c][2w] + j y[c][2w+1]) (zero on masked edges) + jac * dinv[3c + w] * v[3c + w]
 // when a Jacobi term is given (dinv, v non-null)
 __global__ void unpack_kernel(const float* __restrict__ y, float scale, const uint8_t* __restrict__ mask, int nx, int ny,
                               int nxp, float2* z, long long ncell, const float2* __restrict__ dinv,
-                              const float2* __restrict__ v) {
+                              const float2* __restrict__ v, float jac) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
     const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
     const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
@@ -428,8 +428,8 @@ __global__ void unpack_kernel(const float* __restrict__ y, float scale, const ui
       float2 o = ((m >> w) & 1) ? make_float2(0.f, 0.f) : make_float2(scale * y[6 * c + 2 * w], scale * y[6 * c + 2 * w + 1]);
       if (dinv) {
         const float2 d = dinv[3 * c + w], vv = v[3 * c + w];
-        o.x += d.x * vv.x - d.y * vv.y;
-        o.y += d.x * vv.y + d.y * vv.x;
+        o.x += jac * (d.x * vv.x - d.y * vv.y);
+        o.y += jac * (d.x * vv.y + d.y * vv.x);
       }
       z[3 * c + w] = o;
     }
@@ -452,12 +452,21 @@ __global__ void pack_target_kernel(const double2* __restrict__ e, double scale, 
 }
 
 // ---- training pairs ------------------------------------------------------------------------------
-// The partial sums of ||r||^2 written by the apply's residual epilogue (slot q2), summed in a fixed
-// order by one block: out[0] = ||r||^2.
-__global__ void __launch_bounds__(256) pair_norm_kernel(const double* __restrict__ part, long long nslots, double* out) {
+// ||xs - xk||^2 (or ||xs||^2 when xk is null) over the unmasked edges, one block, fixed order: out[0]
+__global__ void __launch_bounds__(256) pair_err_norm_kernel(const double2* __restrict__ xk, const double2* __restrict__ xs,
+                                                            const uint8_t* __restrict__ mask, int nx, int ny, int nxp,
+                                                            long long ncell, double* out) {
   __shared__ double red[256];
   double acc = 0.0;
-  for (long long q = threadIdx.x; q < nslots; q += 256) acc += part[4 * q + 2];
+  for (long long c = threadIdx.x; c < ncell; c += 256) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
+    for (int w = 0; w < 3; ++w)
+      if (!((m >> w) & 1)) {
+        const double2 a = xk ? xk[3 * c + w] : make_double2(0.0, 0.0), b = xs[3 * c + w];
+        acc += (b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y);
+      }
+  }
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
@@ -467,14 +476,14 @@ __global__ void __launch_bounds__(256) pair_norm_kernel(const double* __restrict
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
-// pair[c][0..5] = r / rms, pair[c][6..11] = ((x* - x_k) - D^-1 r) / (s rms), both bf16 and zero on masked
-// edges; rms = sqrt(||r||^2 / n_e), D the SI Jacobi diagonal (Eq. Precond)
+// pair[c][0..5] = r / rms(r), pair[c][6..11] = (x* - x_k) / rms(x* - x_k), both bf16 and zero on masked
+// edges; rms(v) = sqrt(||v||^2 / n_e) with the squared norms in nrm2[0] (residual) and nrm2[1] (error)
 __global__ void pair_pack_kernel(const double2* __restrict__ r, const double2* __restrict__ xk,
-                                 const double2* __restrict__ xs, const double* __restrict__ nrm2, const double* nu,
-                                 const double* ek, const uint8_t* __restrict__ mask, double omega, int nx, int ny, int nxp,
-                                 long long ncell, double s, bf16* pair) {
-  const double rms = sqrt(nrm2[0] / (3.0 * (double)ncell));
-  const double ir = rms > 0.0 ? 1.0 / rms : 0.0, it = rms > 0.0 ? 1.0 / (s * rms) : 0.0;
+                                 const double2* __restrict__ xs, const double* __restrict__ nrm2,
+                                 const uint8_t* __restrict__ mask, int nx, int ny, int nxp, long long ncell, bf16* pair) {
+  const double ne = 3.0 * (double)ncell;
+  const double rr2 = nrm2[0] / ne, re2 = nrm2[1] / ne;
+  const double ir = rr2 > 0.0 ? 1.0 / sqrt(rr2) : 0.0, ie = re2 > 0.0 ? 1.0 / sqrt(re2) : 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
     const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
@@ -484,11 +493,8 @@ __global__ void pair_pack_kernel(const double2* __restrict__ r, const double2* _
       double2 in = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
       if (!((m >> w) & 1)) {
         const double2 rr = r[3 * c + w], a = xk[3 * c + w], b = xs[3 * c + w];
-        const double2 d = fit_jacobi_diag<double>(nu, ek, i, j, k, w, nxp, ny, omega);
-        const double den = d.x * d.x + d.y * d.y;
-        const double2 dr = make_double2((rr.x * d.x + rr.y * d.y) / den, (rr.y * d.x - rr.x * d.y) / den);
         in = make_double2(rr.x * ir, rr.y * ir);
-        t = make_double2((b.x - a.x - dr.x) * it, (b.y - a.y - dr.y) * it);
+        t = make_double2((b.x - a.x) * ie, (b.y - a.y) * ie);
       }
       v[2 * w] = __float2bfloat16((float)in.x);
       v[2 * w + 1] = __float2bfloat16((float)in.y);
@@ -525,13 +531,13 @@ __global__ void pair_sample_kernel(const bf16* __restrict__ pair, const bf16* __
 // Used by the solver: z = scale_out * U(scale_in * v) for one complex64 vector (pack, forward,
 // unpack); all launches are stream-ordered and capturable.
 fit_status fit_unet_apply_vec(fit_unet* u, const fit_grid* g, const void* v, void* z, float scale_in, float scale_out,
-                              void* x16, const void* dinv, cudaStream_t s) {
+                              void* x16, const void* dinv, const void* jac_v, float jac_scale, cudaStream_t s) {
   UCK(check_dims(g->nx, g->ny, g->nz));
   UCK(alloc_acts(u, g->nx, g->ny, g->nz));
   pack_kernel<<<nblocks(g->ncell), 256, 0, s>>>((const float2*)v, scale_in, (const bf16*)g->mat16, (bf16*)x16, g->ncell);
   UCK(forward(u, (const bf16*)x16, s));
   unpack_kernel<<<nblocks(g->ncell), 256, 0, s>>>(u->Y, scale_out, g->mask, g->nx, g->ny, g->nxp, (float2*)z, g->ncell,
-                                                  (const float2*)dinv, (const float2*)v);
+                                                  (const float2*)dinv, (const float2*)jac_v, jac_scale);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
@@ -684,7 +690,7 @@ fit_status fit_unet_unpack(const fit_grid* g, const float* y6, double scale, voi
   FIT_REQUIRE(g && y6 && z, "fit_unet_unpack: null argument");
   FIT_CHECK_CUDA(cudaSetDevice(g->device));
   unpack_kernel<<<nblocks(g->ncell), 256, 0, (cudaStream_t)stream>>>(y6, (float)scale, g->mask, g->nx, g->ny, g->nxp,
-                                                                      (float2*)z, g->ncell, nullptr, nullptr);
+                                                                      (float2*)z, g->ncell, nullptr, nullptr, 0.f);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
@@ -827,8 +833,9 @@ fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, con
   if ((st = tmp.copy(&d_om, &omega, sizeof(double), s)) != FIT_OK) return st;
   if ((st = tmp.alloc(&r, (size_t)g->ne * sizeof(double2))) != FIT_OK) return st;
   if ((st = tmp.alloc(&part, (size_t)nslots * 4 * sizeof(double))) != FIT_OK) return st;
-  if ((st = tmp.alloc(&nrm, sizeof(double))) != FIT_OK) return st;
-  // r = b - A x_k in FP64 with its squared norm from the residual epilogue
+  if ((st = tmp.alloc(&nrm, 2 * sizeof(double))) != FIT_OK) return st;
+  // r = b - A x_k in FP64 (the residual epilogue; its norm partials are not used: the norms below skip the
+  // masked edges)
   fit_epi e;
   e.mode = FIT_EPI_RESID;
   e.u = b;
@@ -838,15 +845,18 @@ fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, con
     fit_set_error("fit_unet_training_pair: the apply wrote more partial slots than were allocated");
     return FIT_ECUDA;
   }
-  pair_norm_kernel<<<1, 256, 0, s>>>((const double*)part, e.nslots, (double*)nrm);
+  pair_err_norm_kernel<<<1, 256, 0, s>>>(nullptr, (const double2*)r, g->mask, g->nx, g->ny, g->nxp, g->ncell,
+                                         (double*)nrm);
+  pair_err_norm_kernel<<<1, 256, 0, s>>>((const double2*)xk, (const double2*)xstar, g->mask, g->nx, g->ny, g->nxp,
+                                         g->ncell, (double*)nrm + 1);
   pair_pack_kernel<<<nblocks(g->ncell), 256, 0, s>>>((const double2*)r, (const double2*)xk, (const double2*)xstar,
-                                                     (const double*)nrm, g->nu64, g->ek64, g->mask, omega, g->nx,
-                                                     g->ny, g->nxp, g->ncell, g->coef_scale, (bf16*)pair);
+                                                     (const double*)nrm, g->mask, g->nx, g->ny, g->nxp, g->ncell,
+                                                     (bf16*)pair);
   FIT_CHECK_CUDA(cudaGetLastError());
   double n2 = 0.0;
   FIT_CHECK_CUDA(cudaMemcpyAsync(&n2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
   FIT_CHECK_CUDA(cudaStreamSynchronize(s));  // the temporaries are freed on return
-  if (rms_out) *rms_out = sqrt(n2 / (double)g->ne);
+  if (rms_out) *rms_out = sqrt(n2 / (double)g->ne);  // rms(r) over the unmasked edges
   return fit_take_device_error(g);
 }
 

@@ -19,7 +19,7 @@ class _Consts:
     ("bicgstab-mixed+eps", (0, 1, 3)),
     ("fgmres-c128+jacobi", (1, 0, 1)),
     ("fgmres-mixed+unet", (1, 1, 2)),
-    ("mixed+unet@0", (1, 1, 2)),
+    ("mixed+unet/3", (1, 1, 2)),
 ])
 def test_parse_kind(kind, want):
     assert bench.valid_kind(kind)
@@ -27,12 +27,12 @@ def test_parse_kind(kind, want):
 
 
 def test_learned_kinds_place_the_network():
-    assert bench.parse_kind(_Consts, "fgmres-mixed+unet")[4] == 2  # every other Arnoldi step
-    assert bench.parse_kind(_Consts, "fgmres-mixed+unet@0")[4] == 30  # each cycle's first vector
+    assert bench.parse_kind(_Consts, "fgmres-mixed+unet")[4] == 0  # once per restart cycle (the default)
+    assert bench.parse_kind(_Consts, "fgmres-mixed+unet/3")[4] == 3  # steps j = 1 mod 3
 
 
 @pytest.mark.parametrize("kind", ["cocg", "cocg-fp32", "gmres-mixed", "cocg-mixed+ilu", "none", "",
-                                  "cocg-mixed+unet", "fgmres-c128+unet"])
+                                  "cocg-mixed+unet", "fgmres-c128+unet", "mixed+unet/1", "mixed+unet/x"])
 def test_invalid_kinds_are_dropped(kind):
     assert not bench.valid_kind(kind)
 

@@ -155,12 +155,12 @@ def _he_params(seed, head_scale):
     return np.concatenate(p).astype(np.float32)
 
 
-def _oracle_unet_precond(case, w, p, s):
-    """The learned right preconditioner written out with the oracle: for Arnoldi step j of a cycle,
-    M(v) = D^-1 v on odd steps and D^-1 v + s rms(v) unpack(U(pack(v / rms(v)))) on even steps, with D the
-    Jacobi diagonal (Eq. Precond), U the oracle network on bf16-rounded inputs, the input channels the
-    residual's (Re, Im) per component then eps_r/10, log10(1+sigma)/8, 1/mu_r and the cell size in mm,
-    and s the scale of the complex64 inner operator (the network's units).  Returns (M, A, mask)."""
+def _oracle_unet_precond(case, w, p, m):
+    """The learned right preconditioner written out with the oracle, for Arnoldi step j of a cycle of m
+    steps with basis V: z_j = D^-1 v_j (the Jacobi diagonal of Eq. Precond) except at the last step
+    j = m - 1, where z = unpack(U(pack(v_0 / rms(v_0)))) / sqrt(n_e) + 1e-3 D^-1 v_j, U the oracle network on
+    bf16-rounded inputs whose channels are the vector's (Re, Im) per component then eps_r/10,
+    log10(1+sigma)/8, 1/mu_r and the cell size in mm.  Returns (M, A, mask, d)."""
     import torch
     from oracle import fit as F
     from oracle import unet as U
@@ -176,10 +176,10 @@ def _oracle_unet_precond(case, w, p, s):
     mat[..., 3] = np.cbrt(case["dz"][:, None, None] * case["dy"][None, :, None] * case["dx"][None, None, :]) * 1e3
     P = U.unflatten(p.astype(np.float64))
 
-    def M(v, j):
-        z = v / d
-        if j % 2:
-            return z
+    def M(V, j):
+        if j != m - 1:
+            return V[j] / d
+        v = V[0]
         rms = np.linalg.norm(v) / np.sqrt(ne)
         vv = (v / rms).reshape(nz, ny, nx, 3)
         x16 = np.zeros((nz, ny, nx, 16))
@@ -188,31 +188,28 @@ def _oracle_unet_precond(case, w, p, s):
         x16[..., 6:10] = mat
         x16 = torch.as_tensor(x16).to(torch.bfloat16).double().numpy()
         y = U.forward(P, x16, bf16=True).numpy()
-        u = (y[..., 0::2] + 1j * y[..., 1::2]).reshape(-1) * (1 - mask)
-        return z + s * rms * u
+        return (y[..., 0::2] + 1j * y[..., 1::2]).reshape(-1) * (1 - mask) / np.sqrt(ne) + 1e-3 * V[j] / d
 
-    return M, A, mask
+    return M, A, mask, d
 
 
 def test_fgmres_with_a_nonzero_network_matches_the_oracle():
-    """FGMRES(10) with a network whose head is non-zero (so every even Arnoldi step goes through the
-    pack, the network, the unpack scale and the rms term) against the oracle's FGMRES with the same
-    preconditioner written out: the true residual after each of the first three restart cycles agrees
-    within bf16 noise (2%; the network changes it by about 19% against Jacobi alone on this system),
-    and the full solve reaches 1e-8 under the oracle's residual."""
+    """FGMRES(10) with a network whose head is non-zero (so the last step of every cycle goes through the
+    pack, the network and the unpack scale) against the oracle's FGMRES with the same preconditioner
+    written out: the true residual after each of the first three restart cycles agrees within bf16 noise
+    (2%), and the full solve reaches 1e-8 under the oracle's residual."""
     torch = torch_cuda()
     fit = fitlib()
     from oracle import krylov as K
     case = G.small_random(16, 16, 12, seed=22, pec_frac=0.05)
     w = 2 * np.pi * 4e9
     p = _he_params(5, 0.2)
-    me, mk, mn, mask0 = oracle_matrices(case)
-    M, A, mask = _oracle_unet_precond(case, w, p, 1.0 / mn.max())
+    M, A, mask, d = _oracle_unet_precond(case, w, p, 10)
     b = G.random_vector(A.shape[0], 7) * (1 - mask)
     hist, hist_j = [], []
     K.fgmres(A, b, tol=1e-8, restart=10, maxiter=30, precond=M, precond_step=True, history=hist)
-    K.fgmres(A, b, tol=1e-8, restart=10, maxiter=30, precond=lambda v, j: M(v, 1), precond_step=True, history=hist_j)
-    assert abs(hist[0] / hist_j[0] - 1) > 0.1  # the network matters on this system
+    K.fgmres(A, b, tol=1e-8, restart=10, maxiter=30, precond=lambda v: v / d, history=hist_j)
+    assert abs(hist[0] / hist_j[0] - 1) > 0.1  # the network's direction matters on this system
     net = fit.UNet(seed=0)
     net.set_params(p)
     with fit.Grid.from_case(case) as g:
@@ -235,10 +232,10 @@ def test_fgmres_with_a_nonzero_network_matches_the_oracle():
 
 
 def test_training_pair_matches_the_oracle():
-    """fit_unet_training_pair against the pair written out with the oracle: r = b - A x_k, rms = ||r|| /
-    sqrt(n_e), input r / rms and target ((x* - x_k) - D^-1 r) / (s rms) with the Jacobi diagonal D, both
-    zero on masked edges and within one bf16 ulp; then fit_unet_pair_sample assembles the network input
-    (residual channels, the material channels of fit_unet_pack, zeros) and the FP32 target."""
+    """fit_unet_training_pair against the pair written out with the oracle: r = b - A x_k and e = x* - x_k,
+    input r / rms(r) and target e / rms(e) (rms over the unmasked edges), both zero on masked edges and
+    within one bf16 ulp; then fit_unet_pair_sample assembles the network input (residual channels, the
+    material channels of fit_unet_pack, zeros) and the FP32 target."""
     torch = torch_cuda()
     fit = fitlib()
     from oracle import fit as F
@@ -247,14 +244,13 @@ def test_training_pair_matches_the_oracle():
     w = 2 * np.pi * 6e9
     me, mk, mn, mask = oracle_matrices(case)
     A = F.system_matrix(w, F.curl(nx, ny, nz), me, mk, mn, mask)
-    d = F.jacobi_diagonal(w, nx, ny, nz, me, mk, mn, mask)
     ne = A.shape[0]
-    xk, xs, b = (G.random_vector(ne, sd) * (1 - mask) for sd in (1, 2, 3))
-    s = 1.0 / mn.max()
-    r = b - A @ xk
+    xk, xs, b = (G.random_vector(ne, sd) for sd in (1, 2, 3))  # masked entries must not count
+    r = (b - A @ xk) * (1 - mask)
+    e = (xs - xk) * (1 - mask)
     rms = np.linalg.norm(r) / np.sqrt(ne)
-    want_in = (r / rms) * (1 - mask)
-    want_t = ((xs - xk) - r / d) / (s * rms) * (1 - mask)
+    want_in = r / rms
+    want_t = e / (np.linalg.norm(e) / np.sqrt(ne))
     with fit.Grid.from_case(case) as g:
         pair = torch.empty(ne // 3, 12, dtype=torch.bfloat16, device="cuda")
         got_rms = fit.fit_unet_training_pair(g.h, w, *(torch.from_numpy(v).cuda() for v in (xk, xs, b)), pair)
