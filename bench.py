@@ -415,7 +415,7 @@ def main():
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length of the sweep mode")
     ap.add_argument("--seq-max-iter", type=int, default=0, help="sweep mode: iteration cap of the sequential solves "
                     "(0: --max-iter)")
-    ap.add_argument("--e2e-chunks", type=int, default=4, help="end-to-end leg: each host<->device copy is split into "
+    ap.add_argument("--e2e-chunks", type=int, default=1, help="end-to-end leg: each host<->device copy is split into "
                     "this many pieces on as many streams (several copy engines per direction)")
     ap.add_argument("--graph", type=int, default=1, help="1: the solve runs as one CUDA graph; 0: host-driven loop "
                     "(for per-kernel profiling)")

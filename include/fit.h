@@ -370,6 +370,21 @@ fit_status fit_unet_training_pair(fit_grid* g, double omega, const void* xk, con
 fit_status fit_unet_pair_sample(long long ncell, const void* pair, const void* base16, void* in16, float* target6,
                                 void* stream);
 
+/* fit_unet_train_step_residual -- one Adam step of the network on the residual-angle loss of one input:
+ * with r^ the normalised residual in the input's first six channels (in16 as fit_unet_pair_sample builds
+ * it, on this grid), z = U(in16) as a complex64 vector (zero on masked edges) and w = A_in(omega) z (the
+ * scaled complex64 operator the network serves),
+ *     L = 1 - |<w, r^>|^2 / (||w||^2 ||r^||^2),
+ * the fraction of the residual that the direction z cannot remove: what flexible GMRES gains from the
+ * network's direction, which it may scale freely.  The gradient goes through the apply's adjoint
+ * (A^H = conj(A), A complex symmetric).  *loss receives L before the step (the call synchronises).
+ * The network keeps four complex64 work vectors of the grid's size between calls. */
+fit_status fit_unet_train_step_residual(fit_unet* net, fit_grid* g, double omega, const void* in16, float lr,
+                                        double* loss, void* stream);
+/* fit_unet_residual_loss -- that loss without a step (validation); synchronising. */
+fit_status fit_unet_residual_loss(fit_unet* net, fit_grid* g, double omega, const void* in16, double* loss,
+                                  void* stream);
+
 /* attach a network to the grid; fit_solve with precond = FIT_PC_UNET (FGMRES, FIT_SOLVE_MIXED) then
  * gives flexible GMRES one direction from the network per restart cycle (see fit_solve_opts.pc_every):
  * z_1 = U(v_0) / sqrt(n_e) + 1e-3 D^-1 v_1, v_0 the normalised residual of the cycle, which the network

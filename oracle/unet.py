@@ -217,3 +217,35 @@ def head_fwd(x, w, b):
 def head_bwd(x, dout, w):
     """Gradients of ``head_fwd`` for the loss sum(out * dout): (din, dW, db)."""
     return dout @ w, dout.T @ x, dout.sum(axis=0)
+
+
+class _SparseApply(torch.autograd.Function):
+    """w = A z for a complex symmetric scipy sparse A (A^T = A), with the adjoint A^H = conj(A) in the
+    backward pass: d conj(z) = A^H d conj(w)."""
+
+    @staticmethod
+    def forward(ctx, z, A):
+        ctx.A = A
+        return torch.as_tensor(A @ z.detach().numpy())
+
+    @staticmethod
+    def backward(ctx, gw):
+        return torch.as_tensor(ctx.A.conj() @ gw.numpy()), None
+
+
+def residual_angle_loss_and_grad(flat, x_ndhwc, A_in, mask):
+    """The residual-angle loss of the network for one input and its gradient by autograd: r = the complex
+    vector of the input's first six channels (zero on masked edges), z = U(x) as a complex vector (zero on
+    masked edges), w = A_in z, L = 1 - |<w, r>|^2 / (||w||^2 ||r||^2).  bf16 rounding as in ``forward``.
+    Returns (L, dL/dflat)."""
+    p = torch.as_tensor(np.asarray(flat, dtype=np.float64)).clone().requires_grad_(True)
+    y = forward(unflatten_t(p), x_ndhwc, bf16=True)
+    keep = torch.as_tensor(1.0 - np.asarray(mask, dtype=np.float64))
+    z = torch.complex(y[..., 0::2], y[..., 1::2]).reshape(-1) * keep
+    xb = torch.as_tensor(np.asarray(x_ndhwc, dtype=np.float64)).to(torch.bfloat16).to(torch.float64)
+    r = torch.complex(xb[..., 0:6:2], xb[..., 1:6:2]).reshape(-1) * keep
+    w = _SparseApply.apply(z, A_in)
+    c = torch.sum(torch.conj(w) * r)
+    loss = 1.0 - (c.abs() ** 2) / (torch.sum(w.abs() ** 2) * torch.sum(r.abs() ** 2))
+    loss.backward()
+    return float(loss.detach()), p.grad.numpy()

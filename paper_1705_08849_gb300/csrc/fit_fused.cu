@@ -83,6 +83,7 @@ struct FusedArgs {
   const double* omega;
   int* err;                  // the grid's error word: 1 = a bounded wait ran out, 2 = aborted
   const volatile int* abort; // the grid's abort word (pinned host memory), polled in every bounded wait
+  const volatile int* abort_first;  // its device-memory copy, read once when the first copies are issued
   int nx, ny, nz, tz, nzc, ntx, nty, ntiles;
   int nb;    // systems in the batch; tile t = (chunk, row, column) * nb + b, so that CTAs running at the
              // same time work on one column for several systems and share its coefficients in L2
@@ -201,6 +202,7 @@ __device__ inline void tma_store_4d(const CUtensorMap* tm, const void* src, int 
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 __device__ inline void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
 __device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // ---- the kernel ----------------------------------------------------------------------------------
@@ -284,10 +286,10 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
     if (tid == 0) {
       for (int q = 0; q < min(S, nplanes); ++q) issue(q);
       for (int q = S; q < S + a.pf; ++q) prefetch(q);  // the planes after the first ring fill
-      // The abort word (pinned host memory) is read once, after the first copies are on their way, so
+      // The abort word's device-memory copy is read once, after the first copies are on their way, so
       // that its latency hides under theirs; the barrier below publishes the answer before anything
       // is written.
-      if (first_tile && *a.abort) {
+      if (first_tile && *a.abort_first) {
         bad = 1;
         atomicExch(a.err, 2);
       }
@@ -584,12 +586,12 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
     unsigned G = 0;
     int bx, by, b, k0, k1, slot;
     bool checked_abort = false;
-    // Read the abort word once, with the first copies already in flight (its latency hides under
-    // theirs); the masking warp waits for this before it releases any plane to the consumers, so a
-    // kernel that starts aborted writes nothing.  Returns true if the CTA must stop.
+    // Read the abort word (its device-memory copy) once, with the first copies already in flight (its
+    // latency hides under theirs); the masking warp waits for this before it releases any plane to the
+    // consumers, so a kernel that starts aborted writes nothing.  Returns true if the CTA must stop.
     auto check_abort = [&]() -> bool {
       checked_abort = true;
-      const bool stop = *a.abort != 0;
+      const bool stop = *a.abort_first != 0;
       if (stop) {
         *quit = 1;
         atomicExch(a.err, 2);
@@ -715,8 +717,8 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       const int er = (ty + 1) * L::EW + 3 * (tx + 2);
       const int nr = (ty + 1) * L::NW + 3 * (tx + 4);
       V* stg = stg_all + ty * 96;
-      dead = !mbar_wait_handoff(&ready[G0 % S], (G0 / S) & 1, a.abort) ||
-             !mbar_wait_handoff(&ready[(G0 + 1) % S], ((G0 + 1) / S) & 1, a.abort);
+      dead = !mbar_wait_handoff(&ready[G0 % S], (G0 / S) & 1, nullptr) ||
+             !mbar_wait_handoff(&ready[(G0 + 1) % S], ((G0 + 1) / S) & 1, nullptr);
       dead = __any_sync(0xffffffffu, dead);  // warp-uniform
       if (!dead) {
         V e0[3], em[3], ejm[3];
@@ -749,7 +751,9 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
 #pragma unroll 2
         for (int k = k0; k < k1; ++k) {
           const int qk = k - k0 + 1, qn = qk + 1;
-          if (__any_sync(0xffffffffu, !mbar_wait_handoff(&ready[(G0 + qn) % S], ((G0 + qn) / S) & 1, a.abort))) {
+          // (the consumers' waits do not read the abort word: the issuing and masking warps do, and a
+          // consumer whose planes stop arriving gives up on its own bound)
+          if (__any_sync(0xffffffffu, !mbar_wait_handoff(&ready[(G0 + qn) % S], ((G0 + qn) / S) & 1, nullptr))) {
             dead = true;
             break;
           }
@@ -988,6 +992,7 @@ fit_status launch_variant(fit_grid* g, int nbatch, const double* omega_dev, cons
   a.omega = omega_dev;
   a.err = g->err_dev;
   a.abort = g->abort_dev;
+  a.abort_first = g->abort_mirror;
   a.nx = g->nx;
   a.ny = g->ny;
   a.nz = g->nz;

@@ -239,10 +239,12 @@ void fit_grid_destroy(fit_grid* g) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(g->device);
-  void* ptrs[] = {g->dx, g->dy, g->dz, g->nu64, g->ek64, g->nu32, g->ek32, g->mask, g->omega_dev, g->err_dev, g->mat16};
+  void* ptrs[] = {g->dx,       g->dy,      g->dz,      g->nu64,  g->ek64,        g->nu32,
+                  g->ek32,     g->mask,    g->omega_dev, g->err_dev, g->mat16,     g->abort_mirror};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->abort_host) cudaFreeHost(g->abort_host);
+  if (g->side) cudaStreamDestroy(g->side);
   cudaSetDevice(cur);
   delete g;
 }
@@ -278,6 +280,7 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
       (st = fit_dev_alloc(g, (void**)&g->ek32, np * 6 * sizeof(float))) ||
       (st = fit_dev_alloc(g, (void**)&g->mask, np)) ||
       (st = fit_dev_alloc(g, (void**)&g->err_dev, sizeof(int))) ||
+      (st = fit_dev_alloc(g, (void**)&g->abort_mirror, sizeof(int))) ||
       (st = fit_dev_alloc(g, (void**)&g->mat16, (size_t)g->ncell * 4 * 2))) {
     fit_grid_destroy(g);
     return st;
@@ -293,6 +296,7 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
       *g->abort_host = 0;
       e = cudaHostGetDevicePointer(&dp, hp, 0);
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       fit_set_error(std::string("fit_grid_create: abort word: ") + cudaGetErrorString(e));
       fit_grid_destroy(g);
@@ -309,6 +313,7 @@ fit_status fit_grid_create(int nx, int ny, int nz, const double* dx, const doubl
   cudaMemset(g->ek32, 0, np * 6 * sizeof(float));
   cudaMemset(g->mask, 0, np);
   cudaMemset(g->err_dev, 0, sizeof(int));
+  cudaMemset(g->abort_mirror, 0, sizeof(int));
   cudaMemset(g->mat16, 0, (size_t)g->ncell * 4 * 2);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -448,6 +453,13 @@ fit_status fit_set_abort(fit_grid* g, int value) {
   FIT_REQUIRE(g && g->abort_host, "fit_set_abort: null grid");
   FIT_REQUIRE(value == 0 || value == 1, "fit_set_abort: value must be 0 or 1");
   __atomic_store_n(g->abort_host, value, __ATOMIC_SEQ_CST);
+  // the device-memory copy the fused kernels read first: a copy on the grid's non-blocking side stream,
+  // which the copy engine carries out while kernels of other streams run
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  static thread_local int staged = 0;
+  staged = value;
+  FIT_CHECK_CUDA(cudaMemcpyAsync(g->abort_mirror, &staged, sizeof(int), cudaMemcpyHostToDevice, g->side));
+  FIT_CHECK_CUDA(cudaStreamSynchronize(g->side));
   return FIT_OK;
 }
 

@@ -47,7 +47,9 @@ struct fit_grid {
   std::map<long long, int> tuned;
   int* err_dev = nullptr;  // device error word: 1 = a bounded wait in a kernel ran out, 2 = aborted
   int* abort_host = nullptr;       // abort word in pinned, mapped host memory (fit_set_abort)
-  const int* abort_dev = nullptr;  // its device alias, polled by the persistent kernels and the solver
+  const int* abort_dev = nullptr;  // its device alias, polled by the kernels' bounded waits and the solver
+  int* abort_mirror = nullptr;     // a device-memory copy of the word, for the fused kernels' first check
+  cudaStream_t side = nullptr;     // non-blocking stream that carries the copy while other work runs
   void* mat16 = nullptr;   // [ncell][4] bf16 material channels of the learned preconditioner
   struct fit_unet* unet = nullptr;  // attached learned preconditioner (not owned)
 };

@@ -49,8 +49,15 @@ struct fit_unet {
   bf16 *A1a, *S1, *P1, *A2a, *S2, *P2, *A3a, *B3, *U2, *A2c, *B2, *U1, *A1c, *B1;
   float *Y, *dY;
   bf16 *g16a, *g16b, *g16c, *g8a, *g8b, *g8c, *g64a, *g64b, *g64c;
+  // residual-angle training: complex64 vectors of the grid (z = U's output, w = A z, the normalised
+  // residual, a scratch vector), the frequency and the reduction sums on the device
+  float2 *rz = nullptr, *rw = nullptr, *rr = nullptr, *rt = nullptr;
+  double *rom = nullptr, *rpart = nullptr, *rsum = nullptr;
+  long long rne = 0;
   ~fit_unet() {
     for (auto& b : bufs) cudaFree(b.first);
+    for (void* q : {(void*)rz, (void*)rw, (void*)rr, (void*)rt, (void*)rom, (void*)rpart, (void*)rsum})
+      if (q) cudaFree(q);
     for (int l = 0; l < kNL; ++l) {
       if (wf[l]) cudaFree(wf[l]);
       if (wt[l]) cudaFree(wt[l]);
@@ -216,6 +223,28 @@ static bool conv_use_tc() {
   return e && !strcmp(e, "tc");
 }
 
+// Weight gradient of a 3x3x3 conv on the tensor cores: dw (27 x cout x cin) and db accumulate (the caller
+// zeroes them); chunks of 1024 voxels per block, 27 taps.
+fit_status wgrad_launch(const unet::WgradArgs& w0, cudaStream_t s) {
+  unet::WgradArgs w = w0;
+  w.chunk = 1024;
+  const long long nv = (long long)w.nx * w.ny * w.nz;
+  const dim3 grid((unsigned)((nv + w.chunk - 1) / w.chunk), 27);
+  const int ci = w.c1 + w.c2, co = w.cout;
+#define FIT_WG(CO_, CI_) \
+  if (co == CO_ && ci == CI_) { unet::conv3_wgrad_mma_kernel<CO_, CI_><<<grid, 256, 0, s>>>(w); return FIT_OK; }
+  FIT_WG(16, 16);
+  FIT_WG(32, 16);
+  FIT_WG(32, 32);
+  FIT_WG(64, 32);
+  FIT_WG(64, 64);
+  FIT_WG(32, 64);
+  FIT_WG(16, 32);
+#undef FIT_WG
+  fit_set_error("U-Net: unsupported weight-gradient shape");
+  return FIT_EINVAL;
+}
+
 // conv3 launch: picks the (CIN, NC, TY) instantiation; in2/out2 implement concat / split
 fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w, const float* bias, bf16* out1, int o1,
                  bf16* out2, int o2, int nx, int ny, int nz, int relu, cudaStream_t s) {
@@ -286,6 +315,7 @@ fit_status backward(fit_unet* u, const bf16* X0, cudaStream_t s) {
   const int mx = nx / 2, my = ny / 2, mz = nz / 2, qx = nx / 4, qy = ny / 4, qz = nz / 4;
   const long long N = (long long)nx * ny * nz, N2 = N / 8, N4 = N / 64;
   FIT_CHECK_CUDA(cudaMemsetAsync(u->g, 0, u->nparams * sizeof(float), s));
+  fit_status wg_status = FIT_OK;
   auto GW = [&](int l) { return u->g + u->woff[l]; };
   auto GB = [&](int l) { return u->g + u->boff[l]; };
   auto wgrad = [&](const bf16* dy, int cout, const bf16* x1, int c1, const bf16* x2, int c2, int l, int ax, int ay,
@@ -302,13 +332,11 @@ fit_status backward(fit_unet* u, const bf16* X0, cudaStream_t s) {
     w.nx = ax;
     w.ny = ay;
     w.nz = az;
-    w.chunk = 4096;
-    const long long nv = (long long)ax * ay * az;
-    unet::conv3_wgrad_kernel<<<dim3((unsigned)((nv + 4095) / 4096), 27), 256, 0, s>>>(w);
+    if (wgrad_launch(w, s) != FIT_OK) wg_status = FIT_EINVAL;
   };
   auto relu_bwd = [&](bf16* gg, const bf16* y, long long n) { unet::relu_bwd_kernel<<<nblocks(n), 256, 0, s>>>(gg, y, n); };
   // head
-  unet::head_bwd_weight_kernel<<<(unsigned)((N + 4095) / 4096), 256, 0, s>>>(u->B1, u->dY, GW(HEAD), GB(HEAD), 16, 6, N);
+  unet::head_bwd_weight_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(u->B1, u->dY, GW(HEAD), GB(HEAD), 16, 6, N);
   unet::head_bwd_data_kernel<<<nblocks(N * 16), 256, 0, s>>>(u->dY, u->p + u->woff[HEAD], u->g16a, 16, 6, N);
   // c1d
   relu_bwd(u->g16a, u->B1, N * 16);
@@ -319,8 +347,8 @@ fit_status backward(fit_unet* u, const bf16* X0, cudaStream_t s) {
   wgrad(u->g16b, 16, u->S1, 16, u->U1, 16, C1C, nx, ny, nz);
   UCK(conv3(u->g16b, 16, nullptr, 0, u->wt[C1C], nullptr, u->g16c, 16, u->g16a, 16, nx, ny, nz, 0, s));
   // t1: d(B2) -> g8a
-  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((N2 + 1023) / 1024), 8), 256, 0, s>>>(u->B2, u->g16a, GW(T1), GB(T1), 32,
-                                                                                      16, nx, ny, nz, 1024);
+  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((N2 + 127) / 128), 8), 256, 0, s>>>(u->B2, u->g16a, GW(T1), GB(T1), 32,
+                                                                                    16, nx, ny, nz, 128);
   unet::tconv_bwd_data_kernel<<<nblocks(N2 * 32), 256, 0, s>>>(u->g16a, u->p + u->woff[T1], u->g8a, 32, 16, nx, ny, nz);
   // c2d
   relu_bwd(u->g8a, u->B2, N2 * 32);
@@ -331,8 +359,8 @@ fit_status backward(fit_unet* u, const bf16* X0, cudaStream_t s) {
   wgrad(u->g8b, 32, u->S2, 32, u->U2, 32, C2C, mx, my, mz);
   UCK(conv3(u->g8b, 32, nullptr, 0, u->wt[C2C], nullptr, u->g8c, 32, u->g8a, 32, mx, my, mz, 0, s));
   // t2: d(B3) -> g64a
-  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((N4 + 1023) / 1024), 8), 256, 0, s>>>(u->B3, u->g8a, GW(T2), GB(T2), 64,
-                                                                                      32, mx, my, mz, 1024);
+  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((N4 + 127) / 128), 8), 256, 0, s>>>(u->B3, u->g8a, GW(T2), GB(T2), 64,
+                                                                                    32, mx, my, mz, 128);
   unet::tconv_bwd_data_kernel<<<nblocks(N4 * 64), 256, 0, s>>>(u->g8a, u->p + u->woff[T2], u->g64a, 64, 32, mx, my, mz);
   // c3b
   relu_bwd(u->g64a, u->B3, N4 * 64);
@@ -364,7 +392,7 @@ fit_status backward(fit_unet* u, const bf16* X0, cudaStream_t s) {
   relu_bwd(u->g16b, u->A1a, N * 16);
   wgrad(u->g16b, 16, X0, 16, nullptr, 0, C1A, nx, ny, nz);
   FIT_CHECK_CUDA(cudaGetLastError());
-  return FIT_OK;
+  return wg_status;
 }
 
 fit_status check_dims(int nx, int ny, int nz) {
@@ -523,6 +551,87 @@ __global__ void pair_sample_kernel(const bf16* __restrict__ pair, const bf16* __
     }
     reinterpret_cast<uint4*>(in16 + 16 * c)[0] = *reinterpret_cast<uint4*>(v);
     reinterpret_cast<uint4*>(in16 + 16 * c)[1] = *reinterpret_cast<uint4*>(v + 8);
+  }
+}
+
+// ---- residual-angle loss ------------------------------------------------------------------------
+// For a normalised residual r^ (the input's first six channels) and the network's output z (complex64,
+// zero on masked edges), with w = A_in z:  L = 1 - |<w, r^>|^2 / (||w||^2 ||r^||^2), the fraction of the
+// residual that the direction z cannot remove (flexible GMRES may scale a direction freely).
+
+// r^ from the input's residual channels (bf16), zero on masked edges
+__global__ void resid_from_in16_kernel(const bf16* __restrict__ in16, const uint8_t* __restrict__ mask, int nx, int ny,
+                                       int nxp, long long ncell, float2* r) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
+    const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
+#pragma unroll
+    for (int w = 0; w < 3; ++w)
+      r[3 * c + w] = ((m >> w) & 1) ? make_float2(0.f, 0.f)
+                                    : make_float2(__bfloat162float(in16[16 * c + 2 * w]),
+                                                  __bfloat162float(in16[16 * c + 2 * w + 1]));
+  }
+}
+
+// per-block partials (fixed assignment) of Re, Im <w, r> = sum conj(w) r, ||w||^2 and ||r||^2
+__global__ void __launch_bounds__(256) angle_partials_kernel(const float2* __restrict__ w, const float2* __restrict__ r,
+                                                             long long n, double* part) {
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+    const float2 a = w[e], b = r[e];
+    acc[0] += a.x * b.x + a.y * b.y;
+    acc[1] += a.x * b.y - a.y * b.x;
+    acc[2] += a.x * a.x + a.y * a.y;
+    acc[3] += b.x * b.x + b.y * b.y;
+  }
+  fit_block_sum<float, 4>(acc, part + 4 * blockIdx.x);
+}
+
+// one block: out[0..3] = the fixed-order sums of nb partial slots
+__global__ void __launch_bounds__(256) angle_final_kernel(const double* __restrict__ part, int nb, double* out) {
+  __shared__ double red[256][4];
+  double a[4] = {0, 0, 0, 0};
+  for (int q = threadIdx.x; q < nb; q += 256)
+    for (int t = 0; t < 4; ++t) a[t] += part[4 * q + t];
+  for (int t = 0; t < 4; ++t) red[threadIdx.x][t] = a[t];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int t = 0; t < 4; ++t) red[threadIdx.x][t] += red[threadIdx.x + h][t];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int t = 0; t < 4; ++t) out[t] = red[0][t];
+}
+
+// G = dL / d conj(w) = -(conj(c) r - (|c|^2 / n) w) / (n m); writes t = conj(G), so that A t = A conj(G) and
+// conj(A t) = conj(A) G = A^H G (A^T = A) is the gradient with respect to conj(z)
+__global__ void angle_grad_kernel(const float2* __restrict__ w, const float2* __restrict__ r, const double* __restrict__ sums,
+                                  long long n, float2* t) {
+  const double cr = sums[0], ci = sums[1], nn = sums[2], mm = sums[3];
+  const bool ok = nn > 0.0 && mm > 0.0;
+  const float a = ok ? (float)(cr / (nn * mm)) : 0.f, b = ok ? (float)(-ci / (nn * mm)) : 0.f;  // conj(c) / (n m)
+  const float q = ok ? (float)((cr * cr + ci * ci) / (nn * nn * mm)) : 0.f;                    // |c|^2 / (n^2 m)
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float2 rv = r[e], wv = w[e];
+    const float gx = -(a * rv.x - b * rv.y - q * wv.x), gy = -(a * rv.y + b * rv.x - q * wv.y);
+    t[e] = make_float2(gx, -gy);
+  }
+}
+
+// dL/dY from the gradient conj(A t) with respect to conj(z): dY[c][2w] = 2 Re, dY[c][2w+1] = 2 Im (0 masked)
+__global__ void angle_dy_kernel(const float2* __restrict__ at, const uint8_t* __restrict__ mask, int nx, int ny, int nxp,
+                                long long ncell, float* dy) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
+    const uint8_t m = mask[i + (long long)nxp * (j + (long long)ny * k)];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      const float2 g = at[3 * c + w];  // A t = conj(gradient)
+      const bool off = (m >> w) & 1;
+      dy[6 * c + 2 * w] = off ? 0.f : 2.f * g.x;
+      dy[6 * c + 2 * w + 1] = off ? 0.f : -2.f * g.y;
+    }
   }
 }
 
@@ -761,9 +870,7 @@ fit_status fit_unet_conv3_wgrad(int nx, int ny, int nz, int cin, int cout, const
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
-  a.chunk = 4096;
-  const long long nv = (long long)nx * ny * nz;
-  unet::conv3_wgrad_kernel<<<dim3((unsigned)((nv + 4095) / 4096), 27), 256, 0, s>>>(a);
+  UCK(wgrad_launch(a, s));
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
@@ -790,8 +897,8 @@ fit_status fit_unet_tconv_backward(int mx, int my, int mz, int cin, int cout, co
   FIT_CHECK_CUDA(cudaMemsetAsync(dw, 0, (size_t)8 * cin * cout * sizeof(float), s));
   FIT_CHECK_CUDA(cudaMemsetAsync(db, 0, (size_t)cout * sizeof(float), s));
   unet::tconv_bwd_data_kernel<<<nblocks(nc * cin), 256, 0, s>>>((const bf16*)dout, w, (bf16*)din, cin, cout, nx, ny, nz);
-  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((nc + 1023) / 1024), 8), 256, 0, s>>>(
-      (const bf16*)in, (const bf16*)dout, dw, db, cin, cout, nx, ny, nz, 1024);
+  unet::tconv_bwd_weight_kernel<<<dim3((unsigned)((nc + 127) / 128), 8), 256, 0, s>>>(
+      (const bf16*)in, (const bf16*)dout, dw, db, cin, cout, nx, ny, nz, 128);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
@@ -810,8 +917,8 @@ fit_status fit_unet_head_backward(long long nvox, const void* in, const float* d
   cudaStream_t s = (cudaStream_t)stream;
   FIT_CHECK_CUDA(cudaMemsetAsync(dw, 0, 6 * 16 * sizeof(float), s));
   FIT_CHECK_CUDA(cudaMemsetAsync(db, 0, 6 * sizeof(float), s));
-  unet::head_bwd_weight_kernel<<<(unsigned)((nvox + 4095) / 4096), 256, 0, s>>>((const bf16*)in, dout, dw, db, 16, 6,
-                                                                                nvox);
+  unet::head_bwd_weight_kernel<<<(unsigned)((nvox + 255) / 256), 256, 0, s>>>((const bf16*)in, dout, dw, db, 16, 6,
+                                                                              nvox);
   unet::head_bwd_data_kernel<<<nblocks(nvox * 16), 256, 0, s>>>(dout, w, (bf16*)din, 16, 6, nvox);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
@@ -868,6 +975,76 @@ fit_status fit_unet_pair_sample(long long ncell, const void* pair, const void* b
   pair_sample_kernel<<<nblocks(ncell), 256, 0, (cudaStream_t)stream>>>((const bf16*)pair, (const bf16*)base16,
                                                                         (bf16*)in16, target6, ncell);
   FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
+namespace {
+constexpr int kAngleBlocks = 608;  // partial slots of the residual-angle sums (4 per SM)
+
+// forward, z = unpack(Y), w = A_in z, r^ from the input, and the four sums; the loss on the host
+fit_status angle_forward(fit_unet* u, fit_grid* g, double omega, const bf16* in16, double* loss, cudaStream_t s) {
+  UCK(check_dims(g->nx, g->ny, g->nz));
+  UCK(alloc_acts(u, g->nx, g->ny, g->nz));
+  if (u->rne != g->ne) {
+    for (void* q : {(void*)u->rz, (void*)u->rw, (void*)u->rr, (void*)u->rt}) if (q) cudaFree(q);
+    u->rz = u->rw = u->rr = u->rt = nullptr;
+    const size_t vb = (size_t)g->ne * sizeof(float2);
+    if (cudaMalloc(&u->rz, vb) || cudaMalloc(&u->rw, vb) || cudaMalloc(&u->rr, vb) || cudaMalloc(&u->rt, vb)) {
+      fit_set_error("fit_unet_train_step_residual: allocation failed");
+      u->rne = 0;
+      return FIT_ENOMEM;
+    }
+    u->rne = g->ne;
+  }
+  if (!u->rom && (cudaMalloc(&u->rom, sizeof(double)) || cudaMalloc(&u->rpart, 4 * kAngleBlocks * sizeof(double)) ||
+                  cudaMalloc(&u->rsum, 4 * sizeof(double)))) {
+    fit_set_error("fit_unet_train_step_residual: allocation failed");
+    return FIT_ENOMEM;
+  }
+  FIT_CHECK_CUDA(cudaMemcpyAsync(u->rom, &omega, sizeof(double), cudaMemcpyHostToDevice, s));
+  UCK(forward(u, in16, s));
+  unpack_kernel<<<nblocks(g->ncell), 256, 0, s>>>(u->Y, 1.f, g->mask, g->nx, g->ny, g->nxp, u->rz, g->ncell, nullptr,
+                                                  nullptr, 0.f);
+  resid_from_in16_kernel<<<nblocks(g->ncell), 256, 0, s>>>(in16, g->mask, g->nx, g->ny, g->nxp, g->ncell, u->rr);
+  UCK(fit_launch_apply(g, 1, u->rom, u->rz, u->rw, FIT_C64, 1.0, s));  // the scaled operator A_in
+  angle_partials_kernel<<<kAngleBlocks, 256, 0, s>>>(u->rw, u->rr, g->ne, u->rpart);
+  angle_final_kernel<<<1, 256, 0, s>>>(u->rpart, kAngleBlocks, u->rsum);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  if (loss) {
+    double h[4];
+    FIT_CHECK_CUDA(cudaMemcpyAsync(h, u->rsum, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FIT_CHECK_CUDA(cudaStreamSynchronize(s));
+    *loss = (h[2] > 0 && h[3] > 0) ? 1.0 - (h[0] * h[0] + h[1] * h[1]) / (h[2] * h[3]) : 1.0;
+  }
+  return FIT_OK;
+}
+}  // namespace
+
+fit_status fit_unet_residual_loss(fit_unet* u, fit_grid* g, double omega, const void* in16, double* loss, void* stream) {
+  FIT_REQUIRE(u && g && in16 && loss, "fit_unet_residual_loss: null argument");
+  FIT_REQUIRE(g->has_materials && isfinite(omega), "fit_unet_residual_loss: materials not set or bad omega");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  return angle_forward(u, g, omega, (const bf16*)in16, loss, (cudaStream_t)stream);
+}
+
+fit_status fit_unet_train_step_residual(fit_unet* u, fit_grid* g, double omega, const void* in16, float lr,
+                                        double* loss, void* stream) {
+  FIT_REQUIRE(u && g && in16 && lr > 0, "fit_unet_train_step_residual: bad argument");
+  FIT_REQUIRE(g->has_materials && isfinite(omega), "fit_unet_train_step_residual: materials not set or bad omega");
+  FIT_CHECK_CUDA(cudaSetDevice(g->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  UCK(angle_forward(u, g, omega, (const bf16*)in16, loss, s));
+  // dL/dY: conj(A conj(G)) with G the gradient with respect to conj(w)
+  angle_grad_kernel<<<nblocks(g->ne), 256, 0, s>>>(u->rw, u->rr, u->rsum, g->ne, u->rt);
+  UCK(fit_launch_apply(g, 1, u->rom, u->rt, u->rw, FIT_C64, 1.0, s));
+  angle_dy_kernel<<<nblocks(g->ncell), 256, 0, s>>>(u->rw, g->mask, g->nx, g->ny, g->nxp, g->ncell, u->dY);
+  UCK(backward(u, (const bf16*)in16, s));
+  u->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)u->step), c2 = 1.f - powf(b2, (float)u->step);
+  unet::adam_kernel<<<nblocks(u->nparams), 256, 0, s>>>(u->p, u->g, u->m, u->v, u->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  u->weights_dirty = true;
   return FIT_OK;
 }
 

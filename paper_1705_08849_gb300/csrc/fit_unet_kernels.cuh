@@ -406,10 +406,8 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(ConvArgs a, int tz) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Weight gradient of a 3x3x3 convolution (FP32 on the CUDA cores):
+// Weight gradient of a 3x3x3 convolution:
 //   dW[tap][co][ci] += sum_v dy[v][co] * x[v + off(tap)][ci],   db[co] += sum_v dy[v][co]
-// Grid (voxel chunks, 27 taps); each thread owns a 4 x 4 block of (co, ci) and accumulates over
-// 32-voxel tiles staged in shared memory; one atomicAdd per owned entry at the end.
 // ------------------------------------------------------------------------------------------------
 struct WgradArgs {
   const bf16* dy;  // [N][cout]
@@ -423,80 +421,102 @@ struct WgradArgs {
   int chunk;       // voxels per CTA
 };
 
-__global__ void __launch_bounds__(256) conv3_wgrad_kernel(WgradArgs a) {
-  const int cin = a.c1 + a.c2;
+// On the tensor cores (mma.sync m16n8k16, bf16 x bf16 -> FP32): for one tap,
+//   dW[tap] (CO x CI) += dY^T (CO x V) X_tap (V x CI),   X_tap[v] = x[v + off(tap)] (zero outside),
+// a GEMM whose K dimension is the voxels.  A block takes one tap (blockIdx.y) and a chunk of voxels
+// (blockIdx.x), stages 64 voxels at a time as [voxel][channel] rows of dY and of the shifted X (rows
+// padded by 8 channels, so that the 8 rows an ldmatrix reads start in distinct banks) and reads them as
+// transposed fragments (ldmatrix .trans): the MMA's A operand is dY^T, its B operand X_tap.  The 4 K-steps
+// of 16 voxels times the (CO/16) x (CI/8) output tiles are spread over the 8 warps, each warp keeping
+// FP32 accumulators for its tiles across all of the block's voxels; the block's partial dW is added with
+// FP32 atomics, and the centre tap's blocks also sum dY for db.
+// ------------------------------------------------------------------------------------------------
+__device__ inline void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ inline void ldsm_x2_t(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+template <int CO, int CI>
+__global__ void __launch_bounds__(256) conv3_wgrad_mma_kernel(WgradArgs a) {
+  constexpr int TV = 64, RSO = CO + 8, RSI = CI + 8;
+  constexpr int MT = CO / 16, NT = CI / 8, TILES = MT * NT;
+  constexpr int NACC = TILES >= 8 ? TILES / 8 : 1;  // output tiles per warp
+  static_assert(CO % 16 == 0 && CI % 8 == 0 && (TILES % 8 == 0 || 8 % TILES == 0), "wgrad tile shape");
+  __shared__ __align__(16) bf16 sdy[TV * RSO];
+  __shared__ __align__(16) bf16 sx[TV * RSI];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tap = blockIdx.y;
   const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
   const long long nvox = (long long)a.nx * a.ny * a.nz;
   const long long v0 = (long long)blockIdx.x * a.chunk;
   const long long v1 = min(nvox, v0 + a.chunk);
-  __shared__ float sdy[32][65];
-  __shared__ float sx[32][65];
-  const int nbco = a.cout / 4, nbci = cin / 4;
-  float acc[4][16];  // up to 4 owned blocks of 4 x 4 (cout/4 * cin/4 <= 1024)
-  float accb[4];
+  float acc[NACC][4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    accb[q] = 0.f;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) acc[q][r] = 0.f;
-  }
-  for (long long vb = v0; vb < v1; vb += 32) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < 32 * 64; q += 256) {
-      const int vi = q / 64, c = q % 64;
+  for (int j = 0; j < NACC; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  float dbs = 0.f;
+  const int q = lane >> 3, r = lane & 7;  // ldmatrix: which 8x8 matrix this lane addresses, and its row
+  for (long long vb = v0; vb < v1; vb += TV) {
+    __syncthreads();  // the previous tile's fragments are read
+    for (int e = tid; e < TV * (CO / 8); e += 256) {  // dY rows, 16-byte vectors
+      const int vi = e / (CO / 8), c8 = e % (CO / 8);
       const long long v = vb + vi;
-      float d = 0.f, xv = 0.f;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (v < v1) val = *reinterpret_cast<const uint4*>(a.dy + v * CO + c8 * 8);
+      *reinterpret_cast<uint4*>(sdy + vi * RSO + c8 * 8) = val;
+    }
+    for (int e = tid; e < TV * (CI / 8); e += 256) {  // X rows shifted by the tap
+      const int vi = e / (CI / 8), c8 = e % (CI / 8);
+      const long long v = vb + vi;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
       if (v < v1) {
-        if (c < a.cout) d = __bfloat162float(a.dy[v * a.cout + c]);
-        if (c < cin) {
-          const int x = (int)(v % a.nx), y = (int)((v / a.nx) % a.ny), z = (int)(v / ((long long)a.nx * a.ny));
-          const int xs = x + dx, ys = y + dy, zs = z + dz;
-          if (xs >= 0 && ys >= 0 && zs >= 0 && xs < a.nx && ys < a.ny && zs < a.nz) {
-            const long long vs = xs + (long long)a.nx * (ys + (long long)a.ny * zs);
-            xv = c < a.c1 ? __bfloat162float(a.x1[vs * a.c1 + c]) : __bfloat162float(a.x2[vs * a.c2 + (c - a.c1)]);
-          }
+        const int x = (int)(v % a.nx), y = (int)((v / a.nx) % a.ny), z = (int)(v / ((long long)a.nx * a.ny));
+        const int xs = x + dx, ys = y + dy, zs = z + dz;
+        if (xs >= 0 && ys >= 0 && zs >= 0 && xs < a.nx && ys < a.ny && zs < a.nz) {
+          const long long vs = xs + (long long)a.nx * (ys + (long long)a.ny * zs);
+          const int c = c8 * 8;
+          val = c < a.c1 ? *reinterpret_cast<const uint4*>(a.x1 + vs * a.c1 + c)
+                         : *reinterpret_cast<const uint4*>(a.x2 + vs * a.c2 + (c - a.c1));
         }
       }
-      sdy[vi][c] = d;
-      sx[vi][c] = xv;
+      *reinterpret_cast<uint4*>(sx + vi * RSI + c8 * 8) = val;
     }
     __syncthreads();
+    if (a.db && tap == 13 && tid < CO)
+      for (int vi = 0; vi < TV; ++vi) dbs += __bfloat162float(sdy[vi * RSO + tid]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int blk = threadIdx.x + 256 * q;
-      if (blk >= nbco * nbci) break;
-      const int co0 = (blk / nbci) * 4, ci0 = (blk % nbci) * 4;
-      for (int vi = 0; vi < 32; ++vi) {
-        float d[4], xv[4];
+    for (int j = 0; j < NACC; ++j) {
+      const int tile = TILES >= 8 ? warp + 8 * j : warp % TILES;
+      const int mt = tile / NT, nt = tile % NT;
+      // K-steps of this warp for this tile: all four, or (with fewer tiles than warps) every 8/TILES-th
+      constexpr int KSTEP = TILES >= 8 ? 1 : 8 / TILES;
+      const int k_first = TILES >= 8 ? 0 : warp / TILES;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          d[r] = sdy[vi][co0 + r];
-          xv[r] = sx[vi][ci0 + r];
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[q][4 * r + c] += d[r] * xv[c];
+      for (int ks = k_first; ks < TV / 16; ks += KSTEP) {
+        const int kk = ks * 16;
+        uint32_t a0, a1, a2, a3, b0, b1;
+        ldsm_x4_t(smem_addr(sdy + (kk + (q >> 1) * 8 + r) * RSO + mt * 16 + (q & 1) * 8), a0, a1, a2, a3);
+        ldsm_x2_t(smem_addr(sx + (kk + (lane & 15)) * RSI + nt * 8), b0, b1);
+        mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
       }
     }
-    if (a.db && tap == 13 && threadIdx.x < a.cout) {
-      float s = 0.f;
-      for (int vi = 0; vi < 32; ++vi) s += sdy[vi][threadIdx.x];
-      accb[0] += s;
-    }
   }
+  const int cin = a.c1 + a.c2;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int blk = threadIdx.x + 256 * q;
-    if (blk >= nbco * nbci) break;
-    const int co0 = (blk / nbci) * 4, ci0 = (blk % nbci) * 4;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) atomicAdd(&a.dw[((long long)tap * a.cout + co0 + r) * cin + ci0 + c], acc[q][4 * r + c]);
+  for (int j = 0; j < NACC; ++j) {
+    const int tile = TILES >= 8 ? warp + 8 * j : warp % TILES;
+    const int mt = tile / NT, nt = tile % NT;
+    const int m = mt * 16 + (lane >> 2), n = nt * 8 + 2 * (lane & 3);
+    float* w0 = a.dw + ((long long)tap * CO + m) * cin + n;
+    atomicAdd(w0, acc[j][0]);
+    atomicAdd(w0 + 1, acc[j][1]);
+    atomicAdd(w0 + 8LL * cin, acc[j][2]);
+    atomicAdd(w0 + 8LL * cin + 1, acc[j][3]);
   }
-  if (a.db && tap == 13 && threadIdx.x < a.cout) atomicAdd(&a.db[threadIdx.x], accb[0]);
+  if (a.db && tap == 13 && tid < CO) atomicAdd(&a.db[tid], dbs);
 }
 
 // ---- pooling ------------------------------------------------------------------------------------
@@ -687,8 +707,8 @@ __global__ void head_bwd_data_kernel(const float* dout, const float* w, bf16* di
 
 __global__ void __launch_bounds__(256) head_bwd_weight_kernel(const bf16* in, const float* dout, float* dw, float* db,
                                                               int cin, int cout, long long nv) {
-  // one thread per (o, c) pair plus the bias; grid-strided over voxel chunks of 4096
-  const long long v0 = (long long)blockIdx.x * 4096, v1 = min(nv, v0 + 4096);
+  // one thread per (o, c) pair plus the bias; one block per chunk of 256 voxels
+  const long long v0 = (long long)blockIdx.x * 256, v1 = min(nv, v0 + 256);
   for (int pair = threadIdx.x; pair < cout * (cin + 1); pair += blockDim.x) {
     const int o = pair / (cin + 1), c = pair % (cin + 1);
     float s = 0.f;
@@ -732,7 +752,8 @@ __global__ void loss_sums_kernel(const float* y, const float* t, long long n, do
 }
 
 __global__ void loss_grad_kernel(const float* y, const float* t, long long n, const double* sums, float* dy) {
-  const float sc = (float)(2.0 / fmax(sums[1], 1e-300));
+  // a zero target (an iterate that already is the solution) carries no direction: no gradient
+  const float sc = sums[1] > 1e-30 ? (float)(2.0 / sums[1]) : 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dy[i] = sc * (y[i] - t[i]);
 }

@@ -128,6 +128,10 @@ def lib():
         L.fit_unet_training_pair.restype = ct.c_int
         L.fit_unet_pair_sample.argtypes = [ll, vp, vp, vp, vp, vp]
         L.fit_unet_pair_sample.restype = ct.c_int
+        L.fit_unet_train_step_residual.argtypes = [vp, vp, d, vp, ct.c_float, ct.POINTER(ct.c_double), vp]
+        L.fit_unet_train_step_residual.restype = ct.c_int
+        L.fit_unet_residual_loss.argtypes = [vp, vp, d, vp, ct.POINTER(ct.c_double), vp]
+        L.fit_unet_residual_loss.restype = ct.c_int
         L.fit_set_abort.argtypes = [vp, i]
         L.fit_set_abort.restype = ct.c_int
         L.fit_sync.argtypes = [vp, vp]
@@ -434,6 +438,19 @@ class UNet:
         loss = ct.c_double()
         _check(lib().fit_unet_train_step(self.h, nx, ny, nz, _ptr(in16), _ptr(target6), float(lr), ct.byref(loss),
                                          _stream_ptr(stream)), "fit_unet_train_step")
+        return loss.value
+
+    def train_step_residual(self, g, omega, in16, lr, stream=None):
+        """One Adam step on the residual-angle loss 1 - |<A z, r>|^2 / (||A z||^2 ||r||^2) on grid handle g."""
+        loss = ct.c_double()
+        _check(lib().fit_unet_train_step_residual(self.h, g, float(omega), _ptr(in16), float(lr), ct.byref(loss),
+                                                  _stream_ptr(stream)), "fit_unet_train_step_residual")
+        return loss.value
+
+    def residual_loss(self, g, omega, in16, stream=None):
+        loss = ct.c_double()
+        _check(lib().fit_unet_residual_loss(self.h, g, float(omega), _ptr(in16), ct.byref(loss), _stream_ptr(stream)),
+               "fit_unet_residual_loss")
         return loss.value
 
     def close(self):

@@ -16,9 +16,14 @@ early and late iterates alike.  Pairs stay on the GPU as one bf16 shard per geom
 ([pairs, cells, 12], 24 bytes per cell and pair: 6.3 MB per 64^3 pair, about 126 GB for 20 000 pairs,
 inside the 288 GB of HBM), so training never waits on storage.
 
-Training.  Adam (cosine learning rate) on ||U(in) - target||^2 / ||target||^2 with the library's own
-forward and backward kernels, one pair per step in a shuffled order, the parameters with the lowest
-validation loss (held-out geometries) kept.
+Training.  Adam (cosine learning rate) with the library's own forward and backward kernels, one pair per
+step in a shuffled order, the parameters with the lowest validation loss (held-out geometries) kept.  The
+default loss is the residual angle (fit_unet_train_step_residual): with z = U(in) and w = A z on the pair's
+own grid and frequency, L = 1 - |<w, r^>|^2 / (||w||^2 ||r^||^2), the part of the residual the network's
+direction cannot remove, which is what flexible GMRES gains from it.  ``--loss error`` trains on the
+error direction instead, ||U(in) - e^||^2 / ||e^||^2: a network that gets the error's direction to within
+18% in that norm still leaves a residual A amplifies (the high-frequency part of its error), so it does
+not help the solver; the residual angle measures the error in the norm the solver sees.
 
 Evaluation (``evaluate``).  FGMRES(30) with one direction from the network per restart cycle (z_1 =
 U(v_0), v_0 the cycle's normalised true residual, the input the pairs are made of; the Jacobi direction
@@ -71,7 +76,8 @@ def _freq(seed, fmin, fmax):
 
 
 def harvest(seeds, n=64, pairs_per_geometry=270, slots=2400, tol=1e-7, fmin=1e9, fmax=10e9, log=print):
-    """One shard per geometry: dict(seed, f, base16 [cells, 16] bf16, pairs [k, cells, 12] bf16) on the GPU."""
+    """One shard per geometry: dict(seed, f, omega, grid (the open fit.Grid, for the residual loss), base16
+    [cells, 16] bf16, pairs [k, cells, 12] bf16) on the GPU."""
     import torch
 
     import fitgen as G
@@ -82,7 +88,8 @@ def harvest(seeds, n=64, pairs_per_geometry=270, slots=2400, tol=1e-7, fmin=1e9,
         f = _freq(s, fmin, fmax)
         w = 2 * math.pi * f
         t0 = time.time()
-        with fit.Grid.from_case(case) as g:
+        g = fit.Grid.from_case(case)
+        if True:  # the grid stays open: the residual loss applies the pair's own operator
             ne, ncell = g.ne, g.ne // 3
             b = (-1j * w) * torch.from_numpy(G.source_vector(case)).cuda()
             x = torch.zeros_like(b)
@@ -90,8 +97,9 @@ def harvest(seeds, n=64, pairs_per_geometry=270, slots=2400, tol=1e-7, fmin=1e9,
             st, rep = g.solve([w], b, x, tol, method=fit.FIT_FGMRES, restart=30, precond=fit.FIT_PC_JACOBI,
                               max_iter=30 * slots, max_outer=slots, history=hist.data_ptr(), history_len=slots,
                               history_every=1)
-            # x* must be the solution: a geometry whose solve did not converge gives no pairs
-            ns = rep[0]["snapshots"] if st == fit.FIT_OK else 0
+            # x* must be the solution: a geometry whose solve did not converge gives no pairs; the last
+            # snapshot is x* itself (no error left), so it is not a pair either
+            ns = max(0, rep[0]["snapshots"] - 1) if st == fit.FIT_OK else 0
             pick = np.unique(np.linspace(0, ns - 1, min(ns, pairs_per_geometry)).round().astype(int)) if ns else []
             pairs = torch.empty(len(pick), ncell, 12, dtype=torch.bfloat16, device="cuda")
             for q, k in enumerate(pick):
@@ -101,7 +109,9 @@ def harvest(seeds, n=64, pairs_per_geometry=270, slots=2400, tol=1e-7, fmin=1e9,
             fit.fit_unet_pack(g.h, torch.zeros(ne, dtype=torch.complex64, device="cuda"), 1.0, base16)
             torch.cuda.synchronize()
         if len(pick):
-            shards.append(dict(seed=int(s), f=f, base16=base16, pairs=pairs))
+            shards.append(dict(seed=int(s), f=f, omega=w, grid=g, base16=base16, pairs=pairs))
+        else:
+            g.close()
         log(f"harvest seed {s}: f = {f / 1e9:.2f} GHz, {fit.status_str(st)}, {rep[0]['iterations']} iterations, "
             f"relres {rep[0]['relres']:.2e}, {rep[0]['snapshots']} snapshots -> {len(pick)} pairs, "
             f"{time.time() - t0:.1f} s")
@@ -112,7 +122,7 @@ def _sample(fit, shard, k, in16, t6):
     fit.fit_unet_pair_sample(in16.shape[0], shard["pairs"][k], shard["base16"], in16, t6)
 
 
-def train(net, shards, n, epochs, lr=5e-4, lr_min=2e-5, seed=0, val=None, checks=10, log=print):
+def train(net, shards, n, epochs, lr=5e-4, lr_min=2e-5, seed=0, val=None, checks=10, loss="residual", log=print):
     """Adam with a cosine learning rate over ``epochs`` passes of the pairs in a shuffled order; with
     validation shards the parameters with the lowest validation loss at the checkpoints are kept."""
     import torch
@@ -125,7 +135,7 @@ def train(net, shards, n, epochs, lr=5e-4, lr_min=2e-5, seed=0, val=None, checks
     in16 = torch.empty(ncell, 16, dtype=torch.bfloat16, device="cuda")
     t6 = torch.empty(ncell, 6, dtype=torch.float32, device="cuda")
     hist = []
-    best = (validate(net, val, n), net.get_params()) if val else None
+    best = (validate(net, val, n, loss=loss), net.get_params()) if val else None
     t0 = time.time()
     order = []
     every = max(1, steps // checks)
@@ -134,12 +144,16 @@ def train(net, shards, n, epochs, lr=5e-4, lr_min=2e-5, seed=0, val=None, checks
             order = list(rng.permutation(len(index)))
         si, k = index[order.pop()]
         lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / steps))
-        _sample(fit, shards[si], k, in16, t6)
-        hist.append(net.train_step(n, n, n, in16, t6, lr_t))
+        sh = shards[si]
+        _sample(fit, sh, k, in16, t6)
+        if loss == "residual":
+            hist.append(net.train_step_residual(sh["grid"].h, sh["omega"], in16, lr_t))
+        else:
+            hist.append(net.train_step(n, n, n, in16, t6, lr_t))
         if (it + 1) % every == 0:
             msg = f"step {it + 1}/{steps}: train loss (mean of last {every}) {np.mean(hist[-every:]):.4f}"
             if val:
-                v = validate(net, val, n)
+                v = validate(net, val, n, loss=loss)
                 msg += f", validation {v:.4f}"
                 if v < best[0]:
                     best = (v, net.get_params())
@@ -149,7 +163,7 @@ def train(net, shards, n, epochs, lr=5e-4, lr_min=2e-5, seed=0, val=None, checks
     return hist, steps
 
 
-def validate(net, shards, n, per_shard=16):
+def validate(net, shards, n, per_shard=16, loss="residual"):
     """Mean loss over up to ``per_shard`` evenly spaced pairs of every validation shard."""
     import torch
 
@@ -162,7 +176,10 @@ def validate(net, shards, n, per_shard=16):
         m = sh["pairs"].shape[0]
         for k in np.unique(np.linspace(0, m - 1, min(m, per_shard)).round().astype(int)):
             _sample(fit, sh, int(k), in16, t6)
-            losses.append(net.backward(n, n, n, in16, t6))
+            if loss == "residual":
+                losses.append(net.residual_loss(sh["grid"].h, sh["omega"], in16))
+            else:
+                losses.append(net.backward(n, n, n, in16, t6))
     torch.cuda.synchronize()
     return float(np.mean(losses))
 
@@ -219,6 +236,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=float, default=3.0)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--seed", type=int, default=1000)
+    ap.add_argument("--loss", default="residual", choices=["residual", "error"])
     ap.add_argument("--eval-n", type=int, default=0, help="grid of an evaluation on unseen geometries (0: none)")
     ap.add_argument("--eval-seeds", default="5000")
     ap.add_argument("--eval-freqs", default="1e9,4e9,7e9,10e9")
@@ -236,18 +254,21 @@ def main(argv=None):
     t_h = time.time() - t0
     npairs = sum(sh["pairs"].shape[0] for sh in shards)
     net = fit.UNet(seed=args.seed)
-    v0 = validate(net, val, args.n) if val else None
+    v0 = validate(net, val, args.n, loss=args.loss) if val else None
     t1 = time.time()
-    hist, steps = train(net, shards, args.n, args.epochs, lr=args.lr, val=val)
+    hist, steps = train(net, shards, args.n, args.epochs, lr=args.lr, val=val, loss=args.loss)
     t_t = time.time() - t1
-    v1 = validate(net, val, args.n) if val else None
+    v1 = validate(net, val, args.n, loss=args.loss) if val else None
     record = {"geometries": [seeds[0], seeds[args.geometries - 1]], "validation_geometries": seeds[args.geometries:],
               "n": args.n, "pairs": npairs, "pairs_per_geometry": per, "epochs": args.epochs, "steps": steps,
+              "loss": args.loss,
               "lr": args.lr, "harvest_s": t_h, "train_s": t_t,
               "final_train_loss": float(np.mean(hist[-max(1, steps // 10):])),
               "validation_loss_initial": v0, "validation_loss_final": v1}
     save(net, args.out, record)
     print(json.dumps(record), flush=True)
+    for sh in shards + (val or []):
+        sh["grid"].close()
     del shards, val
     if args.eval_n:
         res = evaluate(net, [int(v) for v in args.eval_seeds.split(",")], [float(v) for v in args.eval_freqs.split(",")],

@@ -268,3 +268,38 @@ def test_training_pair_matches_the_oracle():
         torch.cuda.synchronize()
         assert torch.equal(in16[:, :6], pair[:, :6]) and torch.equal(in16[:, 6:], base[:, 6:])
         assert torch.equal(t6, pair[:, 6:].float())
+
+
+def test_residual_angle_loss_and_step_match_the_oracle():
+    """fit_unet_residual_loss against the oracle's residual-angle loss (network on the same bf16 input,
+    A_in = s A assembled), and the first Adam step of fit_unet_train_step_residual against the oracle's
+    gradient: on every parameter whose oracle gradient is not tiny the step moves against its sign (the
+    first Adam step is -lr g / (|g| + eps))."""
+    torch = torch_cuda()
+    fit = fitlib()
+    from oracle import fit as F
+    from oracle import unet as U
+    case = G.small_random(16, 16, 12, seed=23, pec_frac=0.05)
+    nx, ny, nz = 16, 16, 12
+    w = 2 * np.pi * 4e9
+    me, mk, mn, mask = oracle_matrices(case)
+    A_in = F.system_matrix(w, F.curl(nx, ny, nz), me, mk, mn, mask) / mn.max()
+    p = _he_params(9, 0.2)
+    net = fit.UNet(seed=0)
+    net.set_params(p)
+    r = G.random_vector(A_in.shape[0], 11) * (1 - mask)
+    rms = np.linalg.norm(r) / np.sqrt(r.size)
+    with fit.Grid.from_case(case) as g:
+        in16 = torch.empty(r.size // 3, 16, dtype=torch.bfloat16, device="cuda")
+        fit.fit_unet_pack(g.h, torch.from_numpy(r).to(torch.complex64).cuda(), 1.0 / rms, in16)
+        x16 = in16.double().cpu().numpy().reshape(nz, ny, nx, 16)
+        lg = net.residual_loss(g.h, w, in16)
+        lo, go = U.residual_angle_loss_and_grad(p, x16, A_in, mask)
+        assert lg == pytest.approx(lo, abs=2e-3), (lg, lo)
+        l0 = net.train_step_residual(g.h, w, in16, 1e-4)
+        assert l0 == pytest.approx(lg, rel=1e-6)
+        dp = net.get_params().astype(np.float64) - p.astype(np.float64)
+    net.close()
+    big = np.abs(go) > 1e-2 * np.abs(go).max()
+    agree = np.mean(np.sign(dp[big]) == -np.sign(go[big]))
+    assert big.sum() > 100 and agree >= 0.99, (int(big.sum()), agree)

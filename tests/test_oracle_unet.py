@@ -114,3 +114,29 @@ def test_head_gradients_are_adjoint_and_linear():
     assert np.sum(U.head_fwd(x, w, np.zeros(6)) * g) == pytest.approx(np.sum(x * din), rel=1e-12)
     w2, b2 = rng.standard_normal((6, 16)), rng.standard_normal(6)
     assert np.sum(U.head_fwd(x, w2, b2) * g) == pytest.approx(np.sum(w2 * dw) + np.sum(b2 * db), rel=1e-12)
+
+
+def test_residual_angle_gradient_matches_finite_differences():
+    """The oracle's residual-angle loss: its autograd gradient (through the sparse apply's adjoint) equals
+    central finite differences in FP64, on a small complex symmetric A."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(8)
+    n = 4
+    ne = 3 * n ** 3
+    M = sp.random(ne, ne, density=0.05, random_state=1) + 1j * sp.random(ne, ne, density=0.05, random_state=2)
+    A = (M + M.T + 4 * sp.eye(ne)).tocsr()  # complex symmetric
+    mask = (rng.random(ne) < 0.1).astype(np.uint8)
+    flat = rng.standard_normal(U.param_count()) * 0.2
+    x = rng.standard_normal((n, n, n, 16))
+    # rounding to bf16 inside forward makes the loss piecewise constant in the conv weights; difference the
+    # head (FP32, no rounding) instead
+    _, g = U.residual_angle_loss_and_grad(flat, x, A, mask)
+    head0 = U.param_count() - 6 * 16 - 6
+    h = 1e-6
+    for i in rng.choice(np.arange(head0, U.param_count()), 6, replace=False):
+        fp, fm = flat.copy(), flat.copy()
+        fp[i] += h
+        fm[i] -= h
+        lp, _ = U.residual_angle_loss_and_grad(fp, x, A, mask)
+        lm, _ = U.residual_angle_loss_and_grad(fm, x, A, mask)
+        assert (lp - lm) / (2 * h) == pytest.approx(g[i], rel=1e-5, abs=1e-10), i
