@@ -251,6 +251,23 @@ def time_solves(fit, torch, case, kinds, max_iter, use_graph=1):
     return out
 
 
+def learned_vs_plain(solves):
+    """The solve half of the headline: seconds per frequency of the learned, mixed-precision FGMRES(30)
+    against the plain complex128 solves and the same mixed FGMRES without the network, with every
+    solve's status (a solve that did not reach 1e-8 is reported, not compared)."""
+    def leg(k):
+        r = solves.get(k)
+        return None if r is None else {"kind": k, "s": r["s_per_freq"], "status": r["status"],
+                                       "iterations": r["iterations"]}
+    out = {"learned": leg("mixed+unet"), "plain_fp64": [v for v in (leg("c128"), leg("cocg-c128")) if v],
+           "without_network": leg("mixed"), "fastest_mixed": leg("cocg-mixed")}
+    ok = [r for r in solves.values() if r["status"] == "FIT_OK"]
+    if ok:
+        best = min(ok, key=lambda r: r["s_per_freq"])
+        out["fastest_converged"] = {"method": best["method"], "s": best["s_per_freq"]}
+    return out
+
+
 def time_sweep(fit, torch, case, nfreq, kind, max_iter, band=None, seq_kind=None, budget_gb=0.0, restart=30,
                seq_max_iter=None):
     """A wide-band sweep: nfreq of the workload's frequencies (evenly picked, or evenly spaced over
@@ -406,10 +423,13 @@ def main():
     ap.add_argument("--ports", type=int, default=4, help="ports of the ports mode (z-edge columns)")
     ap.add_argument("--mode", default="apply", choices=["apply", "solve", "unet", "sweep", "ports"],
                     help="apply: the operator-apply metric (default); solve: only the solve measurement")
-    ap.add_argument("--solve", default="mixed,cocg-mixed",
+    ap.add_argument("--solve", default="cocg-mixed,mixed,mixed+unet,cocg-c128,c128",
                     help="comma list of solves to time, each [method-]precision[+pc] with method fgmres (default), "
-                         "cocg, cocr or bicgstab, precision mixed or c128, pc jacobi (default), eps or none; "
-                         "none for no solve")
+                         "cocg, cocr or bicgstab, precision mixed or c128, pc jacobi (default), eps, none or unet "
+                         "(FGMRES mixed: the committed network's direction once per restart cycle; unet/K: on the "
+                         "steps j = 1 mod K); none for no solve.  The default times the fastest mixed solve, "
+                         "FGMRES(30) mixed without and with the learned network, and the plain complex128 COCG "
+                         "and FGMRES(30)")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")
     ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="sweep mode: the handle's HBM budget (0: none)")
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length of the sweep mode")
@@ -629,6 +649,7 @@ def main():
     g.close()
     if kinds and world == 1:  # the solve leg runs at N = 1 only: under torchrun it would hold every GPU
         line["solve"] = time_solves(fit, torch, case, kinds, args.max_iter)
+        line["learned_vs_plain"] = learned_vs_plain(line["solve"])
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_oracle_apply(case, target_s=10.0)
         cv = r["ne"] * len(r["times"]) / sum(r["times"]) / 1e9

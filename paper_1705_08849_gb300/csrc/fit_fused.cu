@@ -477,14 +477,18 @@ __device__ inline uint64_t global_ns() {
 // Wait for a handoff between warps of the CTA: spin on try_wait (which itself suspends the thread
 // until the phase completes or a short hardware limit passes) with no sleep in between, so the
 // waiting warp resumes as soon as the other side arrives; gives up after 0.5 s of wall time.
-// The host's abort word ends the wait early (read every 256 polls, with the clock); abort = nullptr
-// for the waits that let the CTA's own copies land before it leaves.
+// The host's abort word ends a wait that has already lasted 20 us (far beyond any handoff of a
+// running apply, so the word, in host memory, is never read on the way of a healthy kernel); abort =
+// nullptr for the waits that let the CTA's own copies land before it leaves.
 __device__ inline bool mbar_wait_handoff(uint64_t* bar, uint32_t parity, const volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1; it < (1u << 30); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0u && (global_ns() - t0 > 500000000ull || (abort && *abort))) return false;
+    if ((it & 255u) == 0u) {
+      const uint64_t dt = global_ns() - t0;
+      if (dt > 500000000ull || (abort && dt > 20000ull && *abort)) return false;
+    }
   }
   return false;
 }
@@ -586,12 +590,13 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
     unsigned G = 0;
     int bx, by, b, k0, k1, slot;
     bool checked_abort = false;
-    // Read the abort word (its device-memory copy) once, with the first copies already in flight (its
-    // latency hides under theirs); the masking warp waits for this before it releases any plane to the
-    // consumers, so a kernel that starts aborted writes nothing.  Returns true if the CTA must stop.
-    auto check_abort = [&]() -> bool {
+    // The abort word (its device-memory copy) is loaded before the first copies are issued and used
+    // after them, so that its latency hides under theirs; the masking warp waits for the answer before
+    // it releases any plane to the consumers, so a kernel that starts aborted writes nothing.
+    const int abort_at_start = *a.abort_first;
+    auto check_abort = [&]() -> bool {  // returns true if the CTA must stop
       checked_abort = true;
-      const bool stop = *a.abort_first != 0;
+      const bool stop = abort_at_start != 0;
       if (stop) {
         *quit = 1;
         atomicExch(a.err, 2);
@@ -1164,6 +1169,11 @@ bool fused_fits(const fit_grid* g, int nbatch, const Variant& v) {
 }
 
 }  // namespace
+
+bool fit_tmap_encode(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,
+                     const cuuint64_t* strides, const cuuint32_t* box) {
+  return encode(m, dt, rank, base, dims, strides, box);
+}
 
 fit_status fit_launch_apply_generic(fit_grid* g, int nbatch, const double* omega_dev, const void* x, void* y,
                                     fit_prec prec, double out_scale, cudaStream_t s, fit_epi* epi);

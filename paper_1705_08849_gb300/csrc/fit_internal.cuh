@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of the FIT library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -155,6 +156,10 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
 int fit_tuned_choice(const fit_grid* g, fit_prec prec, int nbatch, int* out7);
 // name (blanks replaced) and SM count of the current device: the device part of a tuning-cache key
 fit_status fit_tuning_device_key(std::string* name, int* sm_count);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no swizzle, no interleave, zero fill
+// outside the tensor, unit element strides); false if the entry point or the encoding fails
+bool fit_tmap_encode(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,
+                     const cuuint64_t* strides, const cuuint32_t* box);
 // Number of partial-sum slots per system that the apply writes for an epilogue.
 long long fit_apply_partials(const fit_grid* g, fit_prec prec);
 

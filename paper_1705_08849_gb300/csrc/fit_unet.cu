@@ -181,12 +181,23 @@ fit_status tconv_fwd(const bf16* in, const float* w, const float* b, bf16* out, 
   return FIT_OK;
 }
 
-// tcgen05 conv3: same z-chunking rule as launch_conv3, 32 x 4 voxel tiles, NC output channels per CTA
-template <int CIN, int NC>
+// 5D tensor map {8 channels, C/8 groups, nx, ny, nz} of an NDHWC bf16 activation with C channels,
+// box {8, 1, 32, 6, 1}: one channel group of a 32 x 6 voxel window of one plane (the tcgen05 conv's
+// staged copy layout)
+static bool conv_tmap(CUtensorMap* m, const bf16* base, int c, int nx, int ny, int nz) {
+  const cuuint64_t dims[5] = {8, (cuuint64_t)(c / 8), (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)c * 2, (cuuint64_t)nx * c * 2, (cuuint64_t)nx * ny * c * 2};
+  const cuuint32_t box[5] = {8, 1, (cuuint32_t)unet::CX, (cuuint32_t)unet::UmmaShape<16, 16, 4>::ROWS, 1};
+  return fit_tmap_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box);
+}
+
+// tcgen05 conv3: 32 x 4 voxel tiles, all output channels per CTA, the same z-chunking rule as
+// launch_conv3
+template <int CIN, int NC, int S>
 fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
-  auto kern = unet::conv3_tc_kernel<CIN, NC>;
-  constexpr int smem = unet::TcShape<CIN, NC>::smem();
-  constexpr int TY = unet::TcShape<CIN, NC>::TY;
+  auto kern = unet::conv3_tc_kernel<CIN, NC, S>;
+  constexpr int smem = unet::UmmaShape<CIN, NC, S>::smem();
+  constexpr int TY = unet::UmmaShape<CIN, NC, S>::TY;
   static int per_sm = 0, nsm = 0;
   if (per_sm == 0) {
     int dev = 0;
@@ -194,33 +205,52 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
     FIT_CHECK_CUDA(cudaGetDevice(&dev));
     FIT_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int p = 0;
-    FIT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kern, 128, smem));
+    FIT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kern, 192, smem));
     if (p < 1) {
       fit_set_error("U-Net: tcgen05 conv tile does not fit on an SM");
       return FIT_EINVAL;
     }
     per_sm = p;
   }
-  const int gx = (a.nx + unet::CX - 1) / unet::CX, gy = (a.ny + TY - 1) / TY, nblk = (a.cout + NC - 1) / NC;
-  const long long cols = (long long)gx * gy * nblk;
+  CUtensorMap m1, m2;
+  if (!conv_tmap(&m1, a.in1, a.c1, a.nx, a.ny, a.nz) || (a.c2 > 0 && !conv_tmap(&m2, a.in2, a.c2, a.nx, a.ny, a.nz))) {
+    fit_set_error("U-Net: tensor map of a conv input could not be encoded");
+    return FIT_ECUDA;
+  }
+  if (a.c2 == 0) m2 = m1;
+  const int gx = (a.nx + unet::CX - 1) / unet::CX, gy = (a.ny + TY - 1) / TY;
+  const long long cols = (long long)gx * gy;
   const long long per_col = std::max(1LL, (long long)per_sm * nsm / cols);
   const int tz = (int)std::max(2LL, ((long long)a.nz + per_col - 1) / per_col);
   const int nzc = (a.nz + tz - 1) / tz;
-  dim3 grid(gx, gy, (unsigned)(nzc * nblk));
-  kern<<<grid, 128, smem, s>>>(a, tz);
+  dim3 grid(gx, gy, (unsigned)nzc);
+  kern<<<grid, 192, smem, s>>>(m1, m2, a, tz);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
 
-// The 16-input-channel convs run on mma.sync by default; FIT_CONV=tc selects the tcgen05 kernel.
-// Both pass the same parity tests.  With N = 16 output channels each tcgen05 MMA is 128 x 16 x 16,
-// and the 27 taps accumulate into one TMEM tile as a dependent chain, so one CTA spends about 5 us
-// per plane on issue, commit and wait: 2.06 ms per 128^3 network application against 1.59 ms on
-// mma.sync.  Interleaving independent accumulators (more row tiles or planes per CTA) is what it
-// needs next.
+// FIT_CONV=mma keeps every conv on the legacy mma.sync kernel; FIT_CONV=tc runs the shapes with 16 or
+// 32 input channels on the tcgen05 kernel (the 64-input-channel convs need more shared memory than a
+// staged ring of three shifted plane copies leaves, and stay on mma.sync).
 static bool conv_use_tc() {
   const char* e = getenv("FIT_CONV");
   return e && !strcmp(e, "tc");
+}
+
+// the tcgen05 kernel for this shape, if there is one: every channel count a multiple of 8, at most 64
+// output channels
+static fit_status conv3_tc(const unet::ConvArgs& a, int cin, cudaStream_t s, bool* done) {
+  *done = false;
+  if (!conv_use_tc() || a.c1 % 8 || a.c2 % 8 || a.o1 % 8 || a.o2 % 8 || a.cout > 64) return FIT_OK;
+  *done = true;
+  if (cin == 16 && a.cout <= 16) return launch_conv3_tc<16, 16, 4>(a, s);
+  if (cin == 16 && a.cout <= 32) return launch_conv3_tc<16, 32, 4>(a, s);
+  if (cin == 16) return launch_conv3_tc<16, 64, 4>(a, s);
+  if (cin == 32 && a.cout <= 16) return launch_conv3_tc<32, 16, 5>(a, s);
+  if (cin == 32 && a.cout <= 32) return launch_conv3_tc<32, 32, 4>(a, s);
+  if (cin == 32) return launch_conv3_tc<32, 64, 3>(a, s);
+  *done = false;
+  return FIT_OK;
 }
 
 // Weight gradient of a 3x3x3 conv on the tensor cores: dw (27 x cout x cin) and db accumulate (the caller
@@ -265,10 +295,9 @@ fit_status conv3(const bf16* in1, int c1, const bf16* in2, int c2, const bf16* w
   a.nz = nz;
   a.relu = relu;
   const int cin = c1 + c2;
-  if (cin == 16 && conv_use_tc()) {
-    if (a.cout <= 16) return launch_conv3_tc<16, 16>(a, s);
-    return launch_conv3_tc<16, 32>(a, s);
-  }
+  bool done = false;
+  const fit_status st = conv3_tc(a, cin, s, &done);
+  if (done) return st;
   // shared memory per CTA: (16,16,8) 86 KB, (16,32,8) 107 KB, (32,16,4) 100 KB, (64,16,4) 180 KB
   if (cin == 16 && a.cout <= 16) return launch_conv3<16, 16, 8>(a, s);
   if (cin == 16) return launch_conv3<16, 32, 8>(a, s);

@@ -4,6 +4,7 @@
 // voxel index x + nx*(y + ny*z)).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -200,30 +201,43 @@ __global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a, int tz) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// The same 3x3x3 convolution on the 5th-generation tensor cores (tcgen05.mma, accumulator in TMEM).
-// A CTA of 4 warps owns 32 x 4 output voxels (M = 128) per z-plane, all NC output channels (N), and
-// marches a chunk of z-planes.  Per plane and tap (dz, dy, dx) the A operand (128 voxels x CIN) is a
-// window of a staged input plane, and one elected thread issues the 27 * CIN / 16 MMAs of K = 16.
-// Layouts (canonical, no swizzle, K-major; a "line" is 8 bf16 channels = 16 bytes):
-//   input plane, staged 3 times (shifted by dx = 0, 1, 2 voxels): [g = CIN/8][r = 6 rows][v = 32] lines,
-//     so the 128 rows of a window (rows dy .. dy+3, voxels 0 .. 31) are 128 consecutive lines:
-//     core matrices of 8 rows are 128 B apart (SBO), channel groups 6 * 32 * 16 B apart (LBO);
-//   weights: [tap][g][n = NC] lines: SBO = 128 B, LBO = NC * 16 B.
-// The ring holds 4 planes (z-1 .. z+1 in use, z+2 arriving by cp.async).  Every mbarrier wait is
-// bounded; on a timeout the CTA records it in g_conv_timeout, waits (bounded) for its MMAs, frees
-// its TMEM and leaves.
+// The same 3x3x3 convolution on the 5th-generation tensor cores: tcgen05.mma with FP32 accumulators
+// in TMEM, input planes staged by TMA (cp.async.bulk.tensor), warp-specialised and pipelined.
+// A CTA owns a 32 x 4 tile of output voxels in (x, y) (M = 128 rows of the MMA, row m = voxel
+// (x0 + m % 32, y0 + m / 32)), all NC output channels (N), and marches a chunk of z-planes.
+//   warp 0 (lane 0): the producer.  Input plane p is staged three times, shifted by dx = 0, 1, 2
+//     voxels along x, as [g = CIN/8][r = 6 rows][v = 32] lines of 16 B (8 channels): one 5D TMA box
+//     {8 channels, 1 group, 32 voxels, 6 rows, 1 plane} per (dx, group), zero-filled outside the grid.
+//     The 128 M-rows of a tap's window (rows dy .. dy+3) are then 128 consecutive lines: canonical
+//     K-major, no swizzle, core matrices 128 B apart along M (SBO), channel groups LINES * 16 B apart
+//     (LBO).  A ring of S planes; output plane z reads planes z-1, z, z+1.
+//   warp 1 (lane 0): the MMA issuer.  For output plane z it issues the 27 * CIN / 16 MMAs of
+//     128 x NC x 16 into accumulator z % 2 (two TMEM buffers of NC columns), then commits them to
+//     that buffer's "full" barrier and to the "empty" barrier of plane z-1's ring slot.
+//   warps 2..5: the epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (tile row w % 4) of the
+//     finished buffer, hands the buffer back, then adds the bias, applies the ReLU and stores bf16
+//     (16 B per 8 channels) to the one or two outputs.
+// So the copies of plane z+2, the MMAs of plane z+1 and the epilogue of plane z run at the same time.
+// Weights: [tap][g][n] lines (SBO 128 B, LBO NC * 16 B), staged once per CTA with cp.async.
+// Every wait is bounded; a role that gives up records it in g_conv_timeout and raises the CTA's stop
+// flag, the other roles leave their loops at their next wait, and the CTA frees its TMEM only after
+// a bounded wait for its last MMAs.
 // ------------------------------------------------------------------------------------------------
 __device__ int g_conv_timeout;
 
-template <int CIN, int NC>
-struct TcShape {
+template <int CIN, int NC, int S>
+struct UmmaShape {
   static constexpr int TY = 4, ROWS = TY + 2, LINES = ROWS * 32;  // lines per channel group of a copy
-  static constexpr int COPY = (CIN / 8) * LINES * 16;              // bytes of one shifted copy
-  static constexpr int PLANE = 3 * COPY;
-  static constexpr int WBYTES = 27 * (CIN / 8) * NC * 16;
+  static constexpr int CG = CIN / 8;
+  static constexpr int GROUP = LINES * 16;                         // bytes of one TMA box
+  static constexpr int COPY = CG * GROUP;                          // bytes of one shifted copy
+  static constexpr int PLANE = 3 * COPY;                           // bytes of a staged plane
+  static constexpr int WBYTES = 27 * CG * NC * 16;
   static constexpr int OFF_RING = ((WBYTES + 1023) / 1024) * 1024;
-  static constexpr int OFF_BAR = OFF_RING + 4 * PLANE;             // mbarrier (8 B) + TMEM address (4 B)
-  static constexpr int smem() { return OFF_BAR + 16 + 1024; }  // + slack for 1 KB alignment
+  static constexpr int OFF_BAR = OFF_RING + S * PLANE;
+  static constexpr int NBAR = 2 * S + 5;  // full[S], empty[S], accf[2], acce[2], done
+  static constexpr int TMEM_COLS = 2 * NC <= 32 ? 32 : (2 * NC <= 64 ? 64 : 128);
+  static constexpr int smem() { return OFF_BAR + NBAR * 8 + 16 + 1024; }  // + slack for 1 KB alignment
 };
 
 __device__ inline uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -234,174 +248,235 @@ __device__ inline uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sb
 __host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ inline bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ inline bool tc_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait (each try_wait suspends for a while); stop != nullptr: also give up once another role
+// of the CTA has raised the stop flag
+__device__ inline bool tc_mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stop = nullptr) {
   for (int it = 0; it < (1 << 22); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
+    if (tc_try_wait(bar, parity)) return true;
+    if (stop && (it & 63) == 63 && *stop) return false;
   }
   return false;
 }
+__device__ inline void tc_mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ inline void tc_mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ inline void tc_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ inline void tc_tma_load_5d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3, int c4,
+                                      uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+__device__ inline void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ inline void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
 
-template <int CIN, int NC>
-__global__ void __launch_bounds__(128) conv3_tc_kernel(ConvArgs a, int tz) {
-  using SH = TcShape<CIN, NC>;
-  constexpr int TY = SH::TY, CG = CIN / 8;
-  static_assert(CIN % 16 == 0 && (NC == 16 || NC == 32), "tcgen05 conv shape");
+// tm1 / tm2: 5D maps {8 channels, groups, nx, ny, nz} of the two inputs (box {8, 1, 32, 6, 1});
+// tm2 is unused when a.c2 == 0.  Requires cout <= NC and every channel count a multiple of 8.
+template <int CIN, int NC, int S>
+__global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1,
+                                                       const __grid_constant__ CUtensorMap tm2, ConvArgs a, int tz) {
+  using SH = UmmaShape<CIN, NC, S>;
+  constexpr int CG = SH::CG;
+  static_assert(CIN % 16 == 0 && NC % 16 == 0 && NC <= 64 && S >= 3, "tcgen05 conv shape");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* w_s = smem;
-  unsigned char* ring = smem + SH::OFF_RING;
-  const uint32_t bar = smem_addr(smem + SH::OFF_BAR);
-  uint32_t* tmem_slot = (uint32_t*)(smem + SH::OFF_BAR + 8);
+  const uint32_t w_s = smem_addr(smem), ring = smem_addr(smem + SH::OFF_RING);
+  const uint32_t bar0 = smem_addr(smem + SH::OFF_BAR);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (S + s); };
+  auto accf = [&](int b) { return bar0 + 8u * (2 * S + b); };
+  auto acce = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
+  const uint32_t done = bar0 + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = (uint32_t*)(smem + SH::OFF_BAR + SH::NBAR * 8);
+  volatile int* stop = (volatile int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * TY;
-  const int nblk_n = (a.cout + NC - 1) / NC;
-  const int zc = blockIdx.z / nblk_n, n0 = (blockIdx.z % nblk_n) * NC;
-  const int z0 = zc * tz, z1 = min(a.nz, z0 + tz);
+  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * SH::TY;
+  const int z0 = blockIdx.z * tz, z1 = min(a.nz, z0 + tz);
   if (z0 >= z1) return;  // uniform over the CTA, before any TMEM is taken
+  const int nout = z1 - z0, nplanes = nout + 2;  // planes z0-1 .. z1
+  const int cg1 = a.c1 / 8, cg2 = a.c2 / 8;
 
-  if (warp == 0) {  // TMEM: 32 columns of 128 lanes x 32 bit hold the 128 x NC FP32 accumulator
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(tmem_slot))
+  if (warp == 1) {  // TMEM: two accumulators of NC FP32 columns (128 lanes)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "n"(SH::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    for (int s = 0; s < S; ++s) {
+      tc_mbar_init(full(s), 1);
+      tc_mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc_mbar_init(accf(b), 1);
+      tc_mbar_init(acce(b), 4);
+    }
+    tc_mbar_init(done, 1);
+    *stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // weights [tap][g][n] lines (output channels beyond cout are zero)
+  for (int q = tid; q < 27 * CG * NC; q += 192) {
+    const int n = q % NC, g = (q / NC) % CG, tap = q / (NC * CG);
+    const bool in = n < a.cout;
+    const void* src = in ? (const void*)(a.w + ((long long)tap * a.cout + n) * CIN + g * 8) : (const void*)a.w;
+    cp_async16(w_s + q * 16, src, in ? 16 : 0);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the weights, to the tensor core's reads
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-
-  // plane p -> ring slot (p - (z0 - 1)) % 4; copy dx, line (g, r, v) at dx*COPY + (g*LINES + r*32 + v)*16
-  auto load_plane = [&](int p) {
-    unsigned char* dst = ring + ((p - (z0 - 1)) & 3) * SH::PLANE;
-    for (int q = tid; q < 3 * CG * SH::LINES; q += 128) {
-      const int v = q & 31, r = (q >> 5) % SH::ROWS, g = (q / SH::LINES) % CG, dx = q / (CG * SH::LINES);
-      const int gx = x0 - 1 + dx + v, gy = y0 - 1 + r;
-      const bool in = gx >= 0 && gy >= 0 && p >= 0 && gx < a.nx && gy < a.ny && p < a.nz;
-      const void* src = a.in1;
-      if (in) {
-        const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * p);
-        const int c = g * 8;
-        src = c < a.c1 ? (const void*)(a.in1 + gv * a.c1 + c) : (const void*)(a.in2 + gv * a.c2 + (c - a.c1));
-      }
-      cp_async16(smem_addr(dst + dx * SH::COPY + (g * SH::LINES + r * 32 + v) * 16), src, in ? 16 : 0);
-    }
+  auto fail = [&]() {
+    atomicExch(&g_conv_timeout, 1);
+    *stop = 1;
   };
-  // weights [tap][g][n] lines, output channels n0 .. n0 + NC - 1
-  for (int q = tid; q < 27 * CG * NC; q += 128) {
-    const int n = q % NC, g = (q / NC) % CG, tap = q / (NC * CG);
-    const bool in = n0 + n < a.cout;
-    const void* src = in ? (const void*)(a.w + ((long long)tap * a.cout + n0 + n) * CIN + g * 8) : (const void*)a.w;
-    cp_async16(smem_addr(w_s + q * 16), src, in ? 16 : 0);
-  }
-  load_plane(z0 - 1);
-  load_plane(z0);
-  load_plane(z0 + 1);
-  cp_async_commit();
 
-  constexpr uint32_t IDESC = tc_idesc_bf16(128, NC);
-  bool bad = false;
-  int step = 0;
-  for (int z = z0; z < z1 && !bad; ++z, ++step) {
-    if (z + 2 <= z1) load_plane(z + 2);
-    cp_async_commit();
-    cp_async_wait<1>();  // planes z-1 .. z+1 (and the weights) have landed
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core's reads
-    __syncthreads();
-    if (tid == 0) {
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int i = 0;
+      for (; i < nplanes; ++i) {
+        const int s = i % S;
+        if (i >= S && !tc_mbar_wait(empty(s), ((i / S) - 1) & 1, stop)) {
+          fail();
+          break;
+        }
+        const int p = z0 - 1 + i;
+        const uint32_t dst = ring + s * SH::PLANE;
+        tc_expect_tx(full(s), SH::PLANE);
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          for (int g = 0; g < cg1; ++g)
+            tc_tma_load_5d(dst + dx * SH::COPY + g * SH::GROUP, &tm1, 0, g, x0 - 1 + dx, y0 - 1, p, full(s));
+          for (int g = 0; g < cg2; ++g)
+            tc_tma_load_5d(dst + dx * SH::COPY + (cg1 + g) * SH::GROUP, &tm2, 0, g, x0 - 1 + dx, y0 - 1, p, full(s));
+        }
+      }
+      // every copy issued lands before the CTA retires (the last S issued; earlier ones were consumed)
+      for (int d = 1; d <= S && d <= i; ++d) (void)tc_mbar_wait(full((i - d) % S), ((i - d) / S) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t IDESC = tc_idesc_bf16(128, NC);
+      int waited = 0;  // planes known to have landed
+      for (int j = 0; j < nout; ++j) {
+        bool ok = true;
+        for (; waited < j + 3 && ok; ++waited) ok = tc_mbar_wait(full(waited % S), (waited / S) & 1, stop);
+        const int b = j & 1;
+        if (ok && j >= 2) ok = tc_mbar_wait(acce(b), ((j >> 1) - 1) & 1, stop);
+        if (!ok) {
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(b * NC);
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const uint32_t abase = ring + ((j + dz) % S) * SH::PLANE + dx * SH::COPY + dy * 32 * 16;
+          const uint32_t bbase = w_s + tap * CG * NC * 16;
+#pragma unroll
+          for (int kk = 0; kk < CIN / 16; ++kk) {
+            const uint64_t ad = tc_smem_desc(abase + kk * 2 * SH::GROUP, SH::GROUP, 128);
+            const uint64_t bd = tc_smem_desc(bbase + kk * 2 * NC * 16, NC * 16, 128);
+            const uint32_t acc = (tap | kk) != 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                : "memory");
+          }
+        }
+        tc_commit(accf(b));        // the epilogue may read accumulator b
+        tc_commit(empty(j % S));   // plane z-1 (ring index j) is no longer read
+      }
+      tc_commit(done);  // every MMA this CTA issued has completed once this barrier flips
+      (void)tc_mbar_wait(done, 0);
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 ----------------
+    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 = tile row q
+    const int gx = x0 + lane, gy = y0 + q;
+    const bool valid = gx < a.nx && gy < a.ny;
+    for (int j = 0; j < nout; ++j) {
+      const int b = j & 1;
+      const bool ok = __all_sync(0xffffffffu, tc_mbar_wait(accf(b), (j >> 1) & 1, stop));
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t wbase = smem_addr(w_s), rbase = smem_addr(ring);
-      for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-        const uint32_t abase = rbase + ((z - 1 + dz - (z0 - 1)) & 3) * SH::PLANE + dx * SH::COPY + dy * 32 * 16;
-        const uint32_t bbase = wbase + tap * CG * NC * 16;
+      float v[NC];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NC);
 #pragma unroll
-        for (int kk = 0; kk < CIN / 16; ++kk) {
-          const uint64_t ad = tc_smem_desc(abase + kk * 2 * SH::LINES * 16, SH::LINES * 16, 128);
-          const uint64_t bd = tc_smem_desc(bbase + kk * 2 * NC * 16, NC * 16, 128);
-          const uint32_t acc = (tap | kk) != 0 ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-              : "memory");
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                   : "memory");
-    }
-    if (!tc_mbar_wait(bar, step & 1)) {  // the MMAs of this plane are done (smem read, TMEM written)
-      bad = true;
-      if (tid == 0) atomicExch(&g_conv_timeout, 1);
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w reads TMEM lanes 32w .. 32w+31 = tile row w, voxel x0 + lane
-    float v[NC];
-    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-    if (NC == 16) {
-      uint32_t r[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
+      for (int h = 0; h < NC / 16; ++h) tc_ld16(taddr + 16 * h, v + 16 * h);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) tc_mbar_arrive(acce(b));  // accumulator b may be overwritten
+      if (valid) {
+        const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * (z0 + j));
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
-    } else {
+        for (int c8 = 0; c8 < NC / 8; ++c8) {
+          const int co = c8 * 8;
+          if (co >= a.cout) break;
+          uint32_t pk[4];
 #pragma unroll
-      for (int h = 0; h < NC / 16; ++h) {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr + 16 * h));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[16 * h + c] = __uint_as_float(r[c]);
+          for (int e = 0; e < 4; ++e) {
+            float v0 = v[co + 2 * e], v1 = v[co + 2 * e + 1];
+            if (a.bias) {
+              v0 += a.bias[co + 2 * e];
+              v1 += a.bias[co + 2 * e + 1];
+            }
+            if (a.relu) {
+              v0 = fmaxf(v0, 0.f);
+              v1 = fmaxf(v1, 0.f);
+            }
+            const __nv_bfloat162 pv = __floats2bfloat162_rn(v0, v1);
+            pk[e] = *reinterpret_cast<const uint32_t*>(&pv);
+          }
+          bf16* dst = co < a.o1 ? a.out1 + gv * a.o1 + co : a.out2 + gv * a.o2 + (co - a.o1);
+          *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
       }
     }
-    const int gx = x0 + lane, gy = y0 + warp;
-    if (gx < a.nx && gy < a.ny) {
-      const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * z);
-#pragma unroll
-      for (int c = 0; c < NC; c += 2) {
-        const int co = n0 + c;
-        if (co >= a.cout) break;
-        float v0 = v[c], v1 = v[c + 1];
-        if (a.bias) {
-          v0 += a.bias[co];
-          v1 += a.bias[co + 1];
-        }
-        if (a.relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
-        }
-        const __nv_bfloat162 pv = __floats2bfloat162_rn(v0, v1);
-        if (co < a.o1) *reinterpret_cast<__nv_bfloat162*>(a.out1 + gv * a.o1 + co) = pv;
-        else *reinterpret_cast<__nv_bfloat162*>(a.out2 + gv * a.o2 + (co - a.o1)) = pv;
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // TMEM read out and plane z-1's slot free before the next plane's MMAs and copies
   }
-  if (bad) (void)tc_mbar_wait(bar, step & 1);  // bounded: let this plane's MMAs finish before freeing TMEM
-  cp_async_wait<0>();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(SH::TMEM_COLS) : "memory");
   }
 }
 

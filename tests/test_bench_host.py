@@ -54,3 +54,17 @@ def test_port_columns_are_seeded_distinct_and_in_range():
     assert len(heads) == 6
     short = bench.port_columns(dict(nx=40, ny=40, nz=5), 2, margin=8)
     assert all(len(e) == 5 for e, _ in short)  # capped at the grid height
+
+
+def test_learned_vs_plain_summary():
+    solves = {
+        "cocg-mixed": {"s_per_freq": 3.4, "status": "FIT_OK", "iterations": 21740, "method": "COCG"},
+        "mixed": {"s_per_freq": 36.0, "status": "FIT_OK", "iterations": 42150, "method": "FGMRES"},
+        "mixed+unet": {"s_per_freq": 30.0, "status": "FIT_OK", "iterations": 30000, "method": "FGMRES+U-Net"},
+        "c128": {"s_per_freq": 270.0, "status": "FIT_NOT_CONVERGED", "iterations": 80000, "method": "FGMRES c128"},
+    }
+    out = bench.learned_vs_plain(solves)
+    assert out["learned"]["s"] == 30.0 and out["without_network"]["s"] == 36.0
+    assert [p["kind"] for p in out["plain_fp64"]] == ["c128"]  # cocg-c128 was not timed
+    assert out["fastest_converged"]["method"] == "COCG"  # the unconverged solve is never the fastest
+    assert bench.learned_vs_plain({})["learned"] is None
