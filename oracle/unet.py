@@ -2,7 +2,8 @@
 
 Plain PyTorch CPU float64 ops (conv3d, avg_pool3d, conv_transpose3d) and autograd for the
 gradients.  With ``bf16=True`` it rounds to bfloat16 exactly where the GPU network stores bf16
-(conv inputs/outputs, pooled and upsampled activations, conv weights), so GPU and oracle can be
+(conv inputs/outputs, pooled and upsampled activations, the 3x3x3 and transposed-conv weights: the
+network keeps BF16 weights and activations with FP32 accumulation), so GPU and oracle can be
 compared on the same rounded values; with ``bf16=False`` it is the exact FP64 network (used for the
 finite-difference pins).
 
@@ -71,7 +72,7 @@ def forward(params, x_ndhwc, bf16=True):
     """Network output [nz, ny, nx, 6] (float64 torch tensor) for an input [nz, ny, nx, 16]."""
     x = torch.as_tensor(np.asarray(x_ndhwc, dtype=np.float64)).permute(3, 0, 1, 2)[None]
     r = lambda t: _bf(t, bf16)
-    W = {k: (r(w) if LAYERS[NAMES.index(k)][0] == "conv3" else w, b) for k, (w, b) in params.items()}
+    W = {k: (r(w) if LAYERS[NAMES.index(k)][0] in ("conv3", "tconv") else w, b) for k, (w, b) in params.items()}
     x0 = r(x)
     a1a = r(conv3(x0, *W["c1a"]))
     s1 = r(conv3(a1a, *W["c1b"]))

@@ -169,7 +169,9 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile 
   }
   return false;
 }
-// the error code a kernel records when a wait gives up: 2 if the host asked it to stop, else 1
+// the error code a kernel records when a wait gives up: 2 if the host asked it to stop, else 1.  Codes
+// are recorded with atomicMax, so an abort seen by any role of any CTA wins over the timeouts it causes
+// in the others.
 __device__ inline int wait_error(const volatile int* abort) { return *abort ? 2 : 1; }
 __device__ inline void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar) {
   asm volatile(
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
     };
     auto wait = [&](int q) {
       if (!mbar_wait(&bars[(G0 + q) % S], ((G0 + q) / S) & 1, a.abort)) {
-        atomicExch(a.err, wait_error(a.abort));
+        atomicMax(a.err, wait_error(a.abort));
         bad = 1;
       }
     };
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
       // is written.
       if (first_tile && *a.abort_first) {
         bad = 1;
-        atomicExch(a.err, 2);
+        atomicMax(a.err, 2);
       }
     }
     first_tile = false;
@@ -541,7 +543,11 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
   }
   __syncthreads();
   auto stage = [&](unsigned gq) -> unsigned char* { return smem + (gq % S) * L::STAGE; };
-  auto fail = [&]() { atomicExch(a.err, wait_error(a.abort)); };
+  // the issuing and masking warps read the abort word when they give up; a consumer warp only gives up
+  // after them (its planes stop arriving), so it records a plain timeout and leaves the abort code to
+  // them (and keeps the host word's address out of its registers)
+  auto fail = [&]() { atomicMax(a.err, wait_error(a.abort)); };
+  auto fail_consumer = [&]() { atomicMax(a.err, 1); };
 
   // This CTA's work, one segment (bx, by, b, planes k0 .. k1-1) at a time; every role walks the
   // same sequence.  Tiled: tiles blockIdx.x, blockIdx.x + gridDim.x, ... of ntx*nty*nzc*nbatch
@@ -599,7 +605,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
       const bool stop = abort_at_start != 0;
       if (stop) {
         *quit = 1;
-        atomicExch(a.err, 2);
+        atomicMax(a.err, 2);
       }
       mbar_arrive(checked);
       return stop;
@@ -690,7 +696,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
   // part[(b * nslots + slot) * 4 + q]; returns true when the consumers must stop.
   auto flush = [&](int b, int slot, long long nslots) -> bool {
     if (dead) {
-      fail();
+      fail_consumer();
       *abort_flag = 1;
     }
     if (EPI == FIT_EPI_NONE) return dead;  // no barrier: a dead warp leaves on its own

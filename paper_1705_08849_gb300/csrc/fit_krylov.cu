@@ -1233,7 +1233,7 @@ __global__ void __launch_bounds__(256) k_fg_cgs_bulk(const typename cplx<T>::t* 
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         bad = 1;
-        atomicExch(p.err, (p.abort && *p.abort) ? 2 : 1);
+        atomicMax(p.err, (p.abort && *p.abort) ? 2 : 1);
       }
       break;
     }
@@ -1418,7 +1418,7 @@ __global__ void k_cond(const Sys* __restrict__ sys, Ctl* ctl, P p, int which, in
     bool stop = false;
     if (p.abort && (which == 1 || (*guard & 63) == 1) && *p.abort) {
       stop = true;
-      atomicExch(p.err, 2);
+      atomicMax(p.err, 2);
     }
     int v = (!stop && any && *guard < guard_max) ? 1 : 0;
     ctl->cond = v;

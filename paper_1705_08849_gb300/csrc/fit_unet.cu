@@ -164,10 +164,34 @@ fit_status launch_conv3(const unet::ConvArgs& a, cudaStream_t s) {
   return FIT_OK;
 }
 
+static bool conv_use_tc();
+
+// tcgen05 transposed conv: persistent CTAs, as many per SM as its TMEM holds accumulators for
+template <int CIN, int COUT>
+fit_status tconv_fwd_tc(const bf16* in, const float* w, const float* b, bf16* out, int mx, int my, int mz,
+                        cudaStream_t s) {
+  using SH = unet::TconvTc<CIN, COUT>;
+  auto kern = unet::tconv_tc_kernel<CIN, COUT>;
+  constexpr int smem = SH::smem();
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    FIT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FIT_CHECK_CUDA(cudaGetDevice(&dev));
+    FIT_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long ntiles = ((long long)mx * my * mz + 127) / 128;
+  const int grid = (int)std::min<long long>(ntiles, (long long)nsm * SH::PER_SM);
+  kern<<<grid, 128, smem, s>>>(in, w, b, out, mx, my, mz);
+  FIT_CHECK_CUDA(cudaGetLastError());
+  return FIT_OK;
+}
+
 // 2x2x2 transposed conv from an mx x my x mz coarse grid to the 2x finer one
 template <int CIN, int COUT>
 fit_status tconv_fwd(const bf16* in, const float* w, const float* b, bf16* out, int mx, int my, int mz,
                      cudaStream_t s) {
+  if (conv_use_tc()) return tconv_fwd_tc<CIN, COUT>(in, w, b, out, mx, my, mz, s);
   auto kern = unet::tconv_fwd_kernel<CIN, COUT>;
   constexpr int smem = unet::tconv_smem<CIN, COUT>();
   static bool attr = false;

@@ -637,7 +637,8 @@ __global__ void pool_bwd_kernel(const bf16* dout, bf16* din, int c, int nx, int 
 }
 
 // ---- 2x2x2 transposed convolution, stride 2 (coarse -> fine) -------------------------------------
-// out[x][y][z][co] = b[co] + sum_ci in[x/2][y/2][z/2][ci] * W[(z%2, y%2, x%2)][co][ci]
+// out[x][y][z][co] = b[co] + sum_ci in[x/2][y/2][z/2][ci] * W[(z%2, y%2, x%2)][co][ci], W rounded to
+// bf16 (like the 3x3x3 convolutions' weights), b in FP32
 template <int CIN, int COUT>
 constexpr int tconv_smem() {
   return (COUT * CIN * 8 + COUT) * (int)sizeof(float);
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(256) tconv_fwd_kernel(const bf16* in, const fl
   float* b_s = tc_smem + COUT * CIN * 8;
   for (int q = threadIdx.x; q < COUT * CIN * 8; q += blockDim.x) {
     const int k = q & 7, ci = (q >> 3) % CIN, co = (q >> 3) / CIN;
-    w_s[q] = w[(k * COUT + co) * CIN + ci];
+    w_s[q] = __bfloat162float(__float2bfloat16(w[(k * COUT + co) * CIN + ci]));
   }
   for (int q = threadIdx.x; q < COUT; q += blockDim.x) b_s[q] = b[q];
   __syncthreads();
@@ -694,6 +695,149 @@ __global__ void __launch_bounds__(256) tconv_fwd_kernel(const bf16* in, const fl
   }
 }
 
+// The same transposed convolution on the 5th-generation tensor cores, one GEMM per tile of 128
+// consecutive coarse voxels V0 .. V0+127:
+//   D[V][k * COUT + co] = sum_ci in[V][ci] * W[k][co][ci]      (M = 128, N = 8 * COUT, K = CIN)
+//   out[child(V, k)][co] = bf16(D[V][k * COUT + co] + b[co])
+// with bf16 weights (rounded from the FP32 master copy when the CTA stages them) and FP32
+// accumulation in TMEM.  Operands in the canonical K-major layout without swizzle: the tile as
+// [g = CIN/8][v = 128] lines of 16 B (cp.async, zero fill past the last voxel), the weights as
+// [g][n = 8 * COUT] lines.  Persistent CTAs of 4 warps (warp w reads TMEM lanes 32w .. 32w+31, one
+// coarse voxel per thread); the dynamic shared memory is padded so that no more CTAs share an SM
+// than its 512 TMEM columns hold.
+template <int CIN, int COUT>
+struct TconvTc {
+  static constexpr int CG = CIN / 8, N = 8 * COUT;
+  static constexpr int ABYTES = CG * 128 * 16;
+  static constexpr int BBYTES = CG * N * 16;
+  static constexpr int OFF_BAR = ABYTES + BBYTES;
+  static constexpr int PER_SM = 512 / N;  // CTAs whose accumulators fit in one SM's TMEM
+  static constexpr int need() { return OFF_BAR + 32 + 1024; }  // two barriers, the TMEM address, alignment slack
+  static constexpr int smem() {
+    return need() > 232448 / (PER_SM + 1) + 1024 ? need() : 232448 / (PER_SM + 1) + 1024;
+  }
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) tconv_tc_kernel(const bf16* in, const float* w, const float* b, bf16* out,
+                                                       int mx, int my, int mz) {
+  using SH = TconvTc<CIN, COUT>;
+  constexpr int CG = SH::CG, N = SH::N;
+  static_assert(CIN % 16 == 0 && COUT % 16 == 0 && N <= 256, "tcgen05 transposed conv shape");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_s = smem_addr(smem), b_s = smem_addr(smem + SH::ABYTES);
+  const uint32_t bar = smem_addr(smem + SH::OFF_BAR), done = bar + 8;
+  uint32_t* tmem_slot = (uint32_t*)(smem + SH::OFF_BAR + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long nvc = (long long)mx * my * mz;
+  const long long ntiles = (nvc + 127) / 128;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "n"(N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    tc_mbar_init(bar, 1);
+    tc_mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // weights: line (g, n = k * COUT + co) holds bf16(W[k][co][8g .. 8g+7])
+  for (int q = tid; q < CG * N; q += 128) {
+    const int n = q % N, g = q / N;
+    const float* src = w + (long long)n * CIN + g * 8;
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 pv = __floats2bfloat162_rn(src[2 * e], src[2 * e + 1]);
+      pk[e] = *reinterpret_cast<const uint32_t*>(&pv);
+    }
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(b_s + q * 16), "r"(pk[0]), "r"(pk[1]), "r"(pk[2]),
+                 "r"(pk[3])
+                 : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+  constexpr uint32_t IDESC = tc_idesc_bf16(128, N);
+
+  int it = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const long long V0 = t * 128;
+    for (int q = tid; q < 128 * CG; q += 128) {  // line (g, v) <- in[V0 + v][8g .. 8g+7]
+      const int v = q % 128, g = q / 128;
+      const bool ok = V0 + v < nvc;
+      cp_async16(a_s + (g * 128 + v) * 16, ok ? (const void*)(in + (V0 + v) * CIN + g * 8) : (const void*)in, ok ? 16 : 0);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tile and the weights, to the tensor core
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < CIN / 16; ++kk) {
+        const uint64_t ad = tc_smem_desc(a_s + kk * 2 * 128 * 16, 128 * 16, 128);
+        const uint64_t bd = tc_smem_desc(b_s + kk * 2 * N * 16, N * 16, 128);
+        const uint32_t acc = kk != 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+            : "memory");
+      }
+      tc_commit(bar);
+    }
+    const bool ok = tc_mbar_wait(bar, it & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(&g_conv_timeout, 1);
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const long long V = V0 + 32 * warp + lane;
+    const bool valid = V < nvc;
+    const int x = (int)(V % mx), y = (int)((V / mx) % my), z = (int)(V / ((long long)mx * my));
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+      float v[COUT];
+#pragma unroll
+      for (int h = 0; h < COUT / 16; ++h) tc_ld16(taddr + k * COUT + 16 * h, v + 16 * h);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!valid) continue;
+      const long long child =
+          (2 * x + (k & 1)) + 2LL * mx * ((2 * y + ((k >> 1) & 1)) + 2LL * my * (2 * z + (k >> 2)));
+      uint4* op = reinterpret_cast<uint4*>(out + child * COUT);
+#pragma unroll
+      for (int c8 = 0; c8 < COUT / 8; ++c8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int co = c8 * 8 + 2 * e;
+          const __nv_bfloat162 pv = __floats2bfloat162_rn(v[co] + b[co], v[co + 1] + b[co + 1]);
+          pk[e] = *reinterpret_cast<const uint32_t*>(&pv);
+        }
+        op[c8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM read out and the tile's smem free before the next tile
+  }
+  if (tid == 0) {  // every MMA issued has completed before the columns are freed (bounded)
+    tc_commit(done);
+    (void)tc_mbar_wait(done, 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(N) : "memory");
+  }
+}
+
 // din[V][ci] = sum_{k, co} dout[child(V, k)][co] * W[k][co][ci]
 __global__ void tconv_bwd_data_kernel(const bf16* dout, const float* w, bf16* din, int cin, int cout, int nx, int ny,
                                       int nz) {
@@ -708,7 +852,8 @@ __global__ void tconv_bwd_data_kernel(const bf16* dout, const float* w, bf16* di
       const int x = 2 * X + (k & 1), y = 2 * Y + ((k >> 1) & 1), z = 2 * Z + (k >> 2);
       const bf16* dp = dout + (x + (long long)nx * (y + (long long)ny * z)) * cout;
       const float* wp = w + (long long)k * cout * cin + ci;
-      for (int co = 0; co < cout; ++co) s += __bfloat162float(dp[co]) * wp[(long long)co * cin];
+      for (int co = 0; co < cout; ++co)  // the bf16 weights the forward pass multiplies with
+        s += __bfloat162float(dp[co]) * __bfloat162float(__float2bfloat16(wp[(long long)co * cin]));
     }
     din[t] = __float2bfloat16(s);
   }

@@ -17,13 +17,16 @@ early and late iterates alike.  Pairs stay on the GPU as one bf16 shard per geom
 inside the 288 GB of HBM), so training never waits on storage.
 
 Training.  Adam (cosine learning rate) with the library's own forward and backward kernels, one pair per
-step in a shuffled order, the parameters with the lowest validation loss (held-out geometries) kept.  The
-default loss is the residual angle (fit_unet_train_step_residual): with z = U(in) and w = A z on the pair's
-own grid and frequency, L = 1 - |<w, r^>|^2 / (||w||^2 ||r^||^2), the part of the residual the network's
-direction cannot remove, which is what flexible GMRES gains from it.  ``--loss error`` trains on the
-error direction instead, ||U(in) - e^||^2 / ||e^||^2: a network that gets the error's direction to within
-18% in that norm still leaves a residual A amplifies (the high-frequency part of its error), so it does
-not help the solver; the residual angle measures the error in the norm the solver sees.
+step in a shuffled order, the parameters with the lowest validation loss (held-out geometries) kept.  Two
+losses, run as stages in the order ``--loss`` lists them (default: error, then residual):
+  - error: the error direction, ||U(in) - e^||^2 / ||e^||^2;
+  - residual: the residual angle (fit_unet_train_step_residual): with z = U(in) and w = A z on the pair's
+    own grid and frequency, L = 1 - |<w, r^>|^2 / (||w||^2 ||r^||^2), the part of the residual the
+    network's direction cannot remove, which is what flexible GMRES gains from it.
+A network that gets the error's direction to within 18% in the first norm still leaves a residual that A
+amplifies (the high-frequency part of its error), so it does not help the solver by itself; the residual
+angle measures the error in the norm the solver sees, and the first stage gives it a start with a
+non-zero output (the angle has no gradient at z = 0).
 
 Evaluation (``evaluate``).  FGMRES(30) with one direction from the network per restart cycle (z_1 =
 U(v_0), v_0 the cycle's normalised true residual, the input the pairs are made of; the Jacobi direction
@@ -226,6 +229,17 @@ def evaluate(net, seeds, freqs, n=128, methods=tuple(METHODS), tol=1e-8, max_ite
     return out
 
 
+def seed_head(net, seed, scale=0.1):
+    """Give the 1x1x1 head (the last 6 x 16 weights and 6 biases of the flat parameters) a small seeded
+    He-normal start.  The library starts it at zero, so that an untrained network adds nothing to the
+    preconditioner; the residual angle has no gradient at a zero output, so a residual-angle stage
+    that starts from scratch starts from here."""
+    p = net.get_params()
+    rng = np.random.default_rng(seed)
+    p[-(6 * 16 + 6):-6] = (scale * np.sqrt(2.0 / 16) * rng.standard_normal(6 * 16)).astype(p.dtype)
+    net.set_params(p)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--out", required=True)
@@ -236,7 +250,10 @@ def main(argv=None):
     ap.add_argument("--epochs", type=float, default=3.0)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--seed", type=int, default=1000)
-    ap.add_argument("--loss", default="residual", choices=["residual", "error"])
+    ap.add_argument("--loss", default="error,residual",
+                    help="comma list of training stages, each 'error' or 'residual', run in order with --epochs "
+                         "epochs each (default: the error direction first, then the residual angle)")
+    ap.add_argument("--init", default="", help="checkpoint to start from (default: the library's seeded start)")
     ap.add_argument("--eval-n", type=int, default=0, help="grid of an evaluation on unseen geometries (0: none)")
     ap.add_argument("--eval-seeds", default="5000")
     ap.add_argument("--eval-freqs", default="1e9,4e9,7e9,10e9")
@@ -254,17 +271,28 @@ def main(argv=None):
     t_h = time.time() - t0
     npairs = sum(sh["pairs"].shape[0] for sh in shards)
     net = fit.UNet(seed=args.seed)
-    v0 = validate(net, val, args.n, loss=args.loss) if val else None
+    if args.init:
+        load(net, args.init)
+    stages = [v for v in args.loss.split(",") if v]
+    if any(v not in ("error", "residual") for v in stages):
+        raise SystemExit(f"--loss: unknown stage in {args.loss!r}")
+    if stages and stages[0] == "residual" and not args.init:
+        seed_head(net, args.seed)
     t1 = time.time()
-    hist, steps = train(net, shards, args.n, args.epochs, lr=args.lr, val=val, loss=args.loss)
+    record_stages, steps = [], 0
+    for loss in stages:
+        v0 = validate(net, val, args.n, loss=loss) if val else None
+        hist, k = train(net, shards, args.n, args.epochs, lr=args.lr, val=val, loss=loss)
+        steps += k
+        record_stages.append({"loss": loss, "steps": k, "final_train_loss": float(np.mean(hist[-max(1, k // 10):])),
+                              "validation_loss_initial": v0,
+                              "validation_loss_final": validate(net, val, args.n, loss=loss) if val else None})
+        print(json.dumps(record_stages[-1]), flush=True)
     t_t = time.time() - t1
-    v1 = validate(net, val, args.n, loss=args.loss) if val else None
     record = {"geometries": [seeds[0], seeds[args.geometries - 1]], "validation_geometries": seeds[args.geometries:],
               "n": args.n, "pairs": npairs, "pairs_per_geometry": per, "epochs": args.epochs, "steps": steps,
-              "loss": args.loss,
-              "lr": args.lr, "harvest_s": t_h, "train_s": t_t,
-              "final_train_loss": float(np.mean(hist[-max(1, steps // 10):])),
-              "validation_loss_initial": v0, "validation_loss_final": v1}
+              "stages": record_stages, "init": os.path.basename(args.init) if args.init else None,
+              "lr": args.lr, "harvest_s": t_h, "train_s": t_t}
     save(net, args.out, record)
     print(json.dumps(record), flush=True)
     for sh in shards + (val or []):

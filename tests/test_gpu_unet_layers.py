@@ -107,7 +107,7 @@ def test_conv3_wgrad(cin, cout):
 
 
 @pytest.mark.parametrize("cin,cout", [(64, 32), (32, 16)])
-def test_tconv_forward_and_backward(cin, cout):
+def test_tconv_forward_and_backward(cin, cout, conv_kernel):
     torch = torch_cuda()
     fit = fitlib()
     from oracle import unet as U
@@ -120,14 +120,15 @@ def test_tconv_forward_and_backward(cin, cout):
     out = torch.empty(8 * mz * my * mx, cout, dtype=torch.bfloat16, device="cuda")
     fit.fit_unet_tconv(mx, my, mz, cin, cout, xb.cuda(), wd, bd, out)
     torch.cuda.synchronize()
-    _check_bf16(torch, out.cpu(), U.tconv_loops(x64, w.astype(np.float64), b.astype(np.float64)))
+    w64 = _bf16(torch, w).double().numpy()  # the network multiplies with bf16 weights
+    _check_bf16(torch, out.cpu(), U.tconv_loops(x64, w64, b.astype(np.float64)))
     gb, g64 = _inputs(torch, cin * 3 + cout + 1, (2 * mz, 2 * my, 2 * mx), cout)
     din = torch.empty(mz * my * mx, cin, dtype=torch.bfloat16, device="cuda")
     dw = torch.full((8, cout, cin), float("nan"), device="cuda")
     db = torch.full((cout,), float("nan"), device="cuda")
     fit.fit_unet_tconv_backward(mx, my, mz, cin, cout, xb.cuda(), gb.cuda(), wd, din, dw, db)
     torch.cuda.synchronize()
-    _check_bf16(torch, din.cpu(), U.tconv_dgrad_loops(g64, w.astype(np.float64)))
+    _check_bf16(torch, din.cpu(), U.tconv_dgrad_loops(g64, w64))
     dwo, dbo = U.tconv_wgrad_loops(x64, g64)
     _check_f32(dw.cpu().numpy(), dwo)
     _check_f32(db.cpu().numpy(), dbo)
