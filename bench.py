@@ -186,8 +186,8 @@ def parse_kind(fit, kind):
     "mixed" (complex64 inner solve inside FP64 refinement) or "c128"; pc jacobi (the Eq. Precond
     diagonal, the default), eps (M_eps^-1: the symmetrised form's change of variable, Eq. e2s), none, or
     unet (the learned preconditioner from the committed checkpoint: one direction from the network per
-    restart cycle, the Jacobi term on the other steps; FGMRES mixed only) / unet/K (the network's direction
-    on the steps j = 1 mod K).
+    restart cycle, at its last step, the Jacobi term on the other steps; FGMRES mixed only) / unet/K (the
+    network's direction on the steps j with (j + 1) % K == 0).
     Returns (method, precision, precond, label, pc_every)."""
     base, _, pcname = kind.partition("+")
     pcname = pcname or "jacobi"
@@ -427,7 +427,7 @@ def main():
                     help="comma list of solves to time, each [method-]precision[+pc] with method fgmres (default), "
                          "cocg, cocr or bicgstab, precision mixed or c128, pc jacobi (default), eps, none or unet "
                          "(FGMRES mixed: the committed network's direction once per restart cycle; unet/K: on the "
-                         "steps j = 1 mod K); none for no solve.  The default times the fastest mixed solve, "
+                         "steps j with (j + 1) %% K == 0); none for no solve.  The default times the fastest mixed solve, "
                          "FGMRES(30) mixed without and with the learned network, and the plain complex128 COCG "
                          "and FGMRES(30)")
     ap.add_argument("--max-iter", type=int, default=80000, help="Krylov iteration cap of the timed solves")

@@ -192,9 +192,10 @@ typedef struct fit_solve_opts {
                         (h * nfreq + f) * n_e (used to harvest training pairs); NULL = off */
   int history_len;   /* slots in history (per system) */
   int history_every; /* outer steps between snapshots (>= 1) */
-  int pc_every;      /* FIT_PC_UNET: the Arnoldi steps j of a cycle with j % pc_every == 1 take the network's
-                        direction z_j = U(v_{j-1}), all others the Jacobi term z_j = D^-1 v_j; 0 (the default)
-                        means once per cycle, at j = 1, where the network's input is the cycle's first vector:
+  int pc_every;      /* FIT_PC_UNET: the Arnoldi steps j = 0 .. m-1 of a cycle with (j + 1) % pc_every == 0
+                        take the network's direction z_j = U(v_{j+1-pc_every}) (see fit_set_preconditioner),
+                        all others the Jacobi term z_j = D^-1 v_j; 0 (the default) means pc_every = m: once
+                        per cycle, at its last step, where the network's input is the cycle's first vector,
                         the normalised true residual it was trained on.  0 or >= 2 */
 } fit_solve_opts;
 
@@ -386,13 +387,16 @@ fit_status fit_unet_residual_loss(fit_unet* net, fit_grid* g, double omega, cons
                                   void* stream);
 
 /* attach a network to the grid; fit_solve with precond = FIT_PC_UNET (FGMRES, FIT_SOLVE_MIXED) then
- * gives flexible GMRES one direction from the network per restart cycle (see fit_solve_opts.pc_every):
- * z_1 = U(v_0) / sqrt(n_e) + 1e-3 D^-1 v_1, v_0 the normalised residual of the cycle, which the network
- * maps to the direction of the current error (fit_unet_training_pair); every other step takes the Jacobi
- * direction D^-1 v_j.  The small Jacobi term keeps z_1 usable if the network outputs zero (an untrained
- * network, whose head starts at zero, gives exactly Jacobi FGMRES).  The residual minimisation decides how much of the network's direction to use, so a poor
- * network costs its application time but cannot stop the Jacobi directions from converging.  The grid
- * does not own the network. */
+ * gives flexible GMRES one direction from the network per restart cycle by default (see
+ * fit_solve_opts.pc_every): at the cycle's last Arnoldi step j = m-1,
+ *     z_j = U(v_0) / sqrt(n_e) + 1e-3 D^-1 v_j,
+ * v_0 the normalised residual of the cycle, which the network maps to a correction direction
+ * (fit_unet_training_pair, fit_unet_train_step_residual); every other step takes the Jacobi direction
+ * D^-1 v_j.  The cycle's subspace is thus the Jacobi Krylov subspace of m-1 steps plus the network's
+ * direction.  The small Jacobi term keeps z_j usable if the network outputs zero (an untrained network,
+ * whose head starts at zero, gives exactly Jacobi FGMRES).  The residual minimisation decides how much of
+ * the network's direction to use, so a poor network costs its application time but cannot stop the
+ * Jacobi directions from converging.  The grid does not own the network. */
 fit_status fit_set_preconditioner(fit_grid* g, int kind, fit_unet* net);
 
 /* fit_jacobi -- y_b = D(omega_b)^-1 x_b with D = diag(A(omega)): for an unmasked edge the sum of M_nu

@@ -28,7 +28,7 @@ def test_parse_kind(kind, want):
 
 def test_learned_kinds_place_the_network():
     assert bench.parse_kind(_Consts, "fgmres-mixed+unet")[4] == 0  # once per restart cycle (the default)
-    assert bench.parse_kind(_Consts, "fgmres-mixed+unet/3")[4] == 3  # steps j = 1 mod 3
+    assert bench.parse_kind(_Consts, "fgmres-mixed+unet/3")[4] == 3  # steps j with (j + 1) % 3 == 0
 
 
 @pytest.mark.parametrize("kind", ["cocg", "cocg-fp32", "gmres-mixed", "cocg-mixed+ilu", "none", "",
