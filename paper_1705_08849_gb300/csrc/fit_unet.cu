@@ -206,22 +206,23 @@ fit_status tconv_fwd(const bf16* in, const float* w, const float* b, bf16* out, 
 }
 
 // 5D tensor map {8 channels, C/8 groups, nx, ny, nz} of an NDHWC bf16 activation with C channels,
-// box {8, 1, 32, 6, 1}: one channel group of a 32 x 6 voxel window of one plane (the tcgen05 conv's
-// staged copy layout)
+// box {8, 1, 10, 18, 1}: one channel group of the 10 x 18 voxel window (an 8 x 16 tile and its halo)
+// of one plane, the tcgen05 conv's staged layout
 static bool conv_tmap(CUtensorMap* m, const bf16* base, int c, int nx, int ny, int nz) {
   const cuuint64_t dims[5] = {8, (cuuint64_t)(c / 8), (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t strides[4] = {16, (cuuint64_t)c * 2, (cuuint64_t)nx * c * 2, (cuuint64_t)nx * ny * c * 2};
-  const cuuint32_t box[5] = {8, 1, (cuuint32_t)unet::CX, (cuuint32_t)unet::UmmaShape<16, 16, 4>::ROWS, 1};
+  using SH = unet::UmmaShape<16, 16, 4>;
+  const cuuint32_t box[5] = {8, 1, (cuuint32_t)SH::PX, (cuuint32_t)SH::PY, 1};
   return fit_tmap_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box);
 }
 
-// tcgen05 conv3: 32 x 4 voxel tiles, all output channels per CTA, the same z-chunking rule as
+// tcgen05 conv3: 8 x 16 voxel tiles, all output channels per CTA, the same z-chunking rule as
 // launch_conv3
 template <int CIN, int NC, int S>
 fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
   auto kern = unet::conv3_tc_kernel<CIN, NC, S>;
   constexpr int smem = unet::UmmaShape<CIN, NC, S>::smem();
-  constexpr int TY = unet::UmmaShape<CIN, NC, S>::TY;
+  constexpr int TX = unet::UmmaShape<CIN, NC, S>::TX, TY = unet::UmmaShape<CIN, NC, S>::TY;
   static int per_sm = 0, nsm = 0;
   if (per_sm == 0) {
     int dev = 0;
@@ -242,7 +243,7 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
     return FIT_ECUDA;
   }
   if (a.c2 == 0) m2 = m1;
-  const int gx = (a.nx + unet::CX - 1) / unet::CX, gy = (a.ny + TY - 1) / TY;
+  const int gx = (a.nx + TX - 1) / TX, gy = (a.ny + TY - 1) / TY;
   const long long cols = (long long)gx * gy;
   const long long per_col = std::max(1LL, (long long)per_sm * nsm / cols);
   const int tz = (int)std::max(2LL, ((long long)a.nz + per_col - 1) / per_col);
@@ -253,9 +254,9 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
   return FIT_OK;
 }
 
-// FIT_CONV=mma keeps every conv on the legacy mma.sync kernel; FIT_CONV=tc runs the shapes with 16 or
-// 32 input channels on the tcgen05 kernel (the 64-input-channel convs need more shared memory than a
-// staged ring of three shifted plane copies leaves, and stay on mma.sync).
+// FIT_CONV=mma keeps every conv on the legacy mma.sync kernel; FIT_CONV=tc runs every shape but 64 -> 64
+// on the tcgen05 kernel (the 64 x 64 x 27 bf16 weights alone take 221 KB of shared memory; that conv,
+// at 32^3, stays on mma.sync).
 static bool conv_use_tc() {
   const char* e = getenv("FIT_CONV");
   return e && !strcmp(e, "tc");
@@ -267,12 +268,14 @@ static fit_status conv3_tc(const unet::ConvArgs& a, int cin, cudaStream_t s, boo
   *done = false;
   if (!conv_use_tc() || a.c1 % 8 || a.c2 % 8 || a.o1 % 8 || a.o2 % 8 || a.cout > 64) return FIT_OK;
   *done = true;
-  if (cin == 16 && a.cout <= 16) return launch_conv3_tc<16, 16, 4>(a, s);
-  if (cin == 16 && a.cout <= 32) return launch_conv3_tc<16, 32, 4>(a, s);
-  if (cin == 16) return launch_conv3_tc<16, 64, 4>(a, s);
-  if (cin == 32 && a.cout <= 16) return launch_conv3_tc<32, 16, 5>(a, s);
-  if (cin == 32 && a.cout <= 32) return launch_conv3_tc<32, 32, 4>(a, s);
-  if (cin == 32) return launch_conv3_tc<32, 64, 3>(a, s);
+  // shared memory per CTA: weights 27 * cin * NC * 2 B plus S planes of cin / 8 * 2944 B
+  if (cin == 16 && a.cout <= 16) return launch_conv3_tc<16, 16, 6>(a, s);  // 50 KB
+  if (cin == 16 && a.cout <= 32) return launch_conv3_tc<16, 32, 4>(a, s);  // 52 KB
+  if (cin == 16) return launch_conv3_tc<16, 64, 4>(a, s);                  // 79 KB
+  if (cin == 32 && a.cout <= 16) return launch_conv3_tc<32, 16, 4>(a, s);  // 76 KB
+  if (cin == 32 && a.cout <= 32) return launch_conv3_tc<32, 32, 4>(a, s);  // 103 KB
+  if (cin == 32) return launch_conv3_tc<32, 64, 4>(a, s);                  // 159 KB
+  if (cin == 64 && a.cout <= 32) return launch_conv3_tc<64, 32, 4>(a, s);  // 206 KB
   *done = false;
   return FIT_OK;
 }

@@ -203,20 +203,22 @@ __global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a, int tz) {
 // ------------------------------------------------------------------------------------------------
 // The same 3x3x3 convolution on the 5th-generation tensor cores: tcgen05.mma with FP32 accumulators
 // in TMEM, input planes staged by TMA (cp.async.bulk.tensor), warp-specialised and pipelined.
-// A CTA owns a 32 x 4 tile of output voxels in (x, y) (M = 128 rows of the MMA, row m = voxel
-// (x0 + m % 32, y0 + m / 32)), all NC output channels (N), and marches a chunk of z-planes.
-//   warp 0 (lane 0): the producer.  Input plane p is staged three times, shifted by dx = 0, 1, 2
-//     voxels along x, as [g = CIN/8][r = 6 rows][v = 32] lines of 16 B (8 channels): one 5D TMA box
-//     {8 channels, 1 group, 32 voxels, 6 rows, 1 plane} per (dx, group), zero-filled outside the grid.
-//     The 128 M-rows of a tap's window (rows dy .. dy+3) are then 128 consecutive lines: canonical
-//     K-major, no swizzle, core matrices 128 B apart along M (SBO), channel groups LINES * 16 B apart
-//     (LBO).  A ring of S planes; output plane z reads planes z-1, z, z+1.
+// A CTA owns an 8 x 16 tile of output voxels in (x, y) (M = 128 rows of the MMA, row m = voxel
+// (x0 + m % 8, y0 + m / 8)), all NC output channels (N), and marches a chunk of z-planes.
+//   warp 0 (lane 0): the producer.  Input plane p is staged once, with its halo, as
+//     [g = CIN/8][r = 18 rows][v = 10 voxels] lines of 16 B (8 channels): one 5D TMA box
+//     {8 channels, 1 group, 10 voxels, 18 rows, 1 plane} per channel group, zero-filled outside the
+//     grid.  In the canonical K-major layout without swizzle a core matrix is 8 consecutive lines,
+//     here the 8 voxels of one tile row; the tap (dy, dx) window starts at line dy * 10 + dx, its
+//     16 core matrices along M (the tile's rows) are 10 lines = 160 B apart (SBO) and the channel
+//     groups GROUP bytes apart (LBO).  The x shift of a tap is thus a start offset, not a copy.
+//     A ring of S planes; output plane z reads planes z-1, z, z+1.
 //   warp 1 (lane 0): the MMA issuer.  For output plane z it issues the 27 * CIN / 16 MMAs of
 //     128 x NC x 16 into accumulator z % 2 (two TMEM buffers of NC columns), then commits them to
 //     that buffer's "full" barrier and to the "empty" barrier of plane z-1's ring slot.
-//   warps 2..5: the epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (tile row w % 4) of the
-//     finished buffer, hands the buffer back, then adds the bias, applies the ReLU and stores bf16
-//     (16 B per 8 channels) to the one or two outputs.
+//   warps 2..5: the epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows 4 (w % 4) ..
+//     +3) of the finished buffer, hands the buffer back, then adds the bias, applies the ReLU and
+//     stores bf16 (16 B per 8 channels) to the one or two outputs.
 // So the copies of plane z+2, the MMAs of plane z+1 and the epilogue of plane z run at the same time.
 // Weights: [tap][g][n] lines (SBO 128 B, LBO NC * 16 B), staged once per CTA with cp.async.
 // Every wait is bounded; a role that gives up records it in g_conv_timeout and raises the CTA's stop
@@ -227,11 +229,12 @@ __device__ int g_conv_timeout;
 
 template <int CIN, int NC, int S>
 struct UmmaShape {
-  static constexpr int TY = 4, ROWS = TY + 2, LINES = ROWS * 32;  // lines per channel group of a copy
+  static constexpr int TX = 8, TY = 16, PX = TX + 2, PY = TY + 2;  // tile and staged plane (with halo)
+  static constexpr int LINES = PX * PY;                             // lines per channel group
   static constexpr int CG = CIN / 8;
-  static constexpr int GROUP = LINES * 16;                         // bytes of one TMA box
-  static constexpr int COPY = CG * GROUP;                          // bytes of one shifted copy
-  static constexpr int PLANE = 3 * COPY;                           // bytes of a staged plane
+  static constexpr int BOX = LINES * 16;                            // bytes one TMA box delivers
+  static constexpr int GROUP = ((BOX + 127) / 128) * 128;           // bytes per group (128 B aligned boxes)
+  static constexpr int PLANE = CG * GROUP;                          // bytes of a staged plane
   static constexpr int WBYTES = 27 * CG * NC * 16;
   static constexpr int OFF_RING = ((WBYTES + 1023) / 1024) * 1024;
   static constexpr int OFF_BAR = OFF_RING + S * PLANE;
@@ -298,14 +301,14 @@ __device__ inline void tc_ld16(uint32_t taddr, float* v) {
   for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-// tm1 / tm2: 5D maps {8 channels, groups, nx, ny, nz} of the two inputs (box {8, 1, 32, 6, 1});
+// tm1 / tm2: 5D maps {8 channels, groups, nx, ny, nz} of the two inputs (box {8, 1, 10, 18, 1});
 // tm2 is unused when a.c2 == 0.  Requires cout <= NC and every channel count a multiple of 8.
 template <int CIN, int NC, int S>
 __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1,
                                                        const __grid_constant__ CUtensorMap tm2, ConvArgs a, int tz) {
   using SH = UmmaShape<CIN, NC, S>;
   constexpr int CG = SH::CG;
-  static_assert(CIN % 16 == 0 && NC % 16 == 0 && NC <= 64 && S >= 3, "tcgen05 conv shape");
+  static_assert(CIN % 16 == 0 && NC % 16 == 0 && NC <= 64 && S >= 3 && SH::smem() <= 232448, "tcgen05 conv shape");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t w_s = smem_addr(smem), ring = smem_addr(smem + SH::OFF_RING);
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
   uint32_t* tmem_slot = (uint32_t*)(smem + SH::OFF_BAR + SH::NBAR * 8);
   volatile int* stop = (volatile int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * CX, y0 = blockIdx.y * SH::TY;
+  const int x0 = blockIdx.x * SH::TX, y0 = blockIdx.y * SH::TY;
   const int z0 = blockIdx.z * tz, z1 = min(a.nz, z0 + tz);
   if (z0 >= z1) return;  // uniform over the CTA, before any TMEM is taken
   const int nout = z1 - z0, nplanes = nout + 2;  // planes z0-1 .. z1
@@ -374,14 +377,10 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
         }
         const int p = z0 - 1 + i;
         const uint32_t dst = ring + s * SH::PLANE;
-        tc_expect_tx(full(s), SH::PLANE);
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          for (int g = 0; g < cg1; ++g)
-            tc_tma_load_5d(dst + dx * SH::COPY + g * SH::GROUP, &tm1, 0, g, x0 - 1 + dx, y0 - 1, p, full(s));
-          for (int g = 0; g < cg2; ++g)
-            tc_tma_load_5d(dst + dx * SH::COPY + (cg1 + g) * SH::GROUP, &tm2, 0, g, x0 - 1 + dx, y0 - 1, p, full(s));
-        }
+        tc_expect_tx(full(s), CG * SH::BOX);  // the boxes' bytes (the 64 B of padding per group stay unwritten)
+        for (int g = 0; g < cg1; ++g) tc_tma_load_5d(dst + g * SH::GROUP, &tm1, 0, g, x0 - 1, y0 - 1, p, full(s));
+        for (int g = 0; g < cg2; ++g)
+          tc_tma_load_5d(dst + (cg1 + g) * SH::GROUP, &tm2, 0, g, x0 - 1, y0 - 1, p, full(s));
       }
       // every copy issued lands before the CTA retires (the last S issued; earlier ones were consumed)
       for (int d = 1; d <= S && d <= i; ++d) (void)tc_mbar_wait(full((i - d) % S), ((i - d) / S) & 1);
@@ -404,11 +403,11 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
         const uint32_t dacc = tmem + (uint32_t)(b * NC);
         for (int tap = 0; tap < 27; ++tap) {
           const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const uint32_t abase = ring + ((j + dz) % S) * SH::PLANE + dx * SH::COPY + dy * 32 * 16;
+          const uint32_t abase = ring + ((j + dz) % S) * SH::PLANE + (dy * SH::PX + dx) * 16;
           const uint32_t bbase = w_s + tap * CG * NC * 16;
 #pragma unroll
           for (int kk = 0; kk < CIN / 16; ++kk) {
-            const uint64_t ad = tc_smem_desc(abase + kk * 2 * SH::GROUP, SH::GROUP, 128);
+            const uint64_t ad = tc_smem_desc(abase + kk * 2 * SH::GROUP, SH::GROUP, SH::PX * 16);
             const uint64_t bd = tc_smem_desc(bbase + kk * 2 * NC * 16, NC * 16, 128);
             const uint32_t acc = (tap | kk) != 0 ? 1u : 0u;
             asm volatile(
@@ -426,8 +425,8 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
     }
   } else {
     // ---------------- epilogue: warps 2..5 ----------------
-    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 = tile row q
-    const int gx = x0 + lane, gy = y0 + q;
+    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 = tile rows 4q .. 4q+3
+    const int gx = x0 + (lane & 7), gy = y0 + 4 * q + (lane >> 3);
     const bool valid = gx < a.nx && gy < a.ny;
     for (int j = 0; j < nout; ++j) {
       const int b = j & 1;
