@@ -239,8 +239,9 @@ struct UmmaShape {
   static constexpr int OFF_RING = ((WBYTES + 1023) / 1024) * 1024;
   static constexpr int OFF_BAR = OFF_RING + S * PLANE;
   static constexpr int NBAR = 2 * S + 5;  // full[S], empty[S], accf[2], acce[2], done
+  static constexpr int OFF_BIAS = OFF_BAR + NBAR * 8 + 16;  // NC FP32 biases (zero past cout or without bias)
   static constexpr int TMEM_COLS = 2 * NC <= 32 ? 32 : (2 * NC <= 64 ? 64 : 128);
-  static constexpr int smem() { return OFF_BAR + NBAR * 8 + 16 + 1024; }  // + slack for 1 KB alignment
+  static constexpr int smem() { return OFF_BIAS + NC * 4 + 1024; }  // + slack for 1 KB alignment
 };
 
 __device__ inline uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -354,6 +355,8 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
     cp_async16(w_s + q * 16, src, in ? 16 : 0);
   }
   cp_async_commit();
+  float* bias_s = (float*)(smem + SH::OFF_BIAS);
+  for (int n = tid; n < NC; n += 192) bias_s[n] = (a.bias && n < a.cout) ? a.bias[n] : 0.f;
   cp_async_wait<0>();
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the weights, to the tensor core's reads
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -453,11 +456,7 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
           uint32_t pk[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            float v0 = v[co + 2 * e], v1 = v[co + 2 * e + 1];
-            if (a.bias) {
-              v0 += a.bias[co + 2 * e];
-              v1 += a.bias[co + 2 * e + 1];
-            }
+            float v0 = v[co + 2 * e] + bias_s[co + 2 * e], v1 = v[co + 2 * e + 1] + bias_s[co + 2 * e + 1];
             if (a.relu) {
               v0 = fmaxf(v0, 0.f);
               v1 = fmaxf(v1, 0.f);

@@ -193,6 +193,8 @@ METHODS = {  # label: (fit_solve method, precision, preconditioner[, pc_every])
     "fgmres30+jacobi": ("FIT_FGMRES", "FIT_SOLVE_MIXED", "FIT_PC_JACOBI"),
     "fgmres30": ("FIT_FGMRES", "FIT_SOLVE_MIXED", "FIT_PC_NONE"),
     "bicgstab": ("FIT_BICGSTAB", "FIT_SOLVE_MIXED", "FIT_PC_NONE"),
+    "bicgstab+jacobi": ("FIT_BICGSTAB", "FIT_SOLVE_MIXED", "FIT_PC_JACOBI"),
+    "cocg+jacobi": ("FIT_COCG", "FIT_SOLVE_MIXED", "FIT_PC_JACOBI"),
 }
 
 
