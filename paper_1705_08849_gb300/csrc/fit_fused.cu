@@ -478,17 +478,23 @@ __device__ inline uint64_t global_ns() {
 }
 // Wait for a handoff between warps of the CTA: spin on try_wait (which itself suspends the thread
 // until the phase completes or a short hardware limit passes) with no sleep in between, so the
-// waiting warp resumes as soon as the other side arrives; gives up after 0.5 s of wall time.
-// The host's abort word ends a wait that has already lasted 20 us (far beyond any handoff of a
-// running apply, so the word, in host memory, is never read on the way of a healthy kernel); abort =
-// nullptr for the waits that let the CTA's own copies land before it leaves.
+// waiting warp resumes as soon as the other side arrives; gives up 0.5 s of wall time after its 256th
+// poll.  The clock is first read at that poll, not on entry, so a handoff that completes sooner (every
+// handoff of a healthy apply) never waits on a timer read.  The host's abort word ends a wait that has
+// already lasted 20 us more (far beyond any handoff of a running apply, so the word, in host memory,
+// is never read on the way of a healthy kernel); abort = nullptr for the waits that let the CTA's own
+// copies land before it leaves.
 __device__ inline bool mbar_wait_handoff(uint64_t* bar, uint32_t parity, const volatile int* abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
+  uint64_t t0 = 0;
   for (uint32_t it = 1; it < (1u << 30); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0u) {
-      const uint64_t dt = global_ns() - t0;
+      const uint64_t now = global_ns();
+      if (it == 256u) {
+        t0 = now;
+        continue;
+      }
+      const uint64_t dt = now - t0;
       if (dt > 500000000ull || (abort && dt > 20000ull && *abort)) return false;
     }
   }
