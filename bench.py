@@ -53,8 +53,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FIT_APPLY_KERNEL after three warm-up steps of this bench) of the launch shapes the autotuner picks
 # on the 128^3 layered workload, one system, complex64; key (warp-specialised, TY, TZ, stages,
 # L2 prefetch).  A shape not in the table reports null.
-TRAFFIC_LAYERED128_C64 = {(1, 8, -1, 4, 0): 166_746_368, (1, 8, -1, 4, 2): 168_329_472,
-                          (0, 8, 0, 3, 0): 163_714_560, (0, 8, 0, 3, 2): 164_562_176}
+TRAFFIC_LAYERED128_C64 = {(1, 8, -1, 4, 0): 168_371_456}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this launch shape on this workload "
+                  "(the apply's ncu summary under profiles/), not measured in this run")
 
 
 def _peaks():
@@ -628,6 +629,7 @@ def main():
     traffic = TRAFFIC_LAYERED128_C64.get(sig) if (args.workload == "layered128" and B == 1 and tuned["choice"] >= 0) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "peak_kind": kind, "traffic": traffic, "traffic_unit": "B per launch",
+            "traffic_source": TRAFFIC_SOURCE if traffic is not None else "no capture of this launch shape",
             "bytes_per_dof": bytes_per_dof,
             "kernel": (("ws_apply_kernel" if tuned["ws"] else "fused_apply_kernel") if tuned["choice"] >= 0
                        else "apply_generic_kernel")}
