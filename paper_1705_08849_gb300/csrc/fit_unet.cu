@@ -223,8 +223,8 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
   auto kern = unet::conv3_tc_kernel<CIN, NC, S>;
   constexpr int smem = unet::UmmaShape<CIN, NC, S>::smem();
   constexpr int TX = unet::UmmaShape<CIN, NC, S>::TX, TY = unet::UmmaShape<CIN, NC, S>::TY;
-  // Resident CTAs per SM, from the SM's shared memory (each CTA also reserves 1 KB), its 512 TMEM columns
-  // and its 2048 threads.  (The runtime's occupancy query answers 1 for this kernel, which left a
+  // Resident CTAs per SM, from the SM's shared memory (each CTA also reserves 1 KB), its 512 TMEM columns,
+  // its 64 K registers and its 2048 threads.  (The runtime's occupancy query answers 1 for this kernel, which left a
   // 128-column grid with one CTA, and one MMA-issuing thread, per SM.)
   static int per_sm = 0, nsm = 0;
   if (per_sm == 0) {
@@ -233,8 +233,11 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
     FIT_CHECK_CUDA(cudaGetDevice(&dev));
     FIT_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     FIT_CHECK_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    FIT_CHECK_CUDA(cudaFuncGetAttributes(&fa, kern));
     const int by_smem = smem_sm / (smem + 1024), by_tmem = 512 / unet::UmmaShape<CIN, NC, S>::TMEM_COLS;
-    const int p = std::min(std::min(by_smem, by_tmem), 2048 / 192);
+    const int by_regs = 65536 / (192 * ((fa.numRegs + 7) / 8 * 8));
+    const int p = std::min(std::min(by_smem, by_tmem), std::min(by_regs, 2048 / 192));
     if (p < 1) {
       fit_set_error("U-Net: tcgen05 conv tile does not fit on an SM");
       return FIT_EINVAL;

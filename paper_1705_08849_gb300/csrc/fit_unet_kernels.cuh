@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t IDESC = tc_idesc_bf16(128, NC);
+      const uint64_t bdesc = tc_smem_desc(w_s, NC * 16, 128);
       int waited = 0;  // planes known to have landed
       for (int j = 0; j < nout; ++j) {
         bool ok = true;
@@ -404,19 +405,24 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dacc = tmem + (uint32_t)(b * NC);
+        // The descriptors of a plane's window and of the weights are formed once; every MMA adds a
+        // compile-time offset (in 16-byte units, inside the 14-bit address field: shared memory is
+        // below 256 KB) to them, with the tap loop unrolled, so that the single issuing thread spends a
+        // few instructions per MMA rather than a chain of address arithmetic.
+        uint64_t adesc[3];
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) adesc[dz] = tc_smem_desc(ring + ((j + dz) % S) * SH::PLANE, SH::GROUP, SH::PX * 16);
+#pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
           const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const uint32_t abase = ring + ((j + dz) % S) * SH::PLANE + (dy * SH::PX + dx) * 16;
-          const uint32_t bbase = w_s + tap * CG * NC * 16;
 #pragma unroll
           for (int kk = 0; kk < CIN / 16; ++kk) {
-            const uint64_t ad = tc_smem_desc(abase + kk * 2 * SH::GROUP, SH::GROUP, SH::PX * 16);
-            const uint64_t bd = tc_smem_desc(bbase + kk * 2 * NC * 16, NC * 16, 128);
-            const uint32_t acc = (tap | kk) != 0 ? 1u : 0u;
+            const uint64_t ad = adesc[dz] + (uint64_t)(((dy * SH::PX + dx) * 16 + kk * 2 * SH::GROUP) >> 4);
+            const uint64_t bd = bdesc + (uint64_t)((tap * CG * NC * 16 + kk * 2 * NC * 16) >> 4);
             asm volatile(
                 "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
-                "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                "l"(ad), "l"(bd), "r"(IDESC), "r"((uint32_t)((tap | kk) != 0 ? 1 : 0))
                 : "memory");
           }
         }
