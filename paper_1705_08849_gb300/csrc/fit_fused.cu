@@ -1279,7 +1279,9 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
   FIT_CHECK_CUDA(cudaEventCreate(&e1));
   fit_epi none;
   // three passes over the candidates (so that slow clocks or a neighbour's traffic during one pass
-  // do not decide), each candidate timed as the median of 7 launches; a candidate keeps its best pass
+  // do not decide), each candidate timed as the mean of the middle 5 of 7 launches (event times of a
+  // single launch come in steps of about 2 us on this part, so a median cannot tell shapes 5% apart);
+  // a candidate keeps its best pass
   std::vector<float> t(n + 1, 1e30f);
   for (int pass = 0; pass < 3; ++pass) {
     for (int c = -1; c < n; ++c) {
@@ -1297,12 +1299,12 @@ fit_status fit_tune_apply(fit_grid* g, int nbatch, const double* omega_dev, cons
         cudaEventElapsedTime(&ms[r], e0, e1);
       }
       std::sort(ms, ms + 7);
-      t[c + 1] = std::min(t[c + 1], ms[3]);
+      t[c + 1] = std::min(t[c + 1], (ms[1] + ms[2] + ms[3] + ms[4] + ms[5]) / 5.0f);
     }
   }
   // The fastest candidate wins, except that a shape with an L2 prefetch must beat the fastest shape
   // without one by 2%: the prefetched planes take L2 room that the tuner's scrubbed L2 does not miss but
-  // a solve's vectors do, and within 2% the two are not told apart by 7-launch medians (on 128^3 the
+  // a solve's vectors do, and within 2% the two are not told apart by the tuner's timing (on 128^3 the
   // even split with a 2-plane prefetch timed level with the plain one here and ran 5% slower in the
   // bench's loop).
   float best_ms = 1e30f, best_np_ms = 1e30f;
