@@ -204,26 +204,32 @@ __global__ void __launch_bounds__(256) conv3_kernel(ConvArgs a, int tz) {
 // The same 3x3x3 convolution on the 5th-generation tensor cores: tcgen05.mma with FP32 accumulators
 // in TMEM, input planes staged by TMA (cp.async.bulk.tensor), warp-specialised and pipelined.
 // A CTA owns an 8 x 16 tile of output voxels in (x, y) (M = 128 rows of the MMA, row m = voxel
-// (x0 + m % 8, y0 + m / 8)), all NC output channels (N), and marches a chunk of z-planes.
+// (x0 + m % 8, y0 + m / 8)), all NC output channels, and marches a chunk of z-planes.
+// The MMAs are organised by input plane, not by output plane: staged plane p feeds output planes
+// p+1, p and p-1 through the z-taps dz = 0, 1, 2, so for each in-plane tap (dy, dx) one MMA with the
+// three z-taps' weights stacked along N (N = 3 NC) reads the plane's window once and adds to three
+// accumulators.  The accumulators live in a ring of R blocks of NC TMEM columns, output plane j of the
+// chunk in block R-1 - j % R: the blocks of outputs j, j-1, j-2 are adjacent in that order, so one MMA
+// writes all three (two MMAs where the ring wraps, one or two blocks at the chunk's ends).  Every MMA
+// accumulates; a block is zeroed (tcgen05.st) at the start and by the epilogue after it drains it.
 //   warp 0 (lane 0): the producer.  Input plane p is staged once, with its halo, as
 //     [g = CIN/8][r = 18 rows][v = 10 voxels] lines of 16 B (8 channels): one 5D TMA box
 //     {8 channels, 1 group, 10 voxels, 18 rows, 1 plane} per channel group, zero-filled outside the
 //     grid.  In the canonical K-major layout without swizzle a core matrix is 8 consecutive lines,
 //     here the 8 voxels of one tile row; the tap (dy, dx) window starts at line dy * 10 + dx, its
 //     16 core matrices along M (the tile's rows) are 10 lines = 160 B apart (SBO) and the channel
-//     groups GROUP bytes apart (LBO).  The x shift of a tap is thus a start offset, not a copy.
-//     A ring of S planes; output plane z reads planes z-1, z, z+1.
-//   warp 1 (lane 0): the MMA issuer.  For output plane z it issues the 27 * CIN / 16 MMAs of
-//     128 x NC x 16 into accumulator z % 2 (two TMEM buffers of NC columns), then commits them to
-//     that buffer's "full" barrier and to the "empty" barrier of plane z-1's ring slot.
+//     groups GROUP bytes apart (LBO).  The x shift of a tap is thus a start offset, not a copy.  A
+//     ring of S planes; each plane is read by the MMAs of one step and then released.
+//   warp 1 (lane 0): the MMA issuer.  For staged plane i of the chunk it issues 9 * CIN / 16 MMAs
+//     (more where the ring wraps), then commits them to the plane's "empty" barrier and to the
+//     "full" barrier of output i-2, which plane i completes.
 //   warps 2..5: the epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows 4 (w % 4) ..
-//     +3) of the finished buffer, hands the buffer back, then adds the bias, applies the ReLU and
+//     +3) of a finished block, zeroes it and hands it back, then adds the bias, applies the ReLU and
 //     stores bf16 (16 B per 8 channels) to the one or two outputs.
-// So the copies of plane z+2, the MMAs of plane z+1 and the epilogue of plane z run at the same time.
-// Weights: [tap][g][n] lines (SBO 128 B, LBO NC * 16 B), staged once per CTA with cp.async.
-// Every wait is bounded; a role that gives up records it in g_conv_timeout and raises the CTA's stop
-// flag, the other roles leave their loops at their next wait, and the CTA frees its TMEM only after
-// a bounded wait for its last MMAs.
+// Weights: [t = dy*3 + dx][g][n3 = dz * NC + n] lines (SBO 128 B, LBO 3 NC * 16 B), staged once per
+// CTA with cp.async.  Every wait is bounded; a role that gives up records it in g_conv_timeout and
+// raises the CTA's stop flag, the other roles leave their loops at their next wait, and the CTA frees
+// its TMEM only after a bounded wait for its last MMAs.
 // ------------------------------------------------------------------------------------------------
 __device__ int g_conv_timeout;
 
@@ -235,12 +241,14 @@ struct UmmaShape {
   static constexpr int BOX = LINES * 16;                            // bytes one TMA box delivers
   static constexpr int GROUP = ((BOX + 127) / 128) * 128;           // bytes per group (128 B aligned boxes)
   static constexpr int PLANE = CG * GROUP;                          // bytes of a staged plane
-  static constexpr int WBYTES = 27 * CG * NC * 16;
+  static constexpr int N3 = 3 * NC;                                 // the three z-taps' output channels
+  static constexpr int WBYTES = 9 * CG * N3 * 16;
   static constexpr int OFF_RING = ((WBYTES + 1023) / 1024) * 1024;
   static constexpr int OFF_BAR = OFF_RING + S * PLANE;
-  static constexpr int NBAR = 2 * S + 5;  // full[S], empty[S], accf[2], acce[2], done
-  static constexpr int OFF_BIAS = OFF_BAR + NBAR * 8 + 16;  // NC FP32 biases (zero past cout or without bias)
-  static constexpr int TMEM_COLS = 2 * NC <= 32 ? 32 : (2 * NC <= 64 ? 64 : 128);
+  static constexpr int R = NC == 64 ? 4 : 8;                        // accumulator blocks in TMEM
+  static constexpr int NBAR = 2 * S + 2 * R + 1;                    // full[S], empty[S], accf[R], acce[R], done
+  static constexpr int OFF_BIAS = OFF_BAR + NBAR * 8 + 16;          // NC FP32 biases (zero past cout or without bias)
+  static constexpr int TMEM_COLS = R * NC <= 32 ? 32 : (R * NC <= 64 ? 64 : (R * NC <= 128 ? 128 : 256));
   static constexpr int smem() { return OFF_BIAS + NC * 4 + 1024; }  // + slack for 1 KB alignment
 };
 
@@ -301,6 +309,23 @@ __device__ inline void tc_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
+// zero 16 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ inline void tc_st16_zero(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+// one MMA of M = 128 into TMEM columns dcol.., N = n (16 .. 256, a multiple of 16), accumulating
+__device__ inline void tc_mma_acc(uint32_t dcol, uint64_t ad, uint64_t bd, int n) {
+  const uint32_t idesc = tc_idesc_bf16(128, 0) | ((uint32_t)(n >> 3) << 17);
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(1u)
+      : "memory");
+}
 
 // tm1 / tm2: 5D maps {8 channels, groups, nx, ny, nz} of the two inputs (box {8, 1, 10, 18, 1});
 // tm2 is unused when a.c2 == 0.  Requires cout <= NC and every channel count a multiple of 8.
@@ -308,17 +333,18 @@ template <int CIN, int NC, int S>
 __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1,
                                                        const __grid_constant__ CUtensorMap tm2, ConvArgs a, int tz) {
   using SH = UmmaShape<CIN, NC, S>;
-  constexpr int CG = SH::CG;
-  static_assert(CIN % 16 == 0 && NC % 16 == 0 && NC <= 64 && S >= 3 && SH::smem() <= 232448, "tcgen05 conv shape");
+  constexpr int CG = SH::CG, R = SH::R, N3 = SH::N3;
+  static_assert(CIN % 16 == 0 && NC % 16 == 0 && NC <= 64 && N3 <= 256 && S >= 2 && SH::smem() <= 232448,
+                "tcgen05 conv shape");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t w_s = smem_addr(smem), ring = smem_addr(smem + SH::OFF_RING);
   const uint32_t bar0 = smem_addr(smem + SH::OFF_BAR);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (S + s); };
-  auto accf = [&](int b) { return bar0 + 8u * (2 * S + b); };
-  auto acce = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
-  const uint32_t done = bar0 + 8u * (2 * S + 4);
+  auto accf = [&](int r) { return bar0 + 8u * (2 * S + r); };
+  auto acce = [&](int r) { return bar0 + 8u * (2 * S + R + r); };
+  const uint32_t done = bar0 + 8u * (2 * S + 2 * R);
   uint32_t* tmem_slot = (uint32_t*)(smem + SH::OFF_BAR + SH::NBAR * 8);
   volatile int* stop = (volatile int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -328,7 +354,7 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
   const int nout = z1 - z0, nplanes = nout + 2;  // planes z0-1 .. z1
   const int cg1 = a.c1 / 8, cg2 = a.c2 / 8;
 
-  if (warp == 1) {  // TMEM: two accumulators of NC FP32 columns (128 lanes)
+  if (warp == 1) {  // TMEM: R accumulator blocks of NC FP32 columns (128 lanes)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "n"(SH::TMEM_COLS)
                  : "memory");
@@ -339,19 +365,21 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
       tc_mbar_init(full(s), 1);
       tc_mbar_init(empty(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      tc_mbar_init(accf(b), 1);
-      tc_mbar_init(acce(b), 4);
+    for (int r = 0; r < R; ++r) {
+      tc_mbar_init(accf(r), 1);
+      tc_mbar_init(acce(r), 4);
     }
     tc_mbar_init(done, 1);
     *stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // weights [tap][g][n] lines (output channels beyond cout are zero)
-  for (int q = tid; q < 27 * CG * NC; q += 192) {
-    const int n = q % NC, g = (q / NC) % CG, tap = q / (NC * CG);
+  // weights: line (t, g, dz * NC + n) = W[dz * 9 + t][n][8g .. 8g+7] (output channels beyond cout are zero)
+  for (int q = tid; q < 9 * CG * N3; q += 192) {
+    const int n3 = q % N3, g = (q / N3) % CG, t = q / (N3 * CG);
+    const int dz = n3 / NC, n = n3 % NC;
     const bool in = n < a.cout;
-    const void* src = in ? (const void*)(a.w + ((long long)tap * a.cout + n) * CIN + g * 8) : (const void*)a.w;
+    const void* src =
+        in ? (const void*)(a.w + ((long long)(dz * 9 + t) * a.cout + n) * CIN + g * 8) : (const void*)a.w;
     cp_async16(w_s + q * 16, src, in ? 16 : 0);
   }
   cp_async_commit();
@@ -363,10 +391,20 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  if (warp >= 2) {  // every accumulator block starts at zero (all MMAs accumulate)
+    const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll
+    for (int c = 0; c < R * NC; c += 16) tc_st16_zero(tl + c);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   auto fail = [&]() {
     atomicExch(&g_conv_timeout, 1);
     *stop = 1;
   };
+  auto blk = [&](int j) { return (R - 1) - j % R; };  // the TMEM block of output plane j of the chunk
 
   if (warp == 0) {
     // ---------------- producer ----------------
@@ -391,43 +429,40 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr uint32_t IDESC = tc_idesc_bf16(128, NC);
-      const uint64_t bdesc = tc_smem_desc(w_s, NC * 16, 128);
-      int waited = 0;  // planes known to have landed
-      for (int j = 0; j < nout; ++j) {
-        bool ok = true;
-        for (; waited < j + 3 && ok; ++waited) ok = tc_mbar_wait(full(waited % S), (waited / S) & 1, stop);
-        const int b = j & 1;
-        if (ok && j >= 2) ok = tc_mbar_wait(acce(b), ((j >> 1) - 1) & 1, stop);
+      const uint64_t bdesc = tc_smem_desc(w_s, N3 * 16, 128);
+      for (int i = 0; i < nplanes; ++i) {
+        // plane i feeds outputs j = i - dz for dz in [dz_lo, dz_hi] (those inside the chunk)
+        const int dz_lo = max(0, i - (nout - 1)), dz_hi = min(2, i);
+        bool ok = tc_mbar_wait(full(i % S), (i / S) & 1, stop);
+        if (ok && dz_lo == 0 && i >= R) ok = tc_mbar_wait(acce(i % R), ((i / R) - 1) & 1, stop);  // block of output i free
         if (!ok) {
           fail();
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dacc = tmem + (uint32_t)(b * NC);
-        // The descriptors of a plane's window and of the weights are formed once; every MMA adds a
-        // compile-time offset (in 16-byte units, inside the 14-bit address field: shared memory is
-        // below 256 KB) to them, with the tap loop unrolled, so that the single issuing thread spends a
-        // few instructions per MMA rather than a chain of address arithmetic.
-        uint64_t adesc[3];
+        // the dz range in at most two runs of adjacent blocks: the ring wraps after the output whose
+        // block is R-1 (j % R == 0), at most once in three outputs (R >= 4)
+        int brk = -1;
+        for (int dz = dz_lo; dz < dz_hi; ++dz)
+          if ((i - dz) % R == 0) brk = dz;
+        const int a1 = dz_lo, b1 = brk >= 0 ? brk : dz_hi;  // first run
+        const int a2 = b1 + 1;                                // second run: a2 .. dz_hi when brk >= 0
+        const uint64_t adesc = tc_smem_desc(ring + (i % S) * SH::PLANE, SH::GROUP, SH::PX * 16);
 #pragma unroll
-        for (int dz = 0; dz < 3; ++dz) adesc[dz] = tc_smem_desc(ring + ((j + dz) % S) * SH::PLANE, SH::GROUP, SH::PX * 16);
-#pragma unroll
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        for (int t = 0; t < 9; ++t) {
+          const int dy = t / 3, dx = t % 3;
 #pragma unroll
           for (int kk = 0; kk < CIN / 16; ++kk) {
-            const uint64_t ad = adesc[dz] + (uint64_t)(((dy * SH::PX + dx) * 16 + kk * 2 * SH::GROUP) >> 4);
-            const uint64_t bd = bdesc + (uint64_t)((tap * CG * NC * 16 + kk * 2 * NC * 16) >> 4);
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
-                "l"(ad), "l"(bd), "r"(IDESC), "r"((uint32_t)((tap | kk) != 0 ? 1 : 0))
-                : "memory");
+            const uint64_t ad = adesc + (uint64_t)(((dy * SH::PX + dx) * 16 + kk * 2 * SH::GROUP) >> 4);
+            const uint64_t bt = bdesc + (uint64_t)(((t * CG + 2 * kk) * N3 * 16) >> 4);
+            tc_mma_acc(tmem + (uint32_t)(blk(i - a1) * NC), ad, bt + (uint64_t)((a1 * NC * 16) >> 4), (b1 - a1 + 1) * NC);
+            if (brk >= 0)
+              tc_mma_acc(tmem + (uint32_t)(blk(i - a2) * NC), ad, bt + (uint64_t)((a2 * NC * 16) >> 4),
+                         (dz_hi - a2 + 1) * NC);
           }
         }
-        tc_commit(accf(b));        // the epilogue may read accumulator b
-        tc_commit(empty(j % S));   // plane z-1 (ring index j) is no longer read
+        tc_commit(empty(i % S));                   // plane i is no longer read
+        if (dz_hi == 2) tc_commit(accf((i - 2) % R));  // output i-2 has all its contributions
       }
       tc_commit(done);  // every MMA this CTA issued has completed once this barrier flips
       (void)tc_mbar_wait(done, 0);
@@ -438,21 +473,23 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
     const int gx = x0 + (lane & 7), gy = y0 + 4 * q + (lane >> 3);
     const bool valid = gx < a.nx && gy < a.ny;
     for (int j = 0; j < nout; ++j) {
-      const int b = j & 1;
-      const bool ok = __all_sync(0xffffffffu, tc_mbar_wait(accf(b), (j >> 1) & 1, stop));
+      const bool ok = __all_sync(0xffffffffu, tc_mbar_wait(accf(j % R), (j / R) & 1, stop));
       if (!ok) {
         if (lane == 0) fail();
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float v[NC];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NC);
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(blk(j) * NC);
 #pragma unroll
       for (int h = 0; h < NC / 16; ++h) tc_ld16(taddr + 16 * h, v + 16 * h);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int h = 0; h < NC / 16; ++h) tc_st16_zero(taddr + 16 * h);  // the block's next output starts at zero
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) tc_mbar_arrive(acce(b));  // accumulator b may be overwritten
+      if (lane == 0) tc_mbar_arrive(acce(j % R));  // the block may take output j + R
       if (valid) {
         const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * (z0 + j));
 #pragma unroll
