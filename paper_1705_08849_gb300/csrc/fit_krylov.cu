@@ -1767,16 +1767,8 @@ struct Seq {
     using V = typename cplx<T>::t;
     constexpr int CH = FgChunk<T>::CH;
     const int nv = j + 1;
-    if (bulk_ok()) {
-      // Three stages while they fit two blocks per SM; beyond that one block per SM with as many
-      // stages as its shared memory holds (a stage is j + 2 rows of CH values): the chunks a block has
-      // in flight while it computes are what keeps HBM busy, and two stages of the largest basis left
-      // the passes at about half the copy bandwidth.
-      const size_t stage = (size_t)(j + 2) * CH * sizeof(V), room = 216 * 1024;
-      if (3 * stage <= 100 * 1024) ortho_bulk<T, MODE, 3>(j, h);
-      else if (6 * stage <= room) ortho_bulk<T, MODE, 6>(j, h);
-      else if (4 * stage <= room) ortho_bulk<T, MODE, 4>(j, h);
-      else if (3 * stage <= room) ortho_bulk<T, MODE, 3>(j, h);
+    if (bulk_ok()) {  // three stages while they fit two blocks per SM, else two
+      if ((size_t)3 * (j + 2) * CH * sizeof(V) <= 100 * 1024) ortho_bulk<T, MODE, 3>(j, h);
       else ortho_bulk<T, MODE, 2>(j, h);
       return;
     }
