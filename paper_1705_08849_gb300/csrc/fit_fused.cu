@@ -50,7 +50,6 @@ constexpr int TX = 32;  // one warp per tile row
 template <typename T, int TY, bool KU = false>  // KU: the stage also holds the epilogue vector u
 struct Layout {
   using V = typename cplx<T>::t;
-  using Real = T;
   static constexpr int CE = sizeof(V) / 8;      // 8-byte copy elements per complex value
   static constexpr int EW = 3 * (TX + 4);       // complex values per staged e row
   static constexpr int ER = TY + 2;
@@ -101,12 +100,8 @@ struct FusedArgs {
 // are mask bytes 14 .. TX+17, i.e. 32-bit words 3 .. 12 of each row (the outer halves of words 3
 // and 12 belong to cells outside the e row).  NT threads share the plane; every thread loads its
 // words first (independent loads, no per-row vote), and only a nonzero word costs any stores.
-// A masked row of A is the identity, so a masked edge's output is its raw x.  Before zeroing a masked
-// edge of one of the tile's own cells (rows 1 .. TY, staged cells 2 .. 33), the raw value is stashed
-// in that edge's own M_eps and M_kappa slots of the staged plane (re in eps[w], im in kappa[w]), which
-// a masked row does not use: the consumers read those slots anyway and need no load from global memory.
 template <typename L, int NT>
-__device__ inline void zero_masked_plane(typename L::V* e, const uint8_t* m, typename L::Real* ek, int t) {
+__device__ inline void zero_masked_plane(typename L::V* e, const uint8_t* m, int t) {
   using V = typename L::V;
   constexpr int NWR = 10, NWORDS = L::ER * NWR, ROUNDS = (NWORDS + NT - 1) / NT;
   static_assert(TX == 32 && L::MW % 4 == 0 && 4 * (3 + NWR) <= L::MW, "mask row layout: 36 staged columns");
@@ -132,17 +127,7 @@ __device__ inline void zero_masked_plane(typename L::V* e, const uint8_t* m, typ
     for (int bi = 0; bi < 4; ++bi) {
       const uint32_t mb = (wv[r] >> (8 * bi)) & 0xFFu;
       if (mb) {
-        const int c = 4 * wi + bi - 14;  // staged cell index of this mask byte
-        V* ec = e + cy * L::EW + 3 * c;
-        if (cy >= 1 && cy <= L::ER - 2 && c >= 2 && c < 2 + TX) {
-          typename L::Real* kc = ek + (cy - 1) * L::KW + 6 * (c - 2);
-#pragma unroll
-          for (int w = 0; w < 3; ++w)
-            if (mb & (1u << w)) {
-              kc[w] = ec[w].x;
-              kc[3 + w] = ec[w].y;
-            }
-        }
+        V* ec = e + cy * L::EW + 3 * (4 * wi + bi - 14);
         if (mb & 1u) ec[0] = czero<V>();
         if (mb & 2u) ec[1] = czero<V>();
         if (mb & 4u) ec[2] = czero<V>();
@@ -296,8 +281,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
       }
     };
     auto zero_pass = [&](int q) {  // P: zero masked components of the staged e plane
-      zero_masked_plane<L, TX * TY>((V*)(stage(G0 + q) + L::E_OFF), stage(G0 + q) + L::M_OFF,
-                                    (T*)(stage(G0 + q) + L::K_OFF), tid);
+      zero_masked_plane<L, TX * TY>((V*)(stage(G0 + q) + L::E_OFF), stage(G0 + q) + L::M_OFF, tid);
       fence_proxy_async();  // order these generic writes before later bulk copies into the stage
     };
 
@@ -404,8 +388,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
         V out;
         V xv = e0[w];
         if ((m >> w) & 1) {
-          xv.x = ek[w];  // raw x on a masked edge, stashed by the masking pass
-          xv.y = ek[3 + w];
+          xv = valid ? xg[cbase + w] : czero<V>();  // raw x on a masked edge
           out = xv;
         } else {
           const T ar = -w2 * ek[w], ai = w1 * ek[3 + w];
@@ -701,7 +684,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
           if (lane == 0) fail();
           return;
         }
-        zero_masked_plane<L, 32>((V*)(stage(G) + L::E_OFF), stage(G) + L::M_OFF, (T*)(stage(G) + L::K_OFF), lane);
+        zero_masked_plane<L, 32>((V*)(stage(G) + L::E_OFF), stage(G) + L::M_OFF, lane);
         fence_proxy_async();  // these generic writes precede the stage's next bulk copy
         __syncwarp();
         if (lane == 0) mbar_arrive(&ready[G % S]);
@@ -837,8 +820,7 @@ __global__ void __launch_bounds__(TX*(TY + 2), ws_min_blocks<T, TY>()) ws_apply_
             V out;
             V xv = e0[w];
             if ((m >> w) & 1) {
-              xv.x = ek[w];  // raw x on a masked edge, stashed by the masking warp
-              xv.y = ek[3 + w];
+              xv = valid ? xg[rowbase + 3 * tx + w] : czero<V>();  // raw x on a masked edge
               out = xv;
             } else {
               const T ar = -w2 * ek[w], ai = w1 * ek[3 + w];
