@@ -460,17 +460,6 @@ __global__ void __launch_bounds__(TX* TY, TY == 4 ? 5 : (TY == 8 ? 3 : 1)) fused
 // the consumers give after their step p - S (planes p - S and p - S + 1), so no role waits on work
 // that depends on its own later progress.  No CTA-wide barrier is needed in the steady state, and
 // the issuing warp runs into the next tile while the consumers finish the current one.
-__device__ inline bool mbar_test_wait(uint64_t* bar, uint32_t parity) {  // non-blocking probe
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 __device__ inline uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
