@@ -250,20 +250,20 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
     return FIT_ECUDA;
   }
   if (a.c2 == 0) m2 = m1;
-  const int gx = (a.nx + TX - 1) / TX, gy = (a.ny + TY - 1) / TY;
-  const long long cols = (long long)gx * gy;
+  const int gx = (a.nx + TX - 1) / TX, gy = (a.ny + TY - 1) / TY, nblk = (a.cout + NC - 1) / NC;
+  const long long cols = (long long)gx * gy * nblk;
   const long long per_col = std::max(1LL, (long long)per_sm * nsm / cols);
   const int tz = (int)std::max(2LL, ((long long)a.nz + per_col - 1) / per_col);
   const int nzc = (a.nz + tz - 1) / tz;
-  dim3 grid(gx, gy, (unsigned)nzc);
+  dim3 grid(gx, gy, (unsigned)(nzc * nblk));
   kern<<<grid, 192, smem, s>>>(m1, m2, a, tz);
   FIT_CHECK_CUDA(cudaGetLastError());
   return FIT_OK;
 }
 
-// The convolutions run on the tcgen05 kernels: every 3x3x3 shape but 64 -> 64 (the 64 x 64 x 27 bf16
-// weights alone take 221 KB of shared memory; that conv, at 32^3, stays on mma.sync) and both transposed
-// convs.  FIT_CONV=mma puts every conv back on the legacy mma.sync / CUDA-core kernels (both paths pass
+// The convolutions run on the tcgen05 kernels: every 3x3x3 shape (the 64 -> 64 conv in two blocks of 32
+// output channels: its 64 x 64 x 27 bf16 weights alone would take 221 KB of shared memory) and both
+// transposed convs.  FIT_CONV=mma puts every conv back on the legacy mma.sync / CUDA-core kernels (both paths pass
 // the same parity tests; at 128^3 the network takes 0.68 ms on tcgen05 against 1.59 ms on mma.sync).
 static bool conv_use_tc() {
   const char* e = getenv("FIT_CONV");
@@ -275,6 +275,7 @@ static bool conv_use_tc() {
 static fit_status conv3_tc(const unet::ConvArgs& a, int cin, cudaStream_t s, bool* done) {
   *done = false;
   if (!conv_use_tc() || a.c1 % 8 || a.c2 % 8 || a.o1 % 8 || a.o2 % 8 || a.cout > 64) return FIT_OK;
+  // (with cout > NC a CTA computes one block of NC output channels)
   *done = true;
   // shared memory per CTA: weights 27 * cin * NC * 2 B plus S planes of cin / 8 * 2944 B
   if (cin == 16 && a.cout <= 16) return launch_conv3_tc<16, 16, 6>(a, s);  // 50 KB
@@ -283,7 +284,7 @@ static fit_status conv3_tc(const unet::ConvArgs& a, int cin, cudaStream_t s, boo
   if (cin == 32 && a.cout <= 16) return launch_conv3_tc<32, 16, 4>(a, s);  // 76 KB
   if (cin == 32 && a.cout <= 32) return launch_conv3_tc<32, 32, 4>(a, s);  // 103 KB
   if (cin == 32) return launch_conv3_tc<32, 64, 4>(a, s);                  // 159 KB
-  if (cin == 64 && a.cout <= 32) return launch_conv3_tc<64, 32, 4>(a, s);  // 206 KB
+  if (cin == 64) return launch_conv3_tc<64, 32, 4>(a, s);                  // 206 KB; 64 -> 64 in two blocks
   *done = false;
   return FIT_OK;
 }

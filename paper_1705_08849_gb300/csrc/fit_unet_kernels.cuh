@@ -328,7 +328,8 @@ __device__ inline void tc_mma_acc(uint32_t dcol, uint64_t ad, uint64_t bd, int n
 }
 
 // tm1 / tm2: 5D maps {8 channels, groups, nx, ny, nz} of the two inputs (box {8, 1, 10, 18, 1});
-// tm2 is unused when a.c2 == 0.  Requires cout <= NC and every channel count a multiple of 8.
+// tm2 is unused when a.c2 == 0.  Every channel count a multiple of 8; with cout > NC the output
+// channels are split into blocks of NC over blockIdx.z.
 template <int CIN, int NC, int S>
 __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1,
                                                        const __grid_constant__ CUtensorMap tm2, ConvArgs a, int tz) {
@@ -349,7 +350,9 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
   volatile int* stop = (volatile int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * SH::TX, y0 = blockIdx.y * SH::TY;
-  const int z0 = blockIdx.z * tz, z1 = min(a.nz, z0 + tz);
+  // blockIdx.z = z-chunk * nblk + output-channel block: a CTA computes output channels n0 .. n0+NC-1
+  const int nblk = (a.cout + NC - 1) / NC, n0 = (blockIdx.z % nblk) * NC;
+  const int z0 = (blockIdx.z / nblk) * tz, z1 = min(a.nz, z0 + tz);
   if (z0 >= z1) return;  // uniform over the CTA, before any TMEM is taken
   const int nout = z1 - z0, nplanes = nout + 2;  // planes z0-1 .. z1
   const int cg1 = a.c1 / 8, cg2 = a.c2 / 8;
@@ -373,18 +376,18 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
     *stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // weights: line (t, g, dz * NC + n) = W[dz * 9 + t][n][8g .. 8g+7] (output channels beyond cout are zero)
+  // weights: line (t, g, dz * NC + n) = W[dz * 9 + t][n0 + n][8g .. 8g+7] (channels beyond cout are zero)
   for (int q = tid; q < 9 * CG * N3; q += 192) {
     const int n3 = q % N3, g = (q / N3) % CG, t = q / (N3 * CG);
     const int dz = n3 / NC, n = n3 % NC;
-    const bool in = n < a.cout;
+    const bool in = n0 + n < a.cout;
     const void* src =
-        in ? (const void*)(a.w + ((long long)(dz * 9 + t) * a.cout + n) * CIN + g * 8) : (const void*)a.w;
+        in ? (const void*)(a.w + ((long long)(dz * 9 + t) * a.cout + n0 + n) * CIN + g * 8) : (const void*)a.w;
     cp_async16(w_s + q * 16, src, in ? 16 : 0);
   }
   cp_async_commit();
   float* bias_s = (float*)(smem + SH::OFF_BIAS);
-  for (int n = tid; n < NC; n += 192) bias_s[n] = (a.bias && n < a.cout) ? a.bias[n] : 0.f;
+  for (int n = tid; n < NC; n += 192) bias_s[n] = (a.bias && n0 + n < a.cout) ? a.bias[n0 + n] : 0.f;
   cp_async_wait<0>();
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the weights, to the tensor core's reads
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -494,12 +497,12 @@ __global__ void __launch_bounds__(192) conv3_tc_kernel(const __grid_constant__ C
         const long long gv = gx + (long long)a.nx * (gy + (long long)a.ny * (z0 + j));
 #pragma unroll
         for (int c8 = 0; c8 < NC / 8; ++c8) {
-          const int co = c8 * 8;
+          const int cl = c8 * 8, co = n0 + cl;  // the block's channel and the layer's
           if (co >= a.cout) break;
           uint32_t pk[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            float v0 = v[co + 2 * e] + bias_s[co + 2 * e], v1 = v[co + 2 * e + 1] + bias_s[co + 2 * e + 1];
+            float v0 = v[cl + 2 * e] + bias_s[cl + 2 * e], v1 = v[cl + 2 * e + 1] + bias_s[cl + 2 * e + 1];
             if (a.relu) {
               v0 = fmaxf(v0, 0.f);
               v1 = fmaxf(v1, 0.f);
