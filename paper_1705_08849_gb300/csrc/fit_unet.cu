@@ -264,7 +264,7 @@ fit_status launch_conv3_tc(const unet::ConvArgs& a, cudaStream_t s) {
 // The convolutions run on the tcgen05 kernels: every 3x3x3 shape (the 64 -> 64 conv in two blocks of 32
 // output channels: its 64 x 64 x 27 bf16 weights alone would take 221 KB of shared memory) and both
 // transposed convs.  FIT_CONV=mma puts every conv back on the legacy mma.sync / CUDA-core kernels (both paths pass
-// the same parity tests; at 128^3 the network takes 0.68 ms on tcgen05 against 1.59 ms on mma.sync).
+// the same parity tests; at 128^3 the network takes 0.66 ms on tcgen05 against 1.59 ms on mma.sync).
 static bool conv_use_tc() {
   const char* e = getenv("FIT_CONV");
   return !(e && !strcmp(e, "mma"));
