@@ -332,16 +332,19 @@ fit_status fit_unet_conv3(int nx, int ny, int nz, int cin, int cout, const void*
  *   din[v][ci] = sum_{tap, co} dout[v - off(tap)][co] W[tap][co][ci];  dout [N][cout] bf16, din [N][cin] bf16 */
 fit_status fit_unet_conv3_dgrad(int nx, int ny, int nz, int cin, int cout, const void* dout, const float* w,
                                 void* din, void* stream);
-/* fit_unet_conv3_wgrad -- its weight gradient (FP32 on the CUDA cores), overwritten:
+/* fit_unet_conv3_wgrad -- its weight gradient (a GEMM over voxels per tap on the tensor cores, bf16 operands,
+ * FP32 accumulation), overwritten:
  *   dw[tap][co][ci] = sum_v dout[v][co] in[v + off(tap)][ci],  db[co] = sum_v dout[v][co] (db may be NULL) */
 fit_status fit_unet_conv3_wgrad(int nx, int ny, int nz, int cin, int cout, const void* in, const void* dout,
                                 float* dw, float* db, void* stream);
 /* fit_unet_tconv -- 2x2x2 transposed convolution, stride 2, from an mx x my x mz grid to the 2x finer one:
  *   out[X][co] = b[co] + sum_ci in[X / 2][ci] W[k][co][ci], k = X_x%2 + 2 (X_y%2) + 4 (X_z%2);
- *   (cin, cout) = (64, 32) or (32, 16); in [mx*my*mz][cin] bf16, w [8][cout][cin] FP32, out bf16 */
+ *   (cin, cout) = (64, 32) or (32, 16); in [mx*my*mz][cin] bf16, w [8][cout][cin] FP32 master weights that
+ *   enter as their bf16 rounding (as in the network), FP32 accumulation, out bf16 */
 fit_status fit_unet_tconv(int mx, int my, int mz, int cin, int cout, const void* in, const float* w,
                           const float* b, void* out, void* stream);
-/* fit_unet_tconv_backward -- din[V][ci] = sum_{k, co} dout[child(V, k)][co] W[k][co][ci] (bf16), and, overwritten,
+/* fit_unet_tconv_backward -- din[V][ci] = sum_{k, co} dout[child(V, k)][co] W[k][co][ci] (bf16, W as its bf16
+ * rounding), and, overwritten,
  * dw[k][co][ci] = sum_V in[V][ci] dout[child(V, k)][co], db[co] = sum dout[.][co] (FP32) */
 fit_status fit_unet_tconv_backward(int mx, int my, int mz, int cin, int cout, const void* in, const void* dout,
                                    const float* w, void* din, float* dw, float* db, void* stream);
